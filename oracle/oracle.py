@@ -1,0 +1,236 @@
+"""ctypes wrapper of the CPU oracle (test infrastructure only).
+
+Only the tests, __graft_entry__.smoke() and bench.py's CPU-baseline leg use
+this module.  Matrices are passed in the interchange format (limb planes,
+exponent, sign) as any object with .limb/.exp/.sign/.p attributes and
+returned as OMat objects with the same attributes.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SIMPLE, BLOCK, STRASSEN, WINOGRAD = 0, 1, 2, 3
+PEEL, MIXED = 0, 1
+EXP_ZERO = np.iinfo(np.int64).min
+
+_lib = None
+
+
+class OMat:
+    """Interchange-format matrix returned by the oracle."""
+
+    def __init__(self, limb, exp, sign, p):
+        self.limb, self.exp, self.sign, self.p = limb, exp, sign, p
+
+    @property
+    def shape(self):
+        return self.exp.shape
+
+    @staticmethod
+    def empty(rows, cols, p):
+        L = (p + 63) // 64
+        return OMat(np.zeros((L, rows, cols), np.uint64),
+                    np.full((rows, cols), EXP_ZERO, np.int64),
+                    np.zeros((rows, cols), np.int8), p)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(_build.build())
+        _lib.orc_api_sample_set.restype = C.c_int64
+        _lib.orc_api_max_threads.restype = C.c_int
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _mat_args(M):
+    limb = np.ascontiguousarray(M.limb, dtype=np.uint64)
+    exp = np.ascontiguousarray(M.exp, dtype=np.int64)
+    sign = np.ascontiguousarray(M.sign, dtype=np.int8)
+    rows, cols = exp.shape
+    keep = (limb, exp, sign)
+    return keep, [_p(limb), _p(exp), _p(sign), C.c_int64(cols), C.c_int64(rows * cols)]
+
+
+def set_threads(n: int):
+    lib().orc_api_set_threads(C.c_int(n))
+
+
+def max_threads() -> int:
+    return lib().orc_api_max_threads()
+
+
+def range_error() -> int:
+    return lib().orc_api_range_error()
+
+
+def _flat(M):
+    """1 x count view of any-shaped interchange arrays."""
+    L = M.limb.shape[0]
+    return OMat(M.limb.reshape(L, 1, -1), M.exp.reshape(1, -1), M.sign.reshape(1, -1), M.p)
+
+
+def scalar(op: str, X, Y):
+    """Elementwise x op y, op in add/sub/mul/div, arrays of equal shape."""
+    code = {"add": 0, "sub": 1, "mul": 2, "div": 3}[op]
+    shape = X.exp.shape
+    Xf, Yf = _flat(X), _flat(Y)
+    count = Xf.exp.shape[1]
+    R = OMat.empty(1, count, X.p)
+    kx, ax = _mat_args(Xf)
+    ky, ay = _mat_args(Yf)
+    kr, ar = _mat_args(R)
+    rc = lib().orc_api_scalar(C.c_int(code), C.c_int(X.p), C.c_int64(count), *ax, *ay, *ar)
+    if rc == -2:
+        raise ValueError("invalid operand encoding")
+    out = OMat(kr[0].reshape((R.limb.shape[0],) + shape), kr[1].reshape(shape),
+               kr[2].reshape(shape), X.p)
+    return out, rc
+
+
+def convert(X, p_to: int):
+    shape = X.exp.shape
+    Xf = _flat(X)
+    count = Xf.exp.shape[1]
+    R = OMat.empty(1, count, p_to)
+    kx, ax = _mat_args(Xf)
+    kr, ar = _mat_args(R)
+    rc = lib().orc_api_convert(C.c_int(X.p), C.c_int(p_to), C.c_int64(count), *ax, *ar)
+    if rc:
+        raise ValueError("invalid operand encoding")
+    return OMat(kr[0].reshape((R.limb.shape[0],) + shape), kr[1].reshape(shape),
+                kr[2].reshape(shape), p_to)
+
+
+def to_double(X) -> np.ndarray:
+    shape = X.exp.shape
+    Xf = _flat(X)
+    count = Xf.exp.shape[1]
+    out = np.zeros(count, np.float64)
+    kx, ax = _mat_args(Xf)
+    rc = lib().orc_api_to_double(C.c_int(X.p), C.c_int64(count), *ax, _p(out))
+    if rc:
+        raise ValueError("invalid operand encoding")
+    return out.reshape(shape)
+
+
+def gemm(algo: int, A, B, cutoff: int = 64, policy: int = PEEL, nb: int = 32):
+    m, l = A.exp.shape
+    l2, n = B.exp.shape
+    assert l == l2 and A.p == B.p
+    Cm = OMat.empty(m, n, A.p)
+    ka, aa = _mat_args(A)
+    kb, ab = _mat_args(B)
+    kc, ac = _mat_args(Cm)
+    rc = lib().orc_api_gemm(C.c_int(algo), C.c_int(cutoff), C.c_int(policy), C.c_int(nb),
+                            C.c_int64(m), C.c_int64(l), C.c_int64(n), C.c_int(A.p),
+                            *aa, *ab, *ac)
+    if rc:
+        raise ValueError("oracle gemm failed: %d" % rc)
+    return OMat(*kc, A.p)
+
+
+def gemm_counted(algo: int, A, B, cutoff: int = 64, policy: int = PEEL, nb: int = 32):
+    m, l = A.exp.shape
+    n = B.exp.shape[1]
+    Cm = OMat.empty(m, n, A.p)
+    ka, aa = _mat_args(A)
+    kb, ab = _mat_args(B)
+    kc, ac = _mat_args(Cm)
+    mul, add = C.c_uint64(), C.c_uint64()
+    rc = lib().orc_api_gemm_counted(C.c_int(algo), C.c_int(cutoff), C.c_int(policy),
+                                    C.c_int(nb), C.c_int64(m), C.c_int64(l), C.c_int64(n),
+                                    C.c_int(A.p), *aa, *ab, *ac, C.byref(mul), C.byref(add))
+    if rc:
+        raise ValueError("oracle gemm failed: %d" % rc)
+    return OMat(*kc, A.p), mul.value, add.value
+
+
+def count_model(algo: int, m: int, l: int, n: int, cutoff: int, policy: int = PEEL):
+    mul, add = C.c_uint64(), C.c_uint64()
+    lib().orc_api_count_model(C.c_int(algo), C.c_int64(m), C.c_int64(l), C.c_int64(n),
+                              C.c_int(cutoff), C.c_int(policy), C.byref(mul), C.byref(add))
+    return mul.value, add.value
+
+
+def sample_set(side: int, algo: int, m: int, l: int, n: int, cutoff: int, policy: int,
+               x0: int) -> np.ndarray:
+    out = np.zeros(4096, np.int64)
+    k = lib().orc_api_sample_set(C.c_int(side), C.c_int(algo), C.c_int64(m), C.c_int64(l),
+                                 C.c_int64(n), C.c_int(cutoff), C.c_int(policy),
+                                 C.c_int64(x0), _p(out), C.c_int64(4096))
+    if k < 0:
+        raise ValueError("sample set too large")
+    return out[:k].copy()
+
+
+def gemm_sampled(algo: int, A, B, rows, cols, cutoff: int = 64, policy: int = PEEL):
+    m, l = A.exp.shape
+    n = B.exp.shape[1]
+    rows = np.ascontiguousarray(rows, np.int64)
+    cols = np.ascontiguousarray(cols, np.int64)
+    Cm = OMat.empty(len(rows), len(cols), A.p)
+    ka, aa = _mat_args(A)
+    kb, ab = _mat_args(B)
+    kc, ac = _mat_args(Cm)
+    rc = lib().orc_api_gemm_sampled(C.c_int(algo), C.c_int(cutoff), C.c_int(policy),
+                                    C.c_int64(m), C.c_int64(l), C.c_int64(n), C.c_int(A.p),
+                                    *aa, *ab, _p(rows), C.c_int64(len(rows)), _p(cols),
+                                    C.c_int64(len(cols)), *ac)
+    if rc:
+        raise ValueError("oracle sampled gemm failed: %d" % rc)
+    return OMat(*kc, A.p)
+
+
+def dot_exact(A, B, rows=None, cols=None, p_out: int | None = None):
+    """RN_{p_out}(exact sum_k a_ik b_kj) on rows x cols (all by default)."""
+    m, l = A.exp.shape
+    n = B.exp.shape[1]
+    p_out = A.p if p_out is None else p_out
+    rows = np.arange(m) if rows is None else rows
+    cols = np.arange(n) if cols is None else cols
+    rows = np.ascontiguousarray(rows, np.int64)
+    cols = np.ascontiguousarray(cols, np.int64)
+    Cm = OMat.empty(len(rows), len(cols), p_out)
+    ka, aa = _mat_args(A)
+    kb, ab = _mat_args(B)
+    kc, ac = _mat_args(Cm)
+    rc = lib().orc_api_dot_exact(C.c_int64(m), C.c_int64(l), C.c_int64(n), C.c_int(A.p),
+                                 C.c_int(p_out), *aa, *ab, _p(rows), C.c_int64(len(rows)),
+                                 _p(cols), C.c_int64(len(cols)), *ac)
+    if rc:
+        raise ValueError("oracle exact dot failed: %d" % rc)
+    return OMat(*kc, p_out)
+
+
+def lu(A, panel: int = 128, algo: int = SIMPLE, cutoff: int = 64, policy: int = PEEL):
+    """Returns (LU factors, piv, status); status 0 ok, k+1 for a zero pivot in column k."""
+    n = A.exp.shape[0]
+    M = OMat(A.limb.copy(), A.exp.copy(), A.sign.copy(), A.p)
+    piv = np.zeros(n, np.int64)
+    km, am = _mat_args(M)
+    rc = lib().orc_api_lu(C.c_int64(n), C.c_int(A.p), C.c_int(panel), C.c_int(algo),
+                          C.c_int(cutoff), C.c_int(policy), *am, _p(piv))
+    return OMat(*km, A.p), piv, rc
+
+
+def lu_solve(LU, piv, b):
+    n = LU.exp.shape[0]
+    X = OMat.empty(n, 1, LU.p)
+    ka, aa = _mat_args(LU)
+    kb, ab = _mat_args(b)
+    kx, ax = _mat_args(X)
+    piv = np.ascontiguousarray(piv, np.int64)
+    rc = lib().orc_api_lu_solve(C.c_int64(n), C.c_int(LU.p), *aa, _p(piv), *ab, *ax)
+    if rc:
+        raise ValueError("oracle solve failed: %d" % rc)
+    return OMat(*kx, LU.p)

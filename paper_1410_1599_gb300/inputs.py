@@ -1,0 +1,304 @@
+"""Seeded synthetic inputs shared by the CUDA path and the CPU oracle.
+
+This module holds only the interchange container and the generators; it does
+no multiple-precision arithmetic of the method (no rounded add, multiply or
+divide).  Every value it produces is exactly representable in the requested
+precision and is built with integer operations.
+
+Interchange format of a rows x cols matrix at precision p, L = ceil(p/64):
+    limb[k, r, c]  uint64   limb k of the mantissa, k = 0 most significant;
+                            the mantissa is the fraction sum_k limb_k 2^(-64(k+1))
+                            in [1/2, 1) with its top bit set
+    exp[r, c]      int64    value = (-1)^sign * mantissa * 2^exp;
+                            EXP_ZERO (INT64_MIN) marks zero
+    sign[r, c]     int8     0 = +, 1 = -
+
+Random draws use SplitMix64 (Steele, Lea, Flood 2014) as a counter-based
+generator: word i of stream `seed` is mix(seed + (i + 1) * 0x9E3779B97F4A7C15).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from fractions import Fraction
+
+import numpy as np
+
+EXP_ZERO = np.iinfo(np.int64).min
+GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def limbs_for(p: int) -> int:
+    return (p + 63) // 64
+
+
+@dataclass
+class HostMP:
+    """A matrix of p-bit numbers in the interchange format (host memory)."""
+
+    limb: np.ndarray  # (L, rows, cols) uint64
+    exp: np.ndarray  # (rows, cols) int64
+    sign: np.ndarray  # (rows, cols) int8
+    p: int
+
+    @property
+    def shape(self):
+        return self.exp.shape
+
+    @property
+    def L(self):
+        return self.limb.shape[0]
+
+    @staticmethod
+    def zeros(rows: int, cols: int, p: int) -> "HostMP":
+        L = limbs_for(p)
+        return HostMP(np.zeros((L, rows, cols), np.uint64),
+                      np.full((rows, cols), EXP_ZERO, np.int64),
+                      np.zeros((rows, cols), np.int8), p)
+
+    def copy(self) -> "HostMP":
+        return HostMP(self.limb.copy(), self.exp.copy(), self.sign.copy(), self.p)
+
+    def sub(self, rows, cols) -> "HostMP":
+        """Entries at the given row and column index arrays (a new matrix)."""
+        r = np.asarray(rows)[:, None]
+        c = np.asarray(cols)[None, :]
+        return HostMP(self.limb[:, r, c], self.exp[r, c], self.sign[r, c], self.p)
+
+    def equal(self, other: "HostMP") -> bool:
+        return (self.p == other.p and self.shape == other.shape
+                and np.array_equal(self.limb, other.limb)
+                and np.array_equal(self.exp, other.exp)
+                and np.array_equal(self.sign, other.sign))
+
+    def mismatches(self, other: "HostMP") -> np.ndarray:
+        """Boolean (rows, cols) mask of entries whose bits differ."""
+        return ((self.limb != other.limb).any(axis=0) | (self.exp != other.exp)
+                | (self.sign != other.sign))
+
+    # exact conversions, for building fixtures and reading results
+    def to_fractions(self):
+        out = []
+        for r in range(self.shape[0]):
+            row = []
+            for c in range(self.shape[1]):
+                row.append(entry_fraction(self, r, c))
+            out.append(row)
+        return out
+
+
+def entry_int(M: HostMP, r: int, c: int) -> int:
+    """Mantissa of entry (r, c) as an integer of 64*L bits."""
+    v = 0
+    for k in range(M.limb.shape[0]):
+        v = (v << 64) | int(M.limb[k, r, c])
+    return v
+
+
+def entry_fraction(M: HostMP, r: int, c: int) -> Fraction:
+    e = int(M.exp[r, c])
+    if e == EXP_ZERO:
+        return Fraction(0)
+    v = Fraction(entry_int(M, r, c), 1 << (64 * M.limb.shape[0])) * (Fraction(2) ** e)
+    return -v if M.sign[r, c] else v
+
+
+def from_exact_ints(values, p: int, shape) -> HostMP:
+    """Matrix of exact values given as (sign, integer numerator N, scale s),
+    value = (-1)^sign N 2^-s, with N < 2^p (so no rounding is needed)."""
+    rows, cols = shape
+    M = HostMP.zeros(rows, cols, p)
+    L = M.L
+    for idx, (sg, N, s) in enumerate(values):
+        r, c = divmod(idx, cols)
+        if N == 0:
+            M.sign[r, c] = sg
+            continue
+        bl = N.bit_length()
+        assert bl <= p, "value needs more than p bits"
+        mant = N << (64 * L - bl)
+        for k in range(L):
+            M.limb[k, r, c] = (mant >> (64 * (L - 1 - k))) & 0xFFFFFFFFFFFFFFFF
+        M.exp[r, c] = bl - s
+        M.sign[r, c] = sg
+    return M
+
+
+def from_ints(mat, p: int) -> HostMP:
+    """Integer matrix (nested lists or 2-D array) to p-bit numbers."""
+    a = [[int(x) for x in row] for row in mat]
+    rows, cols = len(a), len(a[0]) if a else 0
+    vals = [(1 if x < 0 else 0, abs(x), 0) for row in a for x in row]
+    return from_exact_ints(vals, p, (rows, cols))
+
+
+# ---------------------------------------------------------------------------
+# SplitMix64
+# ---------------------------------------------------------------------------
+def splitmix64(seed: int, count: int, offset: int = 0) -> np.ndarray:
+    i = np.arange(offset + 1, offset + count + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + i * GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def _clz64(v: np.ndarray) -> np.ndarray:
+    """Leading zero bits of nonzero uint64 values."""
+    v = v.copy()
+    n = np.zeros(v.shape, np.int64)
+    for s in (32, 16, 8, 4, 2, 1):
+        m = (v >> np.uint64(64 - s)) == 0
+        n += np.where(m, s, 0)
+        v = np.where(m, v << np.uint64(s), v)
+    return n
+
+
+def _normalize(X: np.ndarray, over: np.ndarray):
+    """X: (N, L) uint64 fixed-point fractions (limb 0 most significant), value
+    X / 2^(64L) + over (over in {0,1}, set only when X == 0).  Returns the
+    normalised (N, L) mantissas, exponents and a zero mask."""
+    N, L = X.shape
+    nz = X != 0
+    first = np.where(nz.any(axis=1), nz.argmax(axis=1), L)
+    zero = (first == L) & (over == 0)
+    lead = X[np.arange(N), np.minimum(first, L - 1)]
+    lead = np.where(first < L, lead, np.uint64(1))
+    z = first * 64 + _clz64(lead)
+    z = np.where(first < L, z, 0)
+    zw = z // 64
+    zb = (z % 64).astype(np.uint64)
+    Xp = np.concatenate([X, np.zeros((N, L + 1), np.uint64)], axis=1)
+    out = np.zeros_like(X)
+    for t in range(L):
+        hi = Xp[np.arange(N), t + zw]
+        lo = Xp[np.arange(N), t + zw + 1]
+        sh = np.where(zb == 0, hi, (hi << zb) | (lo >> (np.uint64(64) - np.where(zb == 0, 1, zb).astype(np.uint64))))
+        out[:, t] = sh
+    exp = -z
+    # the value exactly 1.0 (X wrapped to 0 with the carry in `over`)
+    one = (over == 1)
+    out[one, :] = 0
+    out[one, 0] = np.uint64(1) << np.uint64(63)
+    exp = np.where(one, 1, exp)
+    out[zero, :] = 0
+    exp = np.where(zero, EXP_ZERO, exp)
+    return out, exp.astype(np.int64), zero
+
+
+def uniform_pm1(rows: int, cols: int, p: int, seed: int, exp_lo: int = 0,
+                exp_hi: int = 0) -> HostMP:
+    """Entries v * 2^e, v uniform on the grid k / 2^(p-1), k in [-2^(p-1), 2^(p-1)),
+    i.e. uniform in [-1, 1) and exact in p bits; e uniform in [exp_lo, exp_hi]."""
+    L = limbs_for(p)
+    N = rows * cols
+    w = splitmix64(seed, N * (L + 1)).reshape(N, L + 1)
+    neg = (w[:, 0] & np.uint64(1)).astype(np.int8)
+    span = exp_hi - exp_lo + 1
+    e = exp_lo + ((w[:, 0] >> np.uint64(1)) % np.uint64(span)).astype(np.int64)
+    X = w[:, 1:].copy()
+    # keep the top p-1 bits of the 64L-bit string: j in [0, 2^(p-1))
+    drop = 64 * L - (p - 1)
+    for t in range(L - 1, -1, -1):
+        lo_bit = 64 * (L - 1 - t)  # bit index of this limb's LSB in the string
+        k = min(max(drop - lo_bit, 0), 64)
+        if k == 64:
+            X[:, t] = 0
+        elif k > 0:
+            X[:, t] &= ~np.uint64((1 << k) - 1)
+    # negative half: |k| = j + 1, one unit at bit `drop` of the string
+    over = np.zeros(N, np.int64)
+    carry = neg.astype(np.uint64)
+    unit_limb = L - 1 - drop // 64
+    unit = np.uint64(1) << np.uint64(drop % 64)
+    for t in range(unit_limb, -1, -1):
+        add = np.where(carry == 1, unit if t == unit_limb else np.uint64(1), np.uint64(0))
+        with np.errstate(over="ignore"):
+            s = X[:, t] + add
+        carry = ((s < X[:, t]) & (add > 0)).astype(np.uint64)
+        X[:, t] = s
+    over = carry.astype(np.int64)
+    mant, exp, zero = _normalize(X, over)
+    M = HostMP.zeros(rows, cols, p)
+    M.limb[:] = mant.T.reshape(L, rows, cols)
+    M.exp[:] = np.where(zero, EXP_ZERO, exp + e).reshape(rows, cols)
+    M.sign[:] = neg.reshape(rows, cols)
+    return M
+
+
+def rand_bits(seed: int, index: int, bits: int) -> int:
+    """An integer of `bits` random bits: draw `index` of stream `seed`."""
+    nwords = (bits + 63) // 64
+    v = 0
+    for x in splitmix64(seed, nwords, offset=index * nwords):
+        v = (v << 64) | int(x)
+    return v >> (64 * nwords - bits)
+
+
+def well_conditioned(n: int, p: int, seed: int) -> HostMP:
+    """A = U[-1,1) + n I.  Off-diagonal entries as uniform_pm1; the diagonal is
+    n + v with v uniform on the grid k / 2^q, k in [-2^q, 2^q),
+    q = p - bitlen(n) - 2, so that n + v is exact in p bits."""
+    A = uniform_pm1(n, n, p, seed)
+    q = p - n.bit_length() - 2
+    vals = []
+    for i in range(n):
+        k = rand_bits(seed ^ 0x5DEECE66D, i, q + 1) - (1 << q)
+        num = (n << q) + k
+        vals.append((0 if num >= 0 else 1, abs(num), q))
+    D = from_exact_ints(vals, p, (1, n))
+    for i in range(n):
+        A.limb[:, i, i] = D.limb[:, 0, i]
+        A.exp[i, i] = D.exp[0, i]
+        A.sign[i, i] = D.sign[0, i]
+    return A
+
+
+def rn_reciprocal(d: int, p: int):
+    """(sign, N, s) with N 2^-s = 1/d rounded to nearest-even at p bits, d >= 1."""
+    t = d.bit_length()
+    if d & (d - 1) == 0:
+        return (0, 1, t - 1)
+    Q, R = divmod(1 << (p + t - 1), d)
+    if 2 * R > d or (2 * R == d and Q & 1):
+        Q += 1
+    return (0, Q, p + t - 1)
+
+
+def lotkin(n: int, p: int) -> HostMP:
+    """First row all ones; a_ij = 1/(i+j-1) (1-based) rounded to p bits."""
+    cache = {}
+    vals = []
+    for i in range(n):
+        for j in range(n):
+            if i == 0:
+                vals.append((0, 1, 0))
+            else:
+                d = i + j + 1
+                if d not in cache:
+                    cache[d] = rn_reciprocal(d, p)
+                vals.append(cache[d])
+    return from_exact_ints(vals, p, (n, n))
+
+
+def ones(rows: int, cols: int, p: int) -> HostMP:
+    return from_exact_ints([(0, 1, 0)] * (rows * cols), p, (rows, cols))
+
+
+def identity(n: int, p: int) -> HostMP:
+    return from_exact_ints([(0, 1 if i == j else 0, 0) for i in range(n) for j in range(n)],
+                           p, (n, n))
+
+
+def small_ints(rows: int, cols: int, p: int, seed: int, bits: int) -> HostMP:
+    """Integers uniform in (-2^bits, 2^bits)."""
+    w = splitmix64(seed, rows * cols)
+    vals = []
+    for x in w:
+        x = int(x)
+        mag = (x >> 1) & ((1 << bits) - 1)
+        vals.append((x & 1 if mag else 0, mag, 0))
+    return from_exact_ints(vals, p, (rows, cols))

@@ -1,0 +1,201 @@
+"""Pins of the oracle's blocked LU with partial pivoting and the solves
+(arXiv 1410.1599 Sec. 4), and of the correctly rounded exact dot product.
+
+Independent references:
+  * A = L U built exactly from a dyadic unit-lower L with |l_ij| <= 1/2 and
+    an integer upper U: partial pivoting never exchanges rows (the diagonal
+    entry of each eliminated column dominates) and all arithmetic is exact,
+    so the factors must come back bit for bit, for every panel width and
+    trailing-update algorithm; integer right-hand sides solve exactly;
+  * the well-conditioned test matrix A = U[-1,1) + n I is column diagonally
+    dominant, so partial pivoting keeps the identity permutation and the
+    pivoted result equals the paper's unpivoted LU;
+  * a replay of Sec. 4's blocked procedure with mpmath scalar operations;
+  * exact rational sums (Fraction) rounded once by mpmath for the dot product.
+"""
+from fractions import Fraction
+
+import mpmath
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1410_1599_gb300 import inputs as gen
+from tests.mpref import entry_mpf, exact, man_exp, mp_add, mp_div, mp_mul, mp_sub
+
+
+def _factorable(n, p, seed):
+    rng = np.random.default_rng(seed)
+    Lnum = np.tril(rng.integers(-4, 5, (n, n)), -1)          # l = k/8, |l| <= 1/2
+    U = np.triu(rng.integers(-9, 10, (n, n)), 1)
+    d = rng.integers(1, 10, n) * rng.choice([-1, 1], n)
+    U += np.diag(d)
+    Lf = [[Fraction(int(Lnum[i, j]), 8) if i > j else Fraction(int(i == j)) for j in range(n)] for i in range(n)]
+    Af = [[sum(Lf[i][k] * int(U[k, j]) for k in range(n)) for j in range(n)] for i in range(n)]
+    vals = []
+    for row in Af:
+        for x in row:
+            num, den = x.numerator, x.denominator
+            s = den.bit_length() - 1
+            assert den == 1 << s
+            vals.append((int(num < 0), abs(num), s))
+    A = gen.from_exact_ints(vals, p, (n, n))
+    return A, Lf, U
+
+
+@pytest.mark.parametrize("panel", [1, 3, 8, 128])
+@pytest.mark.parametrize("algo,cutoff", [(orc.SIMPLE, 64), (orc.STRASSEN, 2), (orc.WINOGRAD, 2)])
+def test_exactly_factorable(panel, algo, cutoff):
+    n, p = 13, 256
+    A, Lf, U = _factorable(n, p, 3)
+    F, piv, rc = orc.lu(A, panel=panel, algo=algo, cutoff=cutoff)
+    assert rc == 0
+    assert list(piv) == list(range(n))
+    for i in range(n):
+        for j in range(n):
+            want = Lf[i][j] if i > j else Fraction(int(U[i, j]))
+            assert gen.entry_fraction(F, i, j) == want
+    # integer right-hand side: b = A x with x integer -> exact solution
+    xt = np.arange(1, n + 1) * np.array([(-1) ** i for i in range(n)])
+    Af = A.to_fractions()
+    b = gen.from_exact_ints([(int(v < 0), abs(v.numerator), v.denominator.bit_length() - 1)
+                             for v in (sum(Af[i][k] * int(xt[k]) for k in range(n)) for i in range(n))],
+                            p, (n, 1))
+    x = orc.lu_solve(F, piv, b)
+    assert [gen.entry_fraction(x, i, 0) for i in range(n)] == [Fraction(int(v)) for v in xt]
+
+
+def test_pivoting_exchanges_rows():
+    p = 128
+    A = gen.from_ints([[1, 2, 3], [4, 5, 6], [7, 8, 10]], p)
+    F, piv, rc = orc.lu(A, panel=2)
+    assert rc == 0 and list(piv) == [2, 2, 2]
+    # P A = L U exactly representable here? check via the exact product of the factors
+    Ff = [[gen.entry_fraction(F, i, j) for j in range(3)] for i in range(3)]
+    L = [[Ff[i][j] if i > j else Fraction(int(i == j)) for j in range(3)] for i in range(3)]
+    U = [[Ff[i][j] if i <= j else Fraction(0) for j in range(3)] for i in range(3)]
+    LU = [[sum(L[i][k] * U[k][j] for k in range(3)) for j in range(3)] for i in range(3)]
+    rows = [[1, 2, 3], [4, 5, 6], [7, 8, 10]]
+    perm = list(range(3))
+    for k, pk in enumerate(piv):
+        perm[k], perm[pk] = perm[pk], perm[k]
+    PA = [rows[r] for r in perm]
+    err = max(abs(LU[i][j] - PA[i][j]) for i in range(3) for j in range(3))
+    assert err < Fraction(1, 2 ** 120)
+
+
+def test_singular_column_reported():
+    p = 128
+    A = gen.from_ints([[1, 0, 3], [4, 0, 6], [7, 0, 10]], p)
+    _, _, rc = orc.lu(A, panel=2)
+    assert rc == 2                                     # zero pivot in column 1 (1-based 2)
+
+
+def test_well_conditioned_keeps_identity_permutation():
+    n, p = 40, 256
+    A = gen.well_conditioned(n, p, 5)
+    _, piv, rc = orc.lu(A, panel=16, algo=orc.WINOGRAD, cutoff=4)
+    assert rc == 0 and list(piv) == list(range(n))
+
+
+# ---------------------------------------------------------------------------
+# replay of Sec. 4 with mpmath scalar operations
+# ---------------------------------------------------------------------------
+def _replay_lu(A, p, panel):
+    n = len(A)
+    A = [row[:] for row in A]
+    piv = []
+    for j0 in range(0, n, panel):
+        je = min(j0 + panel, n)
+        for k in range(j0, je):
+            mag = lambda x: exact(mpmath.libmp.mpf_abs(x._mpf_))
+            best, pr = mag(A[k][k]), k
+            for i in range(k + 1, n):
+                if mag(A[i][k]) > best:
+                    best, pr = mag(A[i][k]), i
+            piv.append(pr)
+            A[k], A[pr] = A[pr], A[k]
+            for i in range(k + 1, n):
+                A[i][k] = mp_div(A[i][k], A[k][k], p)
+                for j in range(k + 1, je):
+                    A[i][j] = mp_sub(A[i][j], mp_mul(A[i][k], A[k][j], p), p)
+        if je >= n:
+            break
+        for r in range(j0 + 1, je):
+            for j in range(je, n):
+                for s in range(j0, r):
+                    A[r][j] = mp_sub(A[r][j], mp_mul(A[r][s], A[s][j], p), p)
+        for i in range(je, n):
+            for j in range(je, n):
+                t = exact(mpmath.libmp.fzero)
+                for s in range(j0, je):
+                    t = mp_add(t, mp_mul(A[i][s], A[s][j], p), p)
+                A[i][j] = mp_sub(A[i][j], t, p)
+    return A, piv
+
+
+@pytest.mark.parametrize("panel", [1, 2, 3, 9])
+def test_replay_blocked_lu(panel):
+    n, p = 9, 128
+    A = gen.uniform_pm1(n, n, p, 81)
+    F, piv, rc = orc.lu(A, panel=panel, algo=orc.SIMPLE)
+    assert rc == 0
+    ref, rpiv = _replay_lu([[entry_mpf(A, i, j) for j in range(n)] for i in range(n)], p, panel)
+    assert list(piv) == rpiv
+    for i in range(n):
+        for j in range(n):
+            assert entry_mpf(F, i, j) == ref[i][j], (i, j)
+
+
+def test_replay_solve():
+    n, p = 8, 128
+    A = gen.uniform_pm1(n, n, p, 82)
+    b = gen.uniform_pm1(n, 1, p, 83)
+    F, piv, rc = orc.lu(A, panel=3)
+    x = orc.lu_solve(F, piv, b)
+    Fm = [[entry_mpf(F, i, j) for j in range(n)] for i in range(n)]
+    v = [entry_mpf(b, i, 0) for i in range(n)]
+    for k, pk in enumerate(piv):
+        v[k], v[pk] = v[pk], v[k]
+    for i in range(n):
+        for j in range(i):
+            v[i] = mp_sub(v[i], mp_mul(Fm[i][j], v[j], p), p)
+    for i in range(n - 1, -1, -1):
+        for j in range(i + 1, n):
+            v[i] = mp_sub(v[i], mp_mul(Fm[i][j], v[j], p), p)
+        v[i] = mp_div(v[i], Fm[i][i], p)
+    assert [entry_mpf(x, i, 0) for i in range(n)] == v
+
+
+# ---------------------------------------------------------------------------
+# correctly rounded exact dot product
+# ---------------------------------------------------------------------------
+def _rn_fraction(q: Fraction, p: int):
+    num = exact(mpmath.libmp.from_int(q.numerator))
+    den = exact(mpmath.libmp.from_int(q.denominator))
+    return mp_div(num, den, p)        # one correctly rounded division of exact integers
+
+
+@pytest.mark.parametrize("p,p_out", [(128, 128), (256, 256), (256, 512), (512, 128)])
+def test_exact_dot_matches_rational(p, p_out):
+    m, l, n = 3, 37, 4
+    A = gen.uniform_pm1(m, l, p, 91, -20, 20)
+    B = gen.uniform_pm1(l, n, p, 92, -20, 20)
+    R = orc.dot_exact(A, B, p_out=p_out)
+    FA, FB = A.to_fractions(), B.to_fractions()
+    for i in range(m):
+        for j in range(n):
+            q = sum(FA[i][k] * FB[k][j] for k in range(l))
+            assert entry_mpf(R, i, j) == _rn_fraction(q, p_out)
+
+
+def test_exact_dot_cancellation_and_single_term():
+    p = 128
+    A = gen.from_ints([[3, -3, 5, -5]], p)
+    B = gen.from_ints([[7], [7], [1], [1]], p)
+    R = orc.dot_exact(A, B)
+    assert R.exp[0, 0] == gen.EXP_ZERO and R.sign[0, 0] == 0
+    A = gen.uniform_pm1(1, 1, p, 93)
+    B = gen.uniform_pm1(1, 1, p, 94)
+    R = orc.dot_exact(A, B)
+    assert entry_mpf(R, 0, 0) == mp_mul(entry_mpf(A, 0, 0), entry_mpf(B, 0, 0), p)
