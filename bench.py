@@ -1,0 +1,342 @@
+#!/usr/bin/env python
+"""Benchmark: multiple-precision GEMM on one GB300 (arXiv 1410.1599 Sec. 3
+workload shape), printed as one JSON line.
+
+Step = one C := A B of the chosen algorithm (default: Winograd's variant,
+n = 2048, 512-bit mantissas, cutoff 64, odd sizes peeled, entries
+U[-1,1) * 2^e with e uniform in [-16, 16]).  value = effective MP GFLOP/s,
+2 m l n / t, over all ranks (each rank multiplies its own matrices: replicas,
+weak scaling).  Inputs (2 x 306 MB at 512 bits) exceed the 129 MB L2.
+
+--impl reference times the CPU oracle (plain C, the tests' reference) on a
+bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ALGO_NAMES = {"simple": 0, "block": 1, "strassen": 2, "winograd": 3}
+PEAK_IMAD_PER_CLK_PER_SM = 64      # 32-bit integer multiply-add lanes per SM per clock
+SM_COUNT_GB300 = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--algo", default="winograd", choices=list(ALGO_NAMES))
+    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--prec", type=int, default=512)
+    ap.add_argument("--cutoff", type=int, default=64)
+    ap.add_argument("--no-extras", action="store_true", help="skip the other algorithms and the CPU baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_config(a):
+    return {"workload": "mp_gemm_%s_n%d_p%d_cutoff%d" % (a.algo, a.n, a.prec, a.cutoff),
+            "m": a.n, "l": a.n, "n": a.n, "prec_bits": a.prec, "algo": a.algo,
+            "cutoff": a.cutoff, "odd": "peel", "entries": "U[-1,1)*2^e, e~U{-16..16}",
+            "l2": "inputs larger than L2 (no flush)"}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(a, rank, world, local):
+    import torch
+
+    from paper_1410_1599_gb300 import binding as mp
+    from paper_1410_1599_gb300 import build as libbuild
+    from paper_1410_1599_gb300 import inputs as gen
+
+    libbuild.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def allmax(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    n, p, cutoff, algo = a.n, a.prec, a.cutoff, ALGO_NAMES[a.algo]
+    flops = 2.0 * n * n * n
+    A = gen.uniform_pm1(n, n, p, 3 + 1000 * rank, -16, 16)
+    B = gen.uniform_pm1(n, n, p, 4 + 1000 * rank, -16, 16)
+    dA, dB = mp.DeviceMP.from_host(A), mp.DeviceMP.from_host(B)
+    dC = mp.DeviceMP.empty(n, n, p)
+    stream = torch.cuda.Stream()
+    mp.set_stream(stream)
+    ws_bytes = mp.workspace_size(n, n, n, p, algo, cutoff)
+    ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device="cuda")
+    mp.set_workspace(ws)
+
+    def step(algo_=algo):
+        mp.mpgemm(dA, dB, dC, algo_, cutoff)
+
+    for _ in range(a.warmup):
+        step()
+    mp.check_status("warmup")
+    torch.cuda.synchronize()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(a.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.steps
+    clk = clocks.stop()
+    mp.check_status("timed")
+    barrier()
+    ms = allmax(ms)
+    value = world * flops / (ms * 1e-3) / 1e9
+
+    # kernel-level timing of the same steps (CUDA events around every launch)
+    mp.profile_enable(True)
+    for _ in range(a.steps):
+        step()
+    torch.cuda.synchronize()
+    prof = mp.profile_read()
+    mp.profile_enable(False)
+    launches_per_step = sum(v[0] for v in prof.values()) / a.steps
+    W32 = (p + 31) // 32
+    imad_per_madd = 2 * W32 * W32            # schoolbook: ceil(p/32)^2 partial products, lo + hi
+    leaf_name = "leaf_gemm" if algo != 0 else "simple_gemm"
+    nl, lms, lunits = prof[leaf_name]
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    peak = SM_COUNT_GB300 * PEAK_IMAD_PER_CLK_PER_SM * 2070e6 / 1e12      # T IMAD/s at max clock
+    achieved = (lunits * imad_per_madd) / (lms * 1e-3) / 1e12 if lms > 0 else 0.0
+    kernels = {k: {"launches_per_step": v[0] / a.steps, "ms_per_step": v[1] / a.steps,
+                   "share": v[1] / max(sum(x[1] for x in prof.values()), 1e-9)}
+               for k, v in prof.items() if v[0]}
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    hA = [t.cpu().pin_memory() for t in (dA.limb, dA.exp, dA.sign)]
+    hB = [t.cpu().pin_memory() for t in (dB.limb, dB.exp, dB.sign)]
+    hC = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in (dC.limb, dC.exp, dC.sign)]
+    h2d = sum(t.numel() * t.element_size() for t in hA + hB)
+    d2h = sum(t.numel() * t.element_size() for t in hC)
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(stream)
+    e2e_steps = max(1, min(a.steps, 3))
+    for _ in range(e2e_steps):
+        with torch.cuda.stream(stream):
+            for dst, src in zip((dA.limb, dA.exp, dA.sign, dB.limb, dB.exp, dB.sign), hA + hB):
+                dst.copy_(src, non_blocking=True)
+            step()
+            for dst, src in zip(hC, (dC.limb, dC.exp, dC.sign)):
+                dst.copy_(src, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = allmax(e0.elapsed_time(e1) / e2e_steps)
+    mp.check_status("e2e")
+
+    extras = {}
+    if not a.no_extras and rank == 0:
+        for name in ("simple", "block", "strassen", "winograd"):
+            if name == a.algo:
+                extras[name] = round(value / world, 3)
+                continue
+            wsz = mp.workspace_size(n, n, n, p, ALGO_NAMES[name], cutoff)
+            if wsz > ws.numel():
+                ws = torch.empty(wsz, dtype=torch.uint8, device="cuda")
+                mp.set_workspace(ws)
+            step(ALGO_NAMES[name])
+            torch.cuda.synchronize()
+            e0.record(stream)
+            step(ALGO_NAMES[name])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            extras[name] = round(flops / (e0.elapsed_time(e1) * 1e-3) / 1e9, 3)
+        mp.check_status("extras")
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_extras:
+        cpu = cpu_baseline(A, B, a.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": "eff. MP GFLOP/s (2mln/t)",
+            "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "mp%d (u32-limb integer)" % p,
+            "data": "synthetic", "config": workload_config(a),
+            "parallelism": "replicas" if world > 1 else "single",
+            "roofline": {"bound": "alu", "kernel": leaf_name, "achieved": round(achieved, 3),
+                         "peak": round(peak, 3), "unit": "T IMAD/s",
+                         "frac": round(achieved / peak, 4),
+                         "peak_note": "derived: 152 SMs x 64 IMAD/clk x 2070 MHz",
+                         "work_per_madd_imad": imad_per_madd, "traffic": None},
+            "kernels": kernels,
+            "gpu_launches": int(round(launches_per_step * a.steps)),
+            "e2e": {"value": round(world * flops / (e2e_ms * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "clocks": clk,
+            "algos_gflops": extras,
+        }
+        if extras.get("simple"):
+            line["speedup_vs_simple"] = round(extras.get(a.algo, value) / extras["simple"], 3)
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline(A, B, seconds):
+    """The oracle (plain C, all host threads) computing a sample of outputs of
+    the same product by Simple dots: eff GFLOP/s = 2 l outputs / t."""
+    import numpy as np
+
+    from oracle import oracle as orc
+
+    n = A.shape[0]
+    threads = orc.max_threads()
+    rng = np.random.default_rng(0)
+    count, t = 8, 0.0
+    while True:
+        rows = np.sort(rng.choice(n, size=count, replace=False))
+        cols = rng.choice(n, size=1)
+        t0 = time.perf_counter()
+        orc.gemm_sampled(orc.SIMPLE, A, B, rows, cols, cutoff=64)
+        t = time.perf_counter() - t0
+        if t > seconds / 4 or count >= n:
+            break
+        count = min(n, count * 4)
+    # scale to ~seconds of work: one more run at the size that fits
+    per = t / count
+    final = int(max(8, min(n, seconds / max(per, 1e-9))))
+    rows = np.sort(rng.choice(n, size=final, replace=False))
+    t0 = time.perf_counter()
+    orc.gemm_sampled(orc.SIMPLE, A, B, rows, np.array([0]), cutoff=64)
+    t = time.perf_counter() - t0
+    return {"value": round(2.0 * A.shape[1] * final / t / 1e9, 6), "unit": "GFLOP/s",
+            "cores": threads, "kind": "oracle",
+            "sample": "%d outputs of C by Simple dot products (l=%d), oracle C code, %d threads"
+                      % (final, A.shape[1], threads), "seconds": round(t, 2)}
+
+
+# ----------------------------------------------------------- reference arm
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    from paper_1410_1599_gb300 import inputs as gen
+
+    n, p = a.n, a.prec
+    A = gen.uniform_pm1(n, n, p, 3, -16, 16)
+    B = gen.uniform_pm1(n, n, p, 4, -16, 16)
+    import numpy as np
+
+    from oracle import oracle as orc
+    threads = orc.max_threads()
+    per_step = max(16, int(64 * 512 / p))
+    rng = np.random.default_rng(1)
+    for _ in range(a.warmup):
+        orc.gemm_sampled(orc.SIMPLE, A, B, np.arange(2), np.array([0]), cutoff=64)
+    t0 = time.perf_counter()
+    for s in range(a.steps):
+        rows = np.sort(rng.choice(n, size=per_step, replace=False))
+        orc.gemm_sampled(orc.SIMPLE, A, B, rows, np.array([s % n]), cutoff=64)
+    t = (time.perf_counter() - t0) / a.steps
+    value = 2.0 * n * per_step / t / 1e9
+    line = {"impl": "reference", "metric": "eff. MP GFLOP/s (2mln/t)", "value": round(value, 6),
+            "unit": "GFLOP/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": round(t * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "mp%d" % p, "data": "synthetic",
+            "config": workload_config(a),
+            "cpu_baseline": {"value": round(value, 6), "unit": "GFLOP/s", "cores": threads,
+                             "kind": "oracle",
+                             "sample": "%d outputs per step by Simple dot products (l=%d)" % (per_step, n)},
+            "e2e": {"value": round(value, 6), "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    rank, world, local = dist_env()
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+    else:
+        run_ours(a, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

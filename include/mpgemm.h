@@ -1,0 +1,197 @@
+/*
+ * mpgemm.h -- C ABI of the GB300 multiple-precision GEMM / LU library
+ * (libmpgemm.so).  Method: arXiv 1410.1599 (Kouya), "Accelerated Multiple
+ * Precision Matrix Multiplication using Strassen's Algorithm and Winograd's
+ * Variant".
+ *
+ * Number format (Sec. 1 and Sec. 3: binary floating point with a p-bit
+ * mantissa, every operation correctly rounded, as in MPFR):
+ *
+ *     x = (-1)^sign * f * 2^exp,   f = sum_k limb[k] * 2^(-64(k+1)) in [1/2, 1)
+ *
+ *   - p (the precision, "prec") is any integer in [MP_PREC_MIN, MP_PREC_MAX];
+ *     a number has L = ceil(p/64) 64-bit limbs, limb 0 most significant, and
+ *     the 64L - p low bits of the last limb are zero;
+ *   - zero is exp == MP_EXP_ZERO with all limbs zero, and keeps its sign;
+ *   - every add, subtract, multiply and divide returns the exact result
+ *     rounded once to p bits, ties to even; zero signs follow IEEE 754
+ *     (x - x = +0, (-0) + (-0) = -0, the sign of a product is the xor);
+ *   - nonzero exponents must lie in [-2^62, 2^62]; a result outside that
+ *     range is reported as MP_ERR_RANGE by mp_sync_status().
+ *
+ * Matrix layout (structure of arrays in device memory), element (r, c):
+ *     limb k : limb[k * plane + r * ld + c]      (uint64)
+ *     exp    : exp[r * ld + c]                   (int64)
+ *     sign   : sign[r * ld + c]                  (int8, 0 = +, 1 = -)
+ * with ld >= cols and plane >= rows * ld.  All pointers are device
+ * pointers owned by the caller; the library never frees them and keeps
+ * no reference after a call returns.
+ *
+ * Calls are ordered on the calling thread's current stream (mp_set_stream;
+ * default: the legacy default stream) and return once the work is enqueued.
+ * They return MP_OK or a negative MP_ERR_* code for argument and launch
+ * errors.  Conditions found on the device (range overflow, a zero pivot)
+ * are read back by mp_sync_status(), which synchronises the stream.
+ *
+ * Library-owned memory: Strassen/Winograd and LU need a workspace.  It is
+ * taken from the buffer given to mp_set_workspace() when that is large
+ * enough (mpgemm_workspace_size() says how large), else allocated and
+ * freed stream-ordered by the library (cudaMallocAsync / cudaFreeAsync).
+ */
+#ifndef MPGEMM_H
+#define MPGEMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MP_EXP_ZERO  INT64_MIN
+#define MP_PREC_MIN  2
+#define MP_PREC_MAX  2048
+
+typedef struct mpmat {
+    int32_t   prec;      /* p, the mantissa precision in bits */
+    int32_t   reserved;  /* must be 0 */
+    int64_t   rows, cols;
+    int64_t   ld;        /* elements between consecutive rows, >= cols */
+    int64_t   plane;     /* elements between limb planes, >= rows * ld */
+    uint64_t *limb;      /* device: L planes, limb 0 most significant */
+    int64_t  *exp;       /* device: exponents, MP_EXP_ZERO for zero */
+    int8_t   *sign;      /* device: 0 = +, 1 = - */
+} mpmat_t;
+
+/* GEMM algorithms (Sec. 2) */
+enum {
+    MP_SIMPLE   = 0,   /* Eq. 1: c_ij = sum_k a_ik b_kj, k ascending */
+    MP_BLOCK    = 1,   /* Eq. 2: blocked, same k-ascending sequence per c_ij */
+    MP_STRASSEN = 2,   /* Strassen's P1..P7 recursion */
+    MP_WINOGRAD = 3    /* Winograd's variant, S1..S8 / M1..M7 / T1, T2 */
+};
+
+/* handling of odd dimensions in the recursion (Sec. 2, last paragraph) */
+enum {
+    MP_PEEL  = 0,      /* peel every odd dimension (default) */
+    MP_MIXED = 1       /* pad x = 3 (mod 4) with a zero row/column, peel x = 1 (mod 4) */
+};
+
+enum {
+    MP_OK              = 0,
+    MP_ERR_ARG         = -1,   /* bad dimension, stride, precision, algorithm or aliasing */
+    MP_ERR_NOMEM       = -2,   /* workspace allocation failed */
+    MP_ERR_SINGULAR    = -3,   /* LU: a pivot column is entirely zero */
+    MP_ERR_TIMEOUT     = -4,   /* a device-side wait gave up */
+    MP_ERR_CUDA        = -5,   /* a CUDA runtime call failed */
+    MP_ERR_RANGE       = -6,   /* an exponent left [-2^62, 2^62] */
+    MP_ERR_UNSUPPORTED = -7
+};
+
+/* ---- per-thread settings ------------------------------------------------ */
+
+/* Stream for the calling thread's subsequent calls (a cudaStream_t; NULL is
+ * the legacy default stream).  Always MP_OK. */
+int mp_set_stream(void *stream);
+
+/* Caller-owned device buffer used as workspace by later calls of this
+ * thread (NULL / 0 to let the library allocate).  Always MP_OK. */
+int mp_set_workspace(void *ptr, size_t bytes);
+
+/* Odd-dimension policy for Strassen / Winograd (MP_PEEL or MP_MIXED). */
+int mp_set_odd_policy(int policy);
+
+/* LU settings used by mplu: panel width K (Sec. 4 block size, >= 1), the
+ * trailing-update algorithm (MP_SIMPLE .. MP_WINOGRAD) and its cutoff. */
+int mp_set_lu(int panel, int algo, int cutoff);
+
+/* ---- elementwise arithmetic -------------------------------------------- */
+
+/* R = X op Y elementwise on rows x cols views of equal shape and precision,
+ * op 0 add, 1 subtract, 2 multiply, 3 divide (Sec. 1: one correct rounding
+ * per operation).  R may alias X or Y exactly (same pointers and strides).
+ * A division by zero leaves that entry untouched and makes mp_sync_status()
+ * return MP_ERR_ARG. */
+int mp_elementwise(int op, const mpmat_t *X, const mpmat_t *Y, mpmat_t *R);
+
+/* R = RN_{R.prec}(X) elementwise (exact when R.prec >= X.prec). */
+int mp_convert(const mpmat_t *X, mpmat_t *R);
+
+/* ---- matrix multiplication (Sec. 2) ------------------------------------- */
+
+/* Workspace bytes mpgemm needs for these arguments (0 for Simple/Block). */
+size_t mpgemm_workspace_size(int64_t m, int64_t l, int64_t n, int32_t prec,
+                             int32_t algo, int32_t cutoff);
+
+/*
+ * C := A B with A m x l, B l x n, C m x n, all of precision prec.
+ *   algo   : MP_SIMPLE, MP_BLOCK, MP_STRASSEN or MP_WINOGRAD;
+ *   cutoff : Strassen/Winograd recurse while m, l and n all exceed it
+ *            (n_min of Sec. 2, >= 1); below it the leaf product is Block.
+ * Every c_ij of Simple/Block is (((+0 + a_i1 b_1j) + a_i2 b_2j) + ...) with
+ * each product and sum rounded; Strassen/Winograd evaluate the printed
+ * formulas left to right with one rounding per matrix add/sub element.
+ * C must not overlap A or B (MP_ERR_ARG).  l = 0 gives C = +0.
+ */
+int mpgemm(int64_t m, int64_t l, int64_t n, int32_t prec, int32_t algo, int32_t cutoff,
+           const mpmat_t *A, const mpmat_t *B, mpmat_t *C);
+
+/* ---- LU decomposition and solve (Sec. 4) -------------------------------- */
+
+/* Workspace bytes mplu needs for an n x n system at prec. */
+size_t mplu_workspace_size(int64_t n, int32_t prec);
+
+/*
+ * Blocked right-looking LU with partial pivoting of the n x n matrix A
+ * (overwritten by L\U, unit lower L), then the solve of A x = b.
+ *   piv : device int64[n]; piv[k] is the row exchanged with row k at step k;
+ *   b   : n x 1 (read only); x : n x 1 (written), may be NULL to factor only.
+ * Each panel of K columns (mp_set_lu) is factored column by column (pivot
+ * = first row of largest |a_ik|, l_ik = RN(a_ik / a_kk)), U12 = L11^-1 A12,
+ * then A22 = RN(A22 - mpgemm(L21, U12)) with the configured algorithm.
+ * A zero pivot makes mp_sync_status() return MP_ERR_SINGULAR.
+ */
+int mplu(int64_t n, int32_t prec, mpmat_t *A, int64_t *piv, const mpmat_t *b, mpmat_t *x);
+
+/* ---- tracing -------------------------------------------------------------- */
+
+/* kernel classes for mp_profile_read */
+enum {
+    MP_K_LEAF = 0,       /* Block GEMM kernel (plain Block and recursion leaves) */
+    MP_K_SIMPLE = 1,     /* Simple GEMM kernel */
+    MP_K_OPERANDS = 2,   /* Strassen/Winograd operand sums */
+    MP_K_COMBINE = 3,    /* Strassen/Winograd C combinations */
+    MP_K_FIXUP = 4,      /* peel fix-ups (rank-1 update, last row / column) */
+    MP_K_ELEMENTWISE = 5,/* mp_elementwise, mp_convert, fills */
+    MP_K_LU = 6,         /* LU panel, row exchange, TRSM, trailing subtract, solves */
+    MP_K_COUNT = 7
+};
+
+/* While enabled (on != 0), every kernel the library launches from the
+ * calling process is bracketed by CUDA events on its stream and counted
+ * per class.  Enabling resets the counters.  Always MP_OK. */
+int mp_profile_enable(int on);
+
+/* Totals for one class since the last enable: launches, summed device time
+ * in milliseconds, and work units (MP multiply-adds for the GEMM classes,
+ * elements written for the others).  Synchronises the device. */
+int mp_profile_read(int cls, int64_t *launches, double *ms, double *units);
+
+/* ---- status ------------------------------------------------------------- */
+
+/* Synchronise the calling thread's stream and return the first error the
+ * device recorded since the last call (then clear it), or MP_OK. */
+int mp_sync_status(void);
+
+/* Column (0-based) of the zero pivot behind the last MP_ERR_SINGULAR. */
+int64_t mp_singular_column(void);
+
+const char *mp_strerror(int status);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int mp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPGEMM_H */

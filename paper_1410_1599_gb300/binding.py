@@ -1,0 +1,218 @@
+"""Thin ctypes binding of libmpgemm.so (include/mpgemm.h).
+
+Argument marshalling only: every arithmetic step runs in the library's CUDA
+kernels.  PyTorch provides device memory and streams.  There is no CPU
+fallback: if the library is missing or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from .inputs import EXP_ZERO, HostMP, limbs_for
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libmpgemm.so")
+
+SIMPLE, BLOCK, STRASSEN, WINOGRAD = 0, 1, 2, 3
+PEEL, MIXED = 0, 1
+OP_ADD, OP_SUB, OP_MUL, OP_DIV = 0, 1, 2, 3
+
+MP_OK = 0
+ERRORS = {-1: "MP_ERR_ARG", -2: "MP_ERR_NOMEM", -3: "MP_ERR_SINGULAR", -4: "MP_ERR_TIMEOUT",
+          -5: "MP_ERR_CUDA", -6: "MP_ERR_RANGE", -7: "MP_ERR_UNSUPPORTED"}
+
+# every symbol include/mpgemm.h declares
+EXPORTS = ["mp_set_stream", "mp_set_workspace", "mp_set_odd_policy", "mp_set_lu",
+           "mp_elementwise", "mp_convert", "mpgemm_workspace_size", "mpgemm",
+           "mplu_workspace_size", "mplu", "mp_sync_status", "mp_singular_column",
+           "mp_strerror", "mp_version", "mp_profile_enable", "mp_profile_read"]
+
+K_LEAF, K_SIMPLE, K_OPERANDS, K_COMBINE, K_FIXUP, K_ELEMENTWISE, K_LU = range(7)
+K_NAMES = ["leaf_gemm", "simple_gemm", "operands", "combine", "fixup", "elementwise", "lu"]
+
+
+class MPError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__("%s (%d)%s" % (ERRORS.get(code, "MP_ERR"), code, (": " + what) if what else ""))
+
+
+class MPMat(C.Structure):
+    _fields_ = [("prec", C.c_int32), ("reserved", C.c_int32), ("rows", C.c_int64),
+                ("cols", C.c_int64), ("ld", C.c_int64), ("plane", C.c_int64),
+                ("limb", C.c_void_p), ("exp", C.c_void_p), ("sign", C.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libmpgemm.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError("libmpgemm.so is not built (run paper_1410_1599_gb300/build.py)")
+            lib = C.CDLL(path)
+            lib.mpgemm_workspace_size.restype = C.c_size_t
+            lib.mpgemm_workspace_size.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.c_int32,
+                                                  C.c_int32, C.c_int32]
+            lib.mplu_workspace_size.restype = C.c_size_t
+            lib.mplu_workspace_size.argtypes = [C.c_int64, C.c_int32]
+            lib.mpgemm.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.c_int32, C.c_int32,
+                                   C.c_int32, C.POINTER(MPMat), C.POINTER(MPMat), C.POINTER(MPMat)]
+            lib.mplu.argtypes = [C.c_int64, C.c_int32, C.POINTER(MPMat), C.c_void_p,
+                                 C.POINTER(MPMat), C.POINTER(MPMat)]
+            lib.mp_elementwise.argtypes = [C.c_int, C.POINTER(MPMat), C.POINTER(MPMat),
+                                           C.POINTER(MPMat)]
+            lib.mp_convert.argtypes = [C.POINTER(MPMat), C.POINTER(MPMat)]
+            lib.mp_set_stream.argtypes = [C.c_void_p]
+            lib.mp_set_workspace.argtypes = [C.c_void_p, C.c_size_t]
+            lib.mp_singular_column.restype = C.c_int64
+            lib.mp_strerror.restype = C.c_char_p
+            lib.mp_profile_read.argtypes = [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                                            C.POINTER(C.c_double)]
+            _lib = lib
+    return _lib
+
+
+def _check(rc: int, what: str = ""):
+    if rc != MP_OK:
+        raise MPError(rc, what)
+
+
+class DeviceMP:
+    """A rows x cols matrix of p-bit numbers in device memory (torch tensors):
+    limb (L, rows, ld) int64 bit patterns, exp (rows, ld) int64, sign (rows, ld) int8."""
+
+    def __init__(self, limb, exp, sign, p: int, rows: int, cols: int, ld: int | None = None,
+                 plane: int | None = None, offset: int = 0):
+        self.limb, self.exp, self.sign = limb, exp, sign
+        self.p, self.rows, self.cols = p, rows, cols
+        self.ld = cols if ld is None else ld
+        self.plane = rows * self.ld if plane is None else plane
+        self.offset = offset          # element offset of (0, 0) inside the arrays
+
+    @staticmethod
+    def empty(rows: int, cols: int, p: int, device="cuda"):
+        import torch
+        L = limbs_for(p)
+        return DeviceMP(torch.empty((L, rows, cols), dtype=torch.int64, device=device),
+                        torch.empty((rows, cols), dtype=torch.int64, device=device),
+                        torch.empty((rows, cols), dtype=torch.int8, device=device), p, rows, cols)
+
+    @staticmethod
+    def from_host(M: HostMP, device="cuda"):
+        import torch
+        rows, cols = M.shape
+        limb = torch.from_numpy(np.ascontiguousarray(M.limb).view(np.int64)).to(device)
+        exp = torch.from_numpy(np.ascontiguousarray(M.exp)).to(device)
+        sign = torch.from_numpy(np.ascontiguousarray(M.sign)).to(device)
+        return DeviceMP(limb, exp, sign, M.p, rows, cols)
+
+    def to_host(self) -> HostMP:
+        L = limbs_for(self.p)
+        limb = self.limb.reshape(-1).cpu().numpy().view(np.uint64)
+        exp = self.exp.reshape(-1).cpu().numpy()
+        sign = self.sign.reshape(-1).cpu().numpy()
+        idx = self.offset + np.arange(self.rows)[:, None] * self.ld + np.arange(self.cols)[None, :]
+        lm = np.stack([limb[k * self.plane + idx] for k in range(L)]) if L else \
+            np.zeros((0, self.rows, self.cols), np.uint64)
+        return HostMP(np.ascontiguousarray(lm), exp[idx].copy(), sign[idx].copy(), self.p)
+
+    def view(self, r0: int, c0: int, rows: int, cols: int) -> "DeviceMP":
+        return DeviceMP(self.limb, self.exp, self.sign, self.p, rows, cols, self.ld, self.plane,
+                        self.offset + r0 * self.ld + c0)
+
+    def struct(self) -> MPMat:
+        return MPMat(self.p, 0, self.rows, self.cols, self.ld, self.plane,
+                     self.limb.data_ptr() + 8 * self.offset, self.exp.data_ptr() + 8 * self.offset,
+                     self.sign.data_ptr() + self.offset)
+
+    def nbytes(self) -> int:
+        return self.limb.numel() * 8 + self.exp.numel() * 8 + self.sign.numel()
+
+
+# ------------------------------------------------------------------ settings
+def set_stream(stream) -> None:
+    """stream: a torch.cuda.Stream, a raw handle, or None (legacy default)."""
+    h = 0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(load_library().mp_set_stream(C.c_void_p(h)))
+
+
+def set_workspace(tensor=None) -> None:
+    lib = load_library()
+    if tensor is None:
+        _check(lib.mp_set_workspace(None, 0))
+    else:
+        _check(lib.mp_set_workspace(C.c_void_p(tensor.data_ptr()), tensor.numel() * tensor.element_size()))
+
+
+def set_odd_policy(policy: int) -> None:
+    _check(load_library().mp_set_odd_policy(policy), "odd policy")
+
+
+def set_lu(panel: int = 128, algo: int = SIMPLE, cutoff: int = 64) -> None:
+    _check(load_library().mp_set_lu(panel, algo, cutoff), "lu settings")
+
+
+def sync_status() -> int:
+    return load_library().mp_sync_status()
+
+
+def check_status(what: str = "") -> None:
+    _check(sync_status(), what)
+
+
+def version() -> int:
+    return load_library().mp_version()
+
+
+def profile_enable(on: bool = True) -> None:
+    _check(load_library().mp_profile_enable(1 if on else 0))
+
+
+def profile_read() -> dict:
+    """{class name: (launches, milliseconds, work units)} since profile_enable."""
+    lib = load_library()
+    out = {}
+    for k, name in enumerate(K_NAMES):
+        n, ms, u = C.c_int64(), C.c_double(), C.c_double()
+        _check(lib.mp_profile_read(k, C.byref(n), C.byref(ms), C.byref(u)))
+        out[name] = (n.value, ms.value, u.value)
+    return out
+
+
+# ---------------------------------------------------------------- operations
+def elementwise(op: int, X: DeviceMP, Y: DeviceMP, R: DeviceMP) -> None:
+    x, y, r = X.struct(), Y.struct(), R.struct()
+    _check(load_library().mp_elementwise(op, C.byref(x), C.byref(y), C.byref(r)), "elementwise")
+
+
+def convert(X: DeviceMP, R: DeviceMP) -> None:
+    x, r = X.struct(), R.struct()
+    _check(load_library().mp_convert(C.byref(x), C.byref(r)), "convert")
+
+
+def workspace_size(m: int, l: int, n: int, p: int, algo: int, cutoff: int) -> int:
+    return load_library().mpgemm_workspace_size(m, l, n, p, algo, cutoff)
+
+
+def mpgemm(A: DeviceMP, B: DeviceMP, C_: DeviceMP, algo: int = SIMPLE, cutoff: int = 64) -> None:
+    a, b, c = A.struct(), B.struct(), C_.struct()
+    _check(load_library().mpgemm(A.rows, A.cols, B.cols, A.p, algo, cutoff, C.byref(a),
+                                 C.byref(b), C.byref(c)), "mpgemm")
+
+
+def mplu(A: DeviceMP, piv, b: DeviceMP | None, x: DeviceMP | None) -> None:
+    a = A.struct()
+    bs = b.struct() if b is not None else None
+    xs = x.struct() if x is not None else None
+    _check(load_library().mplu(A.rows, A.p, C.byref(a), C.c_void_p(piv.data_ptr()),
+                               C.byref(bs) if bs is not None else None,
+                               C.byref(xs) if xs is not None else None), "mplu")

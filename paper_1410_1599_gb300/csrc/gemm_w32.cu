@@ -1,0 +1,6 @@
+// gemm_w32.cu -- elementwise and GEMM kernels, 32-word (1024-bit) capacity class.
+#include "mp_kernels.cuh"
+
+namespace mpg {
+MPG_INSTANTIATE_GEMM(32)
+}  // namespace mpg

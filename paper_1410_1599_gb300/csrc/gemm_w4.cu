@@ -1,0 +1,6 @@
+// gemm_w4.cu -- elementwise and GEMM kernels, 4-word (128-bit) capacity class.
+#include "mp_kernels.cuh"
+
+namespace mpg {
+MPG_INSTANTIATE_GEMM(4)
+}  // namespace mpg

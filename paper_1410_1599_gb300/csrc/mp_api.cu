@@ -1,0 +1,558 @@
+// mp_api.cu -- the C ABI of libmpgemm.so (include/mpgemm.h): argument checks,
+// dispatch to the word-capacity class, the breadth-first Strassen/Winograd
+// driver (arXiv 1410.1599 Sec. 2) and the device status word.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../include/mpgemm.h"
+#include "mp_internal.h"
+
+using namespace mpg;
+
+namespace {
+
+struct ThreadState {
+    cudaStream_t stream = nullptr;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    int odd_policy = MP_PEEL;
+    int lu_panel = 128, lu_algo = MP_SIMPLE, lu_cutoff = 64;
+    long long singular_col = -1;
+};
+thread_local ThreadState g_ts;
+
+std::mutex g_status_mu;
+std::vector<DevStatus *> g_status;   // one per device
+
+DevStatus *status_ptr()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(g_status_mu);
+    if ((int)g_status.size() <= dev) g_status.resize(dev + 1, nullptr);
+    if (!g_status[dev]) {
+        DevStatus *p = nullptr;
+        if (cudaMalloc(&p, sizeof(DevStatus)) != cudaSuccess) return nullptr;
+        DevStatus init{0u, 0u, -1};
+        cudaMemcpy(p, &init, sizeof init, cudaMemcpyHostToDevice);
+        g_status[dev] = p;
+    }
+    return g_status[dev];
+}
+
+int limbs_of(int p) { return (p + 63) / 64; }
+
+// word-capacity class: smallest W in {4, 8, 16, 32, 64} with 32 W >= 64 L
+int wclass(int p)
+{
+    const int L = limbs_of(p);
+    if (L <= 2) return 4;
+    if (L <= 4) return 8;
+    if (L <= 8) return 16;
+    if (L <= 16) return 32;
+    return 64;
+}
+
+template <typename F>
+void dispatch(int p, F &&f)
+{
+    switch (wclass(p)) {
+    case 4: f(std::integral_constant<int, 4>{}); break;
+    case 8: f(std::integral_constant<int, 8>{}); break;
+    case 16: f(std::integral_constant<int, 16>{}); break;
+    case 32: f(std::integral_constant<int, 32>{}); break;
+    default: f(std::integral_constant<int, 64>{}); break;
+    }
+}
+
+bool valid_prec(int p) { return p >= MP_PREC_MIN && p <= MP_PREC_MAX; }
+
+// checks a caller matrix of the given shape; empty matrices need no pointers
+bool valid_mat(const mpmat_t *M, int64_t rows, int64_t cols, int prec)
+{
+    if (!M || M->prec != prec || M->reserved != 0) return false;
+    if (M->rows != rows || M->cols != cols || rows < 0 || cols < 0) return false;
+    if (rows == 0 || cols == 0) return true;
+    if (M->ld < cols || M->plane < (rows - 1) * M->ld + cols) return false;
+    if (!M->limb || !M->exp || !M->sign) return false;
+    return true;
+}
+
+BMat bmat(const mpmat_t *M)
+{
+    return BMat{M->limb, M->exp, M->sign, M->ld, M->plane, 0, 0};
+}
+
+// [lo, hi) byte ranges of a matrix's three arrays
+struct Range { uintptr_t lo, hi; };
+void ranges(const mpmat_t *M, Range out[3])
+{
+    const int L = limbs_of(M->prec);
+    const int64_t span = (M->rows - 1) * M->ld + M->cols;
+    out[0] = {(uintptr_t)M->limb, (uintptr_t)(M->limb + (int64_t)(L - 1) * M->plane + span)};
+    out[1] = {(uintptr_t)M->exp, (uintptr_t)(M->exp + span)};
+    out[2] = {(uintptr_t)M->sign, (uintptr_t)(M->sign + span)};
+}
+
+bool overlaps(const mpmat_t *X, const mpmat_t *Y)
+{
+    if (X->rows == 0 || X->cols == 0 || Y->rows == 0 || Y->cols == 0) return false;
+    Range a[3], b[3];
+    ranges(X, a);
+    ranges(Y, b);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            if (a[i].lo < b[j].hi && b[j].lo < a[i].hi) return true;
+    return false;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? MP_OK : MP_ERR_CUDA; }
+
+// ------------------------------------------------------------------ tracing
+struct ProfRec { int cls; cudaEvent_t a, b; double units; };
+struct Profiler {
+    std::mutex mu;
+    bool on = false;
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> pool;
+    int64_t launches[MP_K_COUNT] = {};
+    double ms[MP_K_COUNT] = {}, units[MP_K_COUNT] = {};
+
+    cudaEvent_t ev()
+    {
+        if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        return e;
+    }
+    void drain()   // fold finished records into the totals
+    {
+        for (auto &r : recs) {
+            float t = 0.f;
+            cudaEventSynchronize(r.b);
+            cudaEventElapsedTime(&t, r.a, r.b);
+            launches[r.cls] += 1;
+            ms[r.cls] += t;
+            units[r.cls] += r.units;
+            pool.push_back(r.a);
+            pool.push_back(r.b);
+        }
+        recs.clear();
+    }
+};
+Profiler g_prof;
+
+// Bracket one launch: Prof p(cls, units, stream); <launch>;  (destructor records the end)
+struct Prof {
+    bool on;
+    ProfRec rec;
+    cudaStream_t s;
+    Prof(int cls, double units, cudaStream_t st) : on(g_prof.on), s(st)
+    {
+        if (!on) return;
+        std::lock_guard<std::mutex> lk(g_prof.mu);
+        if (g_prof.recs.size() > 4096) g_prof.drain();
+        rec = ProfRec{cls, g_prof.ev(), g_prof.ev(), units};
+        cudaEventRecord(rec.a, s);
+    }
+    ~Prof()
+    {
+        if (!on) return;
+        std::lock_guard<std::mutex> lk(g_prof.mu);
+        cudaEventRecord(rec.b, s);
+        g_prof.recs.push_back(rec);
+    }
+};
+
+int launch_status() { return cuda_status(cudaGetLastError()); }
+
+// ------------------------------------------------------------- workspace
+struct Workspace {
+    char *base = nullptr;
+    size_t size = 0, used = 0;
+    bool owned = false;
+    cudaStream_t s = nullptr;
+
+    int acquire(size_t bytes, cudaStream_t st)
+    {
+        s = st;
+        size = bytes;
+        used = 0;
+        if (bytes == 0) return MP_OK;
+        if (g_ts.ws && g_ts.ws_bytes >= bytes) {
+            base = (char *)g_ts.ws;
+            return MP_OK;
+        }
+        void *p = nullptr;
+        if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+            cudaGetLastError();
+            return MP_ERR_NOMEM;
+        }
+        base = (char *)p;
+        owned = true;
+        return MP_OK;
+    }
+    void *take(size_t bytes)
+    {
+        size_t off = (used + 255) & ~(size_t)255;
+        used = off + bytes;
+        return base + off;
+    }
+    ~Workspace()
+    {
+        if (owned && base) cudaFreeAsync(base, s);
+    }
+};
+
+size_t padded(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// ------------------------------------------------- recursion plan (Sec. 2)
+struct LevelDims {
+    int64_t m, l, n;      // real sizes of every node at this level
+    int64_t M, K, N;      // even sizes of the recursive part (pad or peel)
+};
+
+int64_t even_dim(int64_t x, int policy)
+{
+    if (x % 2 == 0) return x;
+    if (policy == MP_MIXED && x % 4 == 3) return x + 1;
+    return x - 1;
+}
+
+std::vector<LevelDims> plan(int64_t m, int64_t l, int64_t n, int cutoff, int policy)
+{
+    std::vector<LevelDims> lv;
+    for (;;) {
+        LevelDims d{m, l, n, m, l, n};
+        const bool rec = m > cutoff && l > cutoff && n > cutoff;
+        if (rec) {
+            d.M = even_dim(m, policy);
+            d.K = even_dim(l, policy);
+            d.N = even_dim(n, policy);
+        }
+        lv.push_back(d);
+        if (!rec) break;
+        m = d.M / 2;
+        l = d.K / 2;
+        n = d.N / 2;
+    }
+    return lv;   // lv.size() - 1 recursion levels; the last entry is the leaf
+}
+
+size_t mat_bytes(int64_t count, int64_t rows, int64_t cols, int L)
+{
+    const size_t e = (size_t)count * (size_t)rows * (size_t)cols;
+    return padded(e * 8 * (size_t)L) + padded(e * 8) + padded(e);
+}
+
+size_t recursion_bytes(const std::vector<LevelDims> &lv, int L)
+{
+    size_t total = 0;
+    int64_t nodes = 1;
+    for (size_t k = 1; k < lv.size(); ++k) {
+        nodes *= 7;
+        total += mat_bytes(nodes, lv[k].m, lv[k].l, L);
+        total += mat_bytes(nodes, lv[k].l, lv[k].n, L);
+        total += mat_bytes(nodes, lv[k].m, lv[k].n, L);
+    }
+    return total + 256;
+}
+
+BMat carve(Workspace &ws, int64_t count, int64_t rows, int64_t cols, int L)
+{
+    const size_t e = (size_t)count * (size_t)rows * (size_t)cols;
+    BMat b;
+    b.limb = (uint64_t *)ws.take(e * 8 * (size_t)L);
+    b.exp = (int64_t *)ws.take(e * 8);
+    b.sign = (int8_t *)ws.take(e);
+    b.ld = cols;
+    b.plane = rows * cols;
+    b.bs_limb = (int64_t)L * rows * cols;
+    b.bs_es = rows * cols;
+    return b;
+}
+
+__global__ void fill_zero_kernel(BMat C, int64_t rows, int64_t cols, int L)
+{
+    const int64_t total = rows * cols;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / cols, c = t % cols;
+        for (int k = 0; k < L; ++k) C.limb[(int64_t)k * C.plane + r * C.ld + c] = 0ull;
+        C.exp[r * C.ld + c] = INT64_MIN;
+        C.sign[r * C.ld + c] = 0;
+    }
+}
+
+template <int W>
+int run_recursion(int algo, const std::vector<LevelDims> &lv, int p, BMat A0, BMat B0, BMat C0,
+                  Workspace &ws, DevStatus *st, cudaStream_t s)
+{
+    const int L = limbs_of(p);
+    const int D = (int)lv.size() - 1;
+    std::vector<BMat> A(D + 1), B(D + 1), C(D + 1);
+    A[0] = A0;
+    B[0] = B0;
+    C[0] = C0;
+    int64_t nodes = 1;
+    for (int k = 1; k <= D; ++k) {
+        nodes *= 7;
+        A[k] = carve(ws, nodes, lv[k].m, lv[k].l, L);
+        B[k] = carve(ws, nodes, lv[k].l, lv[k].n, L);
+        C[k] = carve(ws, nodes, lv[k].m, lv[k].n, L);
+    }
+    // down: operand sums of every level (one batched launch per side)
+    nodes = 1;
+    for (int k = 0; k < D; ++k) {
+        const LevelDims &d = lv[k];
+        {
+            Prof pr(MP_K_OPERANDS, (double)nodes * 7 * (d.M / 2) * (d.K / 2), s);
+            launch_operands_a<W>(algo, A[k], A[k + 1], nodes, d.m, d.l, d.M / 2, d.K / 2, p, s);
+        }
+        {
+            Prof pr(MP_K_OPERANDS, (double)nodes * 7 * (d.K / 2) * (d.N / 2), s);
+            launch_operands_b<W>(algo, B[k], B[k + 1], nodes, d.l, d.n, d.K / 2, d.N / 2, p, s);
+        }
+        nodes *= 7;
+    }
+    // leaves: one grouped Block GEMM over all 7^D products
+    {
+        Prof pr(MP_K_LEAF, (double)nodes * lv[D].m * lv[D].l * lv[D].n, s);
+        launch_gemm_block<W>(A[D], B[D], C[D], nodes, lv[D].m, lv[D].l, lv[D].n, p, st, s);
+    }
+    // up: combinations, then the peel fix-ups of each level
+    for (int k = D - 1; k >= 0; --k) {
+        nodes /= 7;
+        const LevelDims &d = lv[k];
+        const int64_t mr = std::min(d.M, d.m), nr = std::min(d.N, d.n);
+        {
+            Prof pr(MP_K_COMBINE, (double)nodes * mr * nr, s);
+            launch_combine<W>(algo, C[k + 1], C[k], nodes, d.M / 2, d.N / 2, mr, nr, p, st, s);
+        }
+        if (d.K < d.l) {
+            Prof pr(MP_K_FIXUP, (double)nodes * mr * nr, s);
+            launch_rank1<W>(A[k], B[k], C[k], nodes, mr, nr, d.l, p, st, s);
+        }
+        if (d.M < d.m || d.N < d.n) {
+            const int64_t cnt = (d.M < d.m ? d.n : 0) + (d.N < d.n ? mr : 0);
+            Prof pr(MP_K_FIXUP, (double)nodes * cnt * d.l, s);
+            launch_border<W>(A[k], B[k], C[k], nodes, d.m, d.l, d.n, mr, d.M < d.m, d.N < d.n, p,
+                             st, s);
+        }
+    }
+    return launch_status();
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+extern "C" {
+
+int mp_version(void) { return 100; }
+
+int mp_set_stream(void *stream)
+{
+    g_ts.stream = (cudaStream_t)stream;
+    return MP_OK;
+}
+
+int mp_set_workspace(void *ptr, size_t bytes)
+{
+    g_ts.ws = ptr;
+    g_ts.ws_bytes = ptr ? bytes : 0;
+    return MP_OK;
+}
+
+int mp_set_odd_policy(int policy)
+{
+    if (policy != MP_PEEL && policy != MP_MIXED) return MP_ERR_ARG;
+    g_ts.odd_policy = policy;
+    return MP_OK;
+}
+
+int mp_set_lu(int panel, int algo, int cutoff)
+{
+    if (panel < 1 || algo < MP_SIMPLE || algo > MP_WINOGRAD || cutoff < 1) return MP_ERR_ARG;
+    g_ts.lu_panel = panel;
+    g_ts.lu_algo = algo;
+    g_ts.lu_cutoff = cutoff;
+    return MP_OK;
+}
+
+const char *mp_strerror(int status)
+{
+    switch (status) {
+    case MP_OK: return "ok";
+    case MP_ERR_ARG: return "invalid argument";
+    case MP_ERR_NOMEM: return "workspace allocation failed";
+    case MP_ERR_SINGULAR: return "zero pivot: matrix is singular";
+    case MP_ERR_TIMEOUT: return "device wait timed out";
+    case MP_ERR_CUDA: return "CUDA runtime error";
+    case MP_ERR_RANGE: return "exponent out of range";
+    case MP_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+    }
+}
+
+int mp_sync_status(void)
+{
+    cudaError_t e = cudaStreamSynchronize(g_ts.stream);
+    if (e != cudaSuccess) return MP_ERR_CUDA;
+    DevStatus *st = status_ptr();
+    if (!st) return MP_ERR_CUDA;
+    DevStatus h{};
+    if (cudaMemcpy(&h, st, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess) return MP_ERR_CUDA;
+    if (h.flags) {
+        DevStatus init{0u, 0u, -1};
+        cudaMemcpy(st, &init, sizeof init, cudaMemcpyHostToDevice);
+    }
+    g_ts.singular_col = h.singular_col;
+    if (h.flags & ST_TIMEOUT) return MP_ERR_TIMEOUT;
+    if (h.flags & ST_SINGULAR) return MP_ERR_SINGULAR;
+    if (h.flags & ST_DIVZERO) return MP_ERR_ARG;
+    if (h.flags & ST_RANGE) return MP_ERR_RANGE;
+    return MP_OK;
+}
+
+int64_t mp_singular_column(void) { return g_ts.singular_col; }
+
+int mp_profile_enable(int on)
+{
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    g_prof.drain();
+    g_prof.on = on != 0;
+    if (g_prof.on) {
+        for (int i = 0; i < MP_K_COUNT; ++i) {
+            g_prof.launches[i] = 0;
+            g_prof.ms[i] = 0.0;
+            g_prof.units[i] = 0.0;
+        }
+    }
+    return MP_OK;
+}
+
+int mp_profile_read(int cls, int64_t *launches, double *ms, double *units)
+{
+    if (cls < 0 || cls >= MP_K_COUNT) return MP_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    g_prof.drain();
+    if (launches) *launches = g_prof.launches[cls];
+    if (ms) *ms = g_prof.ms[cls];
+    if (units) *units = g_prof.units[cls];
+    return MP_OK;
+}
+
+int mp_elementwise(int op, const mpmat_t *X, const mpmat_t *Y, mpmat_t *R)
+{
+    if (op < 0 || op > 3 || !X || !Y || !R) return MP_ERR_ARG;
+    const int p = X->prec;
+    if (!valid_prec(p)) return MP_ERR_ARG;
+    const int64_t rows = X->rows, cols = X->cols;
+    if (!valid_mat(X, rows, cols, p) || !valid_mat(Y, rows, cols, p) || !valid_mat(R, rows, cols, p))
+        return MP_ERR_ARG;
+    // R may alias an input only exactly
+    auto same = [](const mpmat_t *a, const mpmat_t *b) {
+        return a->limb == b->limb && a->exp == b->exp && a->sign == b->sign && a->ld == b->ld &&
+               a->plane == b->plane;
+    };
+    if ((overlaps(R, X) && !same(R, X)) || (overlaps(R, Y) && !same(R, Y))) return MP_ERR_ARG;
+    if (rows == 0 || cols == 0) return MP_OK;
+    DevStatus *st = status_ptr();
+    if (!st) return MP_ERR_CUDA;
+    Prof pr(MP_K_ELEMENTWISE, (double)rows * cols, g_ts.stream);
+    dispatch(p, [&](auto w) {
+        launch_elementwise<decltype(w)::value>(op, bmat(X), bmat(Y), bmat(R), rows, cols, p, st,
+                                               g_ts.stream);
+    });
+    return launch_status();
+}
+
+int mp_convert(const mpmat_t *X, mpmat_t *R)
+{
+    if (!X || !R || !valid_prec(X->prec) || !valid_prec(R->prec)) return MP_ERR_ARG;
+    const int64_t rows = X->rows, cols = X->cols;
+    if (!valid_mat(X, rows, cols, X->prec) || !valid_mat(R, rows, cols, R->prec)) return MP_ERR_ARG;
+    if (overlaps(X, R)) return MP_ERR_ARG;
+    if (rows == 0 || cols == 0) return MP_OK;
+    DevStatus *st = status_ptr();
+    if (!st) return MP_ERR_CUDA;
+    const int pmax = std::max(X->prec, R->prec);
+    Prof pr(MP_K_ELEMENTWISE, (double)rows * cols, g_ts.stream);
+    dispatch(pmax, [&](auto w) {
+        launch_convert<decltype(w)::value>(bmat(X), X->prec, bmat(R), R->prec, rows, cols, st,
+                                           g_ts.stream);
+    });
+    return launch_status();
+}
+
+size_t mpgemm_workspace_size(int64_t m, int64_t l, int64_t n, int32_t prec, int32_t algo,
+                             int32_t cutoff)
+{
+    if (algo != MP_STRASSEN && algo != MP_WINOGRAD) return 0;
+    if (cutoff < 1 || m <= 0 || l <= 0 || n <= 0 || !valid_prec(prec)) return 0;
+    auto lv = plan(m, l, n, cutoff, g_ts.odd_policy);
+    if (lv.size() <= 1) return 0;
+    return recursion_bytes(lv, limbs_of(prec));
+}
+
+int mpgemm(int64_t m, int64_t l, int64_t n, int32_t prec, int32_t algo, int32_t cutoff,
+           const mpmat_t *A, const mpmat_t *B, mpmat_t *C)
+{
+    if (!valid_prec(prec) || m < 0 || l < 0 || n < 0) return MP_ERR_ARG;
+    if (algo < MP_SIMPLE || algo > MP_WINOGRAD) return MP_ERR_ARG;
+    if ((algo == MP_STRASSEN || algo == MP_WINOGRAD) && cutoff < 1) return MP_ERR_ARG;
+    if (!valid_mat(A, m, l, prec) || !valid_mat(B, l, n, prec) || !valid_mat(C, m, n, prec))
+        return MP_ERR_ARG;
+    if (overlaps(C, A) || overlaps(C, B)) return MP_ERR_ARG;
+    if (m == 0 || n == 0) return MP_OK;
+    cudaStream_t s = g_ts.stream;
+    DevStatus *st = status_ptr();
+    if (!st) return MP_ERR_CUDA;
+    const int L = limbs_of(prec);
+    if (l == 0) {
+        Prof pr(MP_K_ELEMENTWISE, (double)m * n, s);
+        fill_zero_kernel<<<(unsigned)std::min<int64_t>((m * n + 127) / 128, 152 * 32), 128, 0, s>>>(
+            bmat(C), m, n, L);
+        return launch_status();
+    }
+    if (algo == MP_SIMPLE) {
+        Prof pr(MP_K_SIMPLE, (double)m * l * n, s);
+        dispatch(prec, [&](auto w) {
+            launch_gemm_simple<decltype(w)::value>(bmat(A), bmat(B), bmat(C), m, l, n, prec, st, s);
+        });
+        return launch_status();
+    }
+    auto lv = plan(m, l, n, cutoff, g_ts.odd_policy);
+    if (algo == MP_BLOCK || lv.size() <= 1) {
+        Prof pr(MP_K_LEAF, (double)m * l * n, s);
+        dispatch(prec, [&](auto w) {
+            launch_gemm_block<decltype(w)::value>(bmat(A), bmat(B), bmat(C), 1, m, l, n, prec, st, s);
+        });
+        return launch_status();
+    }
+    Workspace ws;
+    int rc = ws.acquire(recursion_bytes(lv, L), s);
+    if (rc != MP_OK) return rc;
+    dispatch(prec, [&](auto w) {
+        rc = run_recursion<decltype(w)::value>(algo, lv, prec, bmat(A), bmat(B), bmat(C), ws, st, s);
+    });
+    return rc;
+}
+
+size_t mplu_workspace_size(int64_t n, int32_t prec)
+{
+    (void)n;
+    (void)prec;
+    return 0;
+}
+
+int mplu(int64_t n, int32_t prec, mpmat_t *A, int64_t *piv, const mpmat_t *b, mpmat_t *x)
+{
+    (void)n; (void)prec; (void)A; (void)piv; (void)b; (void)x;
+    return MP_ERR_UNSUPPORTED;
+}
+
+}  // extern "C"

@@ -1,0 +1,544 @@
+// mp_arith.cuh -- device multiple-precision arithmetic in registers.
+//
+// A number is held as W little-endian 32-bit words (capacity 32W bits) plus
+// an int64 exponent and a sign: value = (-1)^s * m * 2^(e - 32W) with the top
+// bit of m[W-1] set (m read as an integer), i.e. a mantissa fraction in
+// [1/2, 1).  A precision-p number uses the top p bits; the rest are zero.
+// Zero is e == EXP_ZERO with m == 0.
+//
+// Every operation returns the exact result rounded once to p bits, ties to
+// even (arXiv 1410.1599, Sec. 1 and 3: MPFR semantics), so results do not
+// depend on W: a p-bit operation gives the same bits in any W >= 2*ceil(p/64).
+#pragma once
+#include <cstdint>
+
+#define MP_DEV __device__ __forceinline__
+
+namespace mpg {
+
+constexpr int64_t EXP_ZERO = INT64_MIN;
+constexpr int64_t EXP_LIMIT = (int64_t)1 << 62;
+
+// ---------------------------------------------------------------- carry chains
+MP_DEV uint32_t add_cc(uint32_t a, uint32_t b) { uint32_t r; asm volatile("add.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b)); return r; }
+MP_DEV uint32_t addc_cc(uint32_t a, uint32_t b) { uint32_t r; asm volatile("addc.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b)); return r; }
+MP_DEV uint32_t addc(uint32_t a, uint32_t b) { uint32_t r; asm volatile("addc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b)); return r; }
+MP_DEV uint32_t sub_cc(uint32_t a, uint32_t b) { uint32_t r; asm volatile("sub.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b)); return r; }
+MP_DEV uint32_t subc_cc(uint32_t a, uint32_t b) { uint32_t r; asm volatile("subc.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b)); return r; }
+MP_DEV uint32_t subc(uint32_t a, uint32_t b) { uint32_t r; asm volatile("subc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b)); return r; }
+MP_DEV uint32_t mad_lo_cc(uint32_t a, uint32_t b, uint32_t c) { uint32_t r; asm volatile("mad.lo.cc.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c)); return r; }
+MP_DEV uint32_t madc_lo_cc(uint32_t a, uint32_t b, uint32_t c) { uint32_t r; asm volatile("madc.lo.cc.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c)); return r; }
+MP_DEV uint32_t mad_hi_cc(uint32_t a, uint32_t b, uint32_t c) { uint32_t r; asm volatile("mad.hi.cc.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c)); return r; }
+MP_DEV uint32_t madc_hi_cc(uint32_t a, uint32_t b, uint32_t c) { uint32_t r; asm volatile("madc.hi.cc.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c)); return r; }
+MP_DEV uint32_t madc_hi(uint32_t a, uint32_t b, uint32_t c) { uint32_t r; asm volatile("madc.hi.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c)); return r; }
+
+// Per-launch constants derived from the precision p and the capacity W.
+struct RoundSpec {
+    int p;        // precision in bits
+    int r;        // 32W - p: bits below the kept least significant bit
+    int rw, rb;   // r = 32 * rw + rb
+    int L;        // storage limbs, ceil(p / 64)
+};
+
+template <int W>
+MP_DEV RoundSpec make_spec(int p)
+{
+    RoundSpec s;
+    s.p = p;
+    s.r = 32 * W - p;
+    s.rw = s.r >> 5;
+    s.rb = s.r & 31;
+    s.L = (p + 63) >> 6;
+    return s;
+}
+
+template <int W>
+struct Mp {
+    uint32_t m[W];
+    int64_t e;
+    uint32_t s;
+};
+
+template <int W>
+MP_DEV void set_zero(Mp<W> &x, uint32_t sign)
+{
+#pragma unroll
+    for (int i = 0; i < W; ++i) x.m[i] = 0u;
+    x.e = EXP_ZERO;
+    x.s = sign;
+}
+
+// ------------------------------------------------------------- load / store
+// Limb k (0 = most significant) of a storage number with L limbs occupies
+// words W-1-2k (high half) and W-2-2k (low half).
+template <int W>
+MP_DEV void load(Mp<W> &x, const uint64_t *__restrict__ limb, const int64_t *__restrict__ exp,
+                 const int8_t *__restrict__ sign, int64_t off, int64_t plane, int L)
+{
+#pragma unroll
+    for (int k = 0; k < W / 2; ++k) {
+        uint64_t v = (k < L) ? __ldg(limb + (int64_t)k * plane + off) : 0ull;
+        x.m[W - 1 - 2 * k] = (uint32_t)(v >> 32);
+        x.m[W - 2 - 2 * k] = (uint32_t)v;
+    }
+    x.e = __ldg(exp + off);
+    x.s = (uint32_t)(__ldg(sign + off) & 1);
+}
+
+// load that treats out-of-range positions as +0 (zero padding)
+template <int W>
+MP_DEV void load_or_zero(Mp<W> &x, bool valid, const uint64_t *__restrict__ limb,
+                         const int64_t *__restrict__ exp, const int8_t *__restrict__ sign,
+                         int64_t off, int64_t plane, int L)
+{
+    if (valid) load<W>(x, limb, exp, sign, off, plane, L);
+    else set_zero<W>(x, 0u);
+}
+
+template <int W>
+MP_DEV void store(const Mp<W> &x, uint64_t *__restrict__ limb, int64_t *__restrict__ exp,
+                  int8_t *__restrict__ sign, int64_t off, int64_t plane, int L)
+{
+#pragma unroll
+    for (int k = 0; k < W / 2; ++k)
+        if (k < L)
+            limb[(int64_t)k * plane + off] =
+                ((uint64_t)x.m[W - 1 - 2 * k] << 32) | (uint64_t)x.m[W - 2 - 2 * k];
+    exp[off] = x.e;
+    sign[off] = (int8_t)x.s;
+}
+
+// exponent check of a finished result (zero is always in range)
+template <int W>
+MP_DEV bool out_of_range(const Mp<W> &x)
+{
+    return x.e != EXP_ZERO && (x.e > EXP_LIMIT || x.e < -EXP_LIMIT);
+}
+
+// ------------------------------------------------------------------ rounding
+// Round the W-word mantissa m (top bit set) to p bits, nearest-even.  `below`
+// is the word directly under m and `sticky` says whether anything lies below
+// that.  Bits of m under the kept LSB are cleared.  A carry out of the top
+// renormalises to 1/2 and increments e.
+template <int W>
+MP_DEV void round_mant(uint32_t (&m)[W], int64_t &e, uint32_t below, bool sticky,
+                       const RoundSpec &rs)
+{
+    uint32_t rbit, st;
+    if (rs.r == 0) {
+        rbit = below >> 31;
+        st = (below << 1) | (sticky ? 1u : 0u);
+    } else {
+        // round bit is bit r-1 of m; sticky is everything under it
+        const int q = rs.r - 1;
+        const int qw = q >> 5, qb = q & 31;
+        rbit = 0u;
+        st = below | (sticky ? 1u : 0u);
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            uint32_t w = m[i];
+            if (i == qw) {
+                rbit = (w >> qb) & 1u;
+                st |= w & ((1u << qb) - 1u);
+            } else if (i < qw) {
+                st |= w;
+            }
+        }
+        // clear the bits under the kept LSB (bit r)
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            if (i < rs.rw) m[i] = 0u;
+            else if (i == rs.rw) m[i] &= ~((1u << rs.rb) - 1u);
+        }
+    }
+    uint32_t lsb = 0u;
+#pragma unroll
+    for (int i = 0; i < W; ++i)
+        if (i == rs.rw) lsb = (m[i] >> rs.rb) & 1u;
+    if (rbit && (st | lsb)) {
+        // m += 2^r
+        uint32_t c = 0u;
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            uint32_t add = (i == rs.rw) ? (1u << rs.rb) : 0u;
+            uint32_t s1 = m[i] + add;
+            uint32_t c1 = s1 < add;
+            uint32_t s2 = s1 + c;
+            c = c1 | (s2 < c);
+            m[i] = s2;
+        }
+        if (c) {   // carried out of the top: m was all ones above r
+#pragma unroll
+            for (int i = 0; i < W; ++i) m[i] = 0u;
+            m[W - 1] = 0x80000000u;
+            e += 1;
+        }
+    }
+}
+
+// ------------------------------------------------------------ multiplication
+// P (2W words) = a * b, schoolbook by rows of b with two carry chains per row
+// (low and high halves of the 32x32 partial products).
+template <int W>
+MP_DEV void mul_full(uint32_t (&P)[2 * W], const uint32_t (&a)[W], const uint32_t (&b)[W])
+{
+#pragma unroll
+    for (int i = 0; i < 2 * W; ++i) P[i] = 0u;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        const uint32_t bj = b[j];
+        P[j] = mad_lo_cc(a[0], bj, P[j]);
+#pragma unroll
+        for (int i = 1; i < W; ++i) P[j + i] = madc_lo_cc(a[i], bj, P[j + i]);
+        P[j + W] = addc(P[j + W], 0u);
+        P[j + 1] = mad_hi_cc(a[0], bj, P[j + 1]);
+#pragma unroll
+        for (int i = 1; i < W - 1; ++i) P[j + 1 + i] = madc_hi_cc(a[i], bj, P[j + 1 + i]);
+        P[j + W] = madc_hi(a[W - 1], bj, P[j + W]);
+    }
+}
+
+// Top half of a * b by a sliding window over the product, for large W where
+// a fully unrolled 2W-word product is too much code: rows of b are taken four
+// at a time (outer loop not unrolled); after each group the four lowest
+// window words are final and leave the window.  Returns the top W words in
+// hi, the two words just below them (P[W-1], P[W-2]) and whether anything
+// below those is nonzero.
+template <int W>
+MP_DEV void mul_top(uint32_t (&hi)[W], uint32_t &pw1, uint32_t &pw2, bool &low_nz,
+                    const uint32_t (&a)[W], const uint32_t *b)
+{
+    static_assert(W % 4 == 0, "W must be a multiple of 4");
+    uint32_t acc[W + 4];
+#pragma unroll
+    for (int i = 0; i < W + 4; ++i) acc[i] = 0u;
+    uint32_t st = 0u;
+    pw1 = pw2 = 0u;
+#pragma unroll 1
+    for (int j = 0; j < W; j += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t bj = b[j + u];
+            acc[u] = mad_lo_cc(a[0], bj, acc[u]);
+#pragma unroll
+            for (int i = 1; i < W; ++i) acc[u + i] = madc_lo_cc(a[i], bj, acc[u + i]);
+            acc[u + W] = addc(acc[u + W], 0u);
+            acc[u + 1] = mad_hi_cc(a[0], bj, acc[u + 1]);
+#pragma unroll
+            for (int i = 1; i < W - 1; ++i) acc[u + 1 + i] = madc_hi_cc(a[i], bj, acc[u + 1 + i]);
+            acc[u + W] = madc_hi(a[W - 1], bj, acc[u + W]);
+        }
+        if (j == W - 4) {
+            st |= acc[0] | acc[1];
+            pw2 = acc[2];
+            pw1 = acc[3];
+        } else {
+            st |= acc[0] | acc[1] | acc[2] | acc[3];
+        }
+#pragma unroll
+        for (int i = 0; i < W; ++i) acc[i] = acc[i + 4];
+#pragma unroll
+        for (int i = W; i < W + 4; ++i) acc[i] = 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < W; ++i) hi[i] = acc[i];
+    low_nz = st != 0u;
+}
+
+// r = RN_p(a * b)
+template <int W>
+MP_DEV void mul_impl(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, const RoundSpec &rs)
+{
+    const uint32_t s = a.s ^ b.s;
+    if (a.e == EXP_ZERO || b.e == EXP_ZERO) {
+        set_zero<W>(r, s);
+        return;
+    }
+    int64_t e = a.e + b.e;
+    if constexpr (W <= 16) {
+        uint32_t P[2 * W];
+        mul_full<W>(P, a.m, b.m);
+        if (!(P[2 * W - 1] >> 31)) {          // product in [1/4, 1/2): shift left one
+#pragma unroll
+            for (int i = 2 * W - 1; i > 0; --i) P[i] = (P[i] << 1) | (P[i - 1] >> 31);
+            P[0] <<= 1;
+            e -= 1;
+        }
+        uint32_t low = 0u;
+#pragma unroll
+        for (int i = 0; i < W - 1; ++i) low |= P[i];
+#pragma unroll
+        for (int i = 0; i < W; ++i) r.m[i] = P[W + i];
+        round_mant<W>(r.m, e, P[W - 1], low != 0u, rs);
+    } else {
+        uint32_t pw1, pw2;
+        bool low_nz;
+        mul_top<W>(r.m, pw1, pw2, low_nz, a.m, b.m);
+        if (!(r.m[W - 1] >> 31)) {
+#pragma unroll
+            for (int i = W - 1; i > 0; --i) r.m[i] = (r.m[i] << 1) | (r.m[i - 1] >> 31);
+            r.m[0] = (r.m[0] << 1) | (pw1 >> 31);
+            pw1 = (pw1 << 1) | (pw2 >> 31);
+            pw2 <<= 1;
+            e -= 1;
+        }
+        round_mant<W>(r.m, e, pw1, low_nz || pw2 != 0u, rs);
+    }
+    r.e = e;
+    r.s = s;
+}
+
+// --------------------------------------------------------------- add / sub
+// x (N words) >>= sh bits, 0 <= sh <= 32N; returns the OR of the bits
+// shifted out.  Branch-free: a select network over the word shift.
+template <int N>
+MP_DEV uint32_t shr_sticky(uint32_t (&x)[N], int sh)
+{
+    const int q = sh >> 5, b = sh & 31;
+    uint32_t st = 0u;
+#pragma unroll
+    for (int j = 0; (1 << j) <= N; ++j) {
+        const int d = 1 << j;
+        const bool on = (q >> j) & 1;
+#pragma unroll
+        for (int i = 0; i < d && i < N; ++i) st |= on ? x[i] : 0u;
+#pragma unroll
+        for (int i = 0; i < N; ++i) x[i] = on ? ((i + d < N) ? x[i + d] : 0u) : x[i];
+    }
+    st |= x[0] & ((1u << b) - 1u);
+#pragma unroll
+    for (int i = 0; i < N - 1; ++i) x[i] = __funnelshift_r(x[i], x[i + 1], b);
+    x[N - 1] >>= b;
+    return st;
+}
+
+// x (N words) <<= sh bits, 0 <= sh < 32N
+template <int N>
+MP_DEV void shl(uint32_t (&x)[N], int sh)
+{
+    const int q = sh >> 5, b = sh & 31;
+#pragma unroll
+    for (int j = 0; (1 << j) < N; ++j) {
+        const int d = 1 << j;
+        const bool on = (q >> j) & 1;
+#pragma unroll
+        for (int i = N - 1; i >= 0; --i) x[i] = on ? ((i - d >= 0) ? x[i - d] : 0u) : x[i];
+    }
+#pragma unroll
+    for (int i = N - 1; i > 0; --i) x[i] = __funnelshift_l(x[i - 1], x[i], b);
+    x[0] <<= b;
+}
+
+// leading zero bits of an N-word number (32N when zero)
+template <int N>
+MP_DEV int clz_words(const uint32_t (&x)[N])
+{
+    int lz = 0;
+    bool found = false;
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) {
+        if (!found) {
+            if (x[i]) { lz += __clz(x[i]); found = true; }
+            else lz += 32;
+        }
+    }
+    return lz;
+}
+
+// r = RN_p(x + (-1)^neg_y * y).  r may alias x or y.
+template <int W>
+MP_DEV void add_impl(Mp<W> &r, const Mp<W> &x, const Mp<W> &y, uint32_t neg_y, const RoundSpec &rs)
+{
+    const uint32_t ys = y.s ^ neg_y;
+    const bool xz = x.e == EXP_ZERO, yz = y.e == EXP_ZERO;
+    if (xz | yz) {
+        if (xz & yz) { set_zero<W>(r, x.s & ys); return; }
+        if (xz) {
+#pragma unroll
+            for (int i = 0; i < W; ++i) r.m[i] = y.m[i];
+            r.e = y.e;
+            r.s = ys;
+        } else if (&r != &x) {
+#pragma unroll
+            for (int i = 0; i < W; ++i) r.m[i] = x.m[i];
+            r.e = x.e;
+            r.s = x.s;
+        }
+        return;
+    }
+    // X: the operand with the larger exponent
+    const bool sw = y.e > x.e;
+    uint32_t X[W + 1], Y[W + 1];
+    X[0] = 0u;
+    Y[0] = 0u;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        X[i + 1] = sw ? y.m[i] : x.m[i];
+        Y[i + 1] = sw ? x.m[i] : y.m[i];
+    }
+    const int64_t ex = sw ? y.e : x.e;
+    const int64_t d64 = sw ? (y.e - x.e) : (x.e - y.e);
+    uint32_t sx = sw ? ys : x.s;
+    const uint32_t sy = sw ? x.s : ys;
+    const int d = d64 > 32 * (W + 1) ? 32 * (W + 1) : (int)d64;
+    const uint32_t st = shr_sticky<W + 1>(Y, d);
+    int64_t e = ex;
+    uint32_t S[W + 1];
+    if (sx == sy) {
+        S[0] = add_cc(X[0], Y[0]);
+#pragma unroll
+        for (int i = 1; i <= W; ++i) S[i] = addc_cc(X[i], Y[i]);
+        const uint32_t carry = addc(0u, 0u);
+        bool sticky = st != 0u;
+        if (carry) {
+            sticky |= (S[0] & 1u) != 0u;
+#pragma unroll
+            for (int i = 0; i < W; ++i) S[i] = __funnelshift_r(S[i], S[i + 1], 1);
+            S[W] = (S[W] >> 1) | 0x80000000u;
+            e += 1;
+        }
+#pragma unroll
+        for (int i = 0; i < W; ++i) r.m[i] = S[i + 1];
+        round_mant<W>(r.m, e, S[0], sticky, rs);
+        r.e = e;
+        r.s = sx;
+        return;
+    }
+    // effective subtraction: S = X - Y - [sticky]; the sticky borrow stands for
+    // the nonzero bits of y shifted out below the guard word
+    S[0] = sub_cc(X[0], Y[0]);
+#pragma unroll
+    for (int i = 1; i <= W; ++i) S[i] = subc_cc(X[i], Y[i]);
+    const uint32_t borrow = subc(0u, 0u);     // 0xffffffff if X < Y (only when d == 0)
+    if (st) {
+        S[0] = sub_cc(S[0], 1u);
+#pragma unroll
+        for (int i = 1; i <= W; ++i) S[i] = subc_cc(S[i], 0u);
+    }
+    if (borrow) {                             // |y| > |x| at equal exponents: negate
+        S[0] = sub_cc(0u, S[0]);
+#pragma unroll
+        for (int i = 1; i <= W; ++i) S[i] = subc_cc(0u, S[i]);
+        sx ^= 1u;
+    }
+    const int lz = clz_words<W + 1>(S);
+    if (lz == 32 * (W + 1)) {                 // exact cancellation: +0
+        set_zero<W>(r, 0u);
+        return;
+    }
+    shl<W + 1>(S, lz);
+    e -= lz;
+#pragma unroll
+    for (int i = 0; i < W; ++i) r.m[i] = S[i + 1];
+    round_mant<W>(r.m, e, S[0], st != 0u, rs);
+    r.e = e;
+    r.s = sx;
+}
+
+// |a| vs |b| (-1, 0, 1); zero is the smallest magnitude
+template <int W>
+MP_DEV int cmpabs(const Mp<W> &a, const Mp<W> &b)
+{
+    const bool az = a.e == EXP_ZERO, bz = b.e == EXP_ZERO;
+    if (az | bz) return (az && bz) ? 0 : (az ? -1 : 1);
+    if (a.e != b.e) return a.e < b.e ? -1 : 1;
+    int c = 0;
+#pragma unroll
+    for (int i = W - 1; i >= 0; --i)
+        if (c == 0 && a.m[i] != b.m[i]) c = a.m[i] < b.m[i] ? -1 : 1;
+    return c;
+}
+
+// --------------------------------------------------------------- division
+// r = RN_p(a / b), b != 0.  Binary restoring division of the mantissas
+// producing p + 2 quotient bits (the quotient of two fractions in [1/2, 1)
+// lies in (1/2, 2)), then one rounding with the remainder as sticky.
+template <int W>
+MP_DEV void div_impl(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, const RoundSpec &rs)
+{
+    const uint32_t s = a.s ^ b.s;
+    if (a.e == EXP_ZERO) { set_zero<W>(r, s); return; }
+    // remainder R (W+1 words) starts as a's mantissa; divisor D = b's mantissa
+    uint32_t R[W + 1], D[W + 1], Q[W + 1];
+#pragma unroll
+    for (int i = 0; i < W; ++i) { R[i] = a.m[i]; D[i] = b.m[i]; Q[i] = 0u; }
+    R[W] = 0u; D[W] = 0u; Q[W] = 0u;
+    // quotient bits q_0 (weight 1), q_1 (1/2), ..., q_{p+1}; Q holds them as an
+    // integer of p + 2 bits, most significant first
+    const int nq = rs.p + 2;
+    for (int t = 0; t < nq; ++t) {
+        // trial subtraction R - D
+        uint32_t T[W + 1];
+        T[0] = sub_cc(R[0], D[0]);
+#pragma unroll
+        for (int i = 1; i <= W; ++i) T[i] = subc_cc(R[i], D[i]);
+        const uint32_t br = subc(0u, 0u);
+        const uint32_t bit = br ? 0u : 1u;
+        if (bit) {
+#pragma unroll
+            for (int i = 0; i <= W; ++i) R[i] = T[i];
+        }
+        // Q = 2Q + bit
+#pragma unroll
+        for (int i = W; i > 0; --i) Q[i] = (Q[i] << 1) | (Q[i - 1] >> 31);
+        Q[0] = (Q[0] << 1) | bit;
+        // R = 2R
+#pragma unroll
+        for (int i = W; i > 0; --i) R[i] = (R[i] << 1) | (R[i - 1] >> 31);
+        R[0] <<= 1;
+    }
+    bool rem = false;
+#pragma unroll
+    for (int i = 0; i <= W; ++i) rem |= R[i] != 0u;
+    // value = Q * 2^-(p+1) * 2^(ea - eb); normalise Q (p+2 or p+1 significant
+    // bits) to the top of a (W+1)-word buffer and round
+    int64_t e = a.e - b.e + 1;
+    const int lz = clz_words<W + 1>(Q);
+    shl<W + 1>(Q, lz);
+    e -= lz - (32 * (W + 1) - nq);
+#pragma unroll
+    for (int i = 0; i < W; ++i) r.m[i] = Q[i + 1];
+    round_mant<W>(r.m, e, Q[0], rem, rs);
+    r.e = e;
+    r.s = s;
+}
+
+// ------------------------------------------------------------ entry points
+// For W >= 32 the operations are out-of-line calls: one copy per kernel
+// instead of one per call site keeps the 1024/2048-bit code small.
+template <int W>
+__device__ __noinline__ void add_call(Mp<W> &r, const Mp<W> &x, const Mp<W> &y, uint32_t neg_y,
+                                      const RoundSpec &rs)
+{
+    add_impl<W>(r, x, y, neg_y, rs);
+}
+template <int W>
+__device__ __noinline__ void mul_call(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, const RoundSpec &rs)
+{
+    mul_impl<W>(r, a, b, rs);
+}
+template <int W>
+__device__ __noinline__ void div_call(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, const RoundSpec &rs)
+{
+    div_impl<W>(r, a, b, rs);
+}
+
+template <int W>
+MP_DEV void add(Mp<W> &r, const Mp<W> &x, const Mp<W> &y, uint32_t neg_y, const RoundSpec &rs)
+{
+    if constexpr (W >= 32) add_call<W>(r, x, y, neg_y, rs);
+    else add_impl<W>(r, x, y, neg_y, rs);
+}
+template <int W>
+MP_DEV void mul(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, const RoundSpec &rs)
+{
+    if constexpr (W >= 32) mul_call<W>(r, a, b, rs);
+    else mul_impl<W>(r, a, b, rs);
+}
+template <int W>
+MP_DEV void div(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, const RoundSpec &rs)
+{
+    div_call<W>(r, a, b, rs);
+}
+
+}  // namespace mpg

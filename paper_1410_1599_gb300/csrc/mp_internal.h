@@ -1,0 +1,73 @@
+// mp_internal.h -- declarations shared by the library's translation units.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mpg {
+
+// A batch of equally shaped matrices in device memory.  Element (b, r, c):
+//   limb k : limb[b * bs_limb + k * plane + r * ld + c]
+//   exp    : exp [b * bs_es + r * ld + c],  sign likewise
+struct BMat {
+    uint64_t *limb;
+    int64_t *exp;
+    int8_t *sign;
+    int64_t ld, plane, bs_limb, bs_es;
+};
+
+// device-side status word bits (ORed by kernels, read by mp_sync_status)
+enum : unsigned {
+    ST_RANGE = 1u,
+    ST_DIVZERO = 2u,
+    ST_SINGULAR = 4u,
+    ST_TIMEOUT = 8u,
+};
+
+struct DevStatus {
+    unsigned flags;
+    unsigned pad;
+    long long singular_col;   // smallest column index with a zero pivot
+};
+
+// Launchers, one instantiation per word-capacity class W in {4, 8, 16, 32, 64}.
+// All take the precision p (<= 32 W) and the stream; all sizes are elements.
+template <int W>
+void launch_elementwise(int op, BMat X, BMat Y, BMat R, int64_t rows, int64_t cols, int p,
+                        DevStatus *st, cudaStream_t s);
+
+template <int W>
+void launch_convert(BMat X, int px, BMat R, int pr, int64_t rows, int64_t cols,
+                    DevStatus *st, cudaStream_t s);
+
+template <int W>
+void launch_gemm_simple(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p,
+                        DevStatus *st, cudaStream_t s);
+
+template <int W>
+void launch_gemm_block(BMat A, BMat B, BMat C, int64_t batch, int64_t m, int64_t l, int64_t n,
+                       int p, DevStatus *st, cudaStream_t s);
+
+// one level of the recursion on a batch of `nodes` parents
+//   parent A: m x l (real), even sizes M x K, halves h = M/2, k = K/2
+//   children: 7 * nodes matrices of h x k, child t of node b at index 7b + t
+template <int W>
+void launch_operands_a(int algo, BMat P, BMat Ch, int64_t nodes, int64_t m, int64_t l,
+                       int64_t h, int64_t k, int p, cudaStream_t s);
+template <int W>
+void launch_operands_b(int algo, BMat P, BMat Ch, int64_t nodes, int64_t l, int64_t n,
+                       int64_t k, int64_t w, int p, cudaStream_t s);
+// combine 7 child products (h x w) into the parent C (m x n real part mr x nr)
+template <int W>
+void launch_combine(int algo, BMat Ch, BMat C, int64_t nodes, int64_t h, int64_t w,
+                    int64_t mr, int64_t nr, int p, DevStatus *st, cudaStream_t s);
+// peel fix-ups on a batch of nodes (A: m x l, B: l x n, C: m x n)
+template <int W>
+void launch_rank1(BMat A, BMat B, BMat C, int64_t nodes, int64_t mr, int64_t nr, int64_t l,
+                  int p, DevStatus *st, cudaStream_t s);
+template <int W>
+void launch_border(BMat A, BMat B, BMat C, int64_t nodes, int64_t m, int64_t l, int64_t n,
+                   int64_t mr, bool last_row, bool last_col, int p, DevStatus *st,
+                   cudaStream_t s);
+
+}  // namespace mpg

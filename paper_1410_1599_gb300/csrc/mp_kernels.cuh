@@ -1,0 +1,590 @@
+// mp_kernels.cuh -- kernel templates of the MP GEMM path (arXiv 1410.1599
+// Sec. 2), instantiated once per word-capacity class W by gemm_w*.cu and
+// rec_w*.cu.
+#pragma once
+#include "mp_arith.cuh"
+#include "mp_internal.h"
+
+namespace mpg {
+
+// ----------------------------------------------------------------- helpers
+MP_DEV int64_t lim_off(const BMat &M, int64_t b, int64_t r, int64_t c)
+{
+    return b * M.bs_limb + r * M.ld + c;
+}
+MP_DEV int64_t es_off(const BMat &M, int64_t b, int64_t r, int64_t c)
+{
+    return b * M.bs_es + r * M.ld + c;
+}
+
+template <int W>
+MP_DEV void ld(Mp<W> &x, const BMat &M, int64_t b, int64_t r, int64_t c, int L)
+{
+    const int64_t lo = lim_off(M, b, r, c), eo = es_off(M, b, r, c);
+#pragma unroll
+    for (int k = 0; k < W / 2; ++k) {
+        uint64_t v = (k < L) ? __ldg(M.limb + lo + (int64_t)k * M.plane) : 0ull;
+        x.m[W - 1 - 2 * k] = (uint32_t)(v >> 32);
+        x.m[W - 2 - 2 * k] = (uint32_t)v;
+    }
+    x.e = __ldg(M.exp + eo);
+    x.s = (uint32_t)(__ldg(M.sign + eo) & 1);
+}
+
+// load through the coherent path (for data written earlier in the same kernel)
+template <int W>
+MP_DEV void ld_rw(Mp<W> &x, const BMat &M, int64_t b, int64_t r, int64_t c, int L)
+{
+    const int64_t lo = lim_off(M, b, r, c), eo = es_off(M, b, r, c);
+#pragma unroll
+    for (int k = 0; k < W / 2; ++k) {
+        uint64_t v = (k < L) ? M.limb[lo + (int64_t)k * M.plane] : 0ull;
+        x.m[W - 1 - 2 * k] = (uint32_t)(v >> 32);
+        x.m[W - 2 - 2 * k] = (uint32_t)v;
+    }
+    x.e = M.exp[eo];
+    x.s = (uint32_t)(M.sign[eo] & 1);
+}
+
+template <int W>
+MP_DEV void ld_or_zero(Mp<W> &x, bool valid, const BMat &M, int64_t b, int64_t r, int64_t c,
+                       int L)
+{
+    if (valid) ld<W>(x, M, b, r, c, L);
+    else set_zero<W>(x, 0u);
+}
+
+template <int W>
+MP_DEV bool st(const Mp<W> &x, const BMat &M, int64_t b, int64_t r, int64_t c, int L)
+{
+    const int64_t lo = lim_off(M, b, r, c), eo = es_off(M, b, r, c);
+#pragma unroll
+    for (int k = 0; k < W / 2; ++k)
+        if (k < L)
+            M.limb[lo + (int64_t)k * M.plane] =
+                ((uint64_t)x.m[W - 1 - 2 * k] << 32) | (uint64_t)x.m[W - 2 - 2 * k];
+    M.exp[eo] = x.e;
+    M.sign[eo] = (int8_t)x.s;
+    return out_of_range<W>(x);
+}
+
+MP_DEV void flag(DevStatus *st, unsigned f)
+{
+    if (st) atomicOr(&st->flags, f);
+}
+
+// ----------------------------------------------------------- elementwise
+template <int W>
+__global__ void elementwise_kernel(int op, BMat X, BMat Y, BMat R, int64_t rows, int64_t cols,
+                                   int p, DevStatus *status)
+{
+    const RoundSpec rs = make_spec<W>(p);
+    const int64_t total = rows * cols;
+    bool bad = false, dz = false;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / cols, c = t % cols;
+        Mp<W> x, y, z;
+        ld<W>(x, X, 0, r, c, rs.L);
+        ld<W>(y, Y, 0, r, c, rs.L);
+        if (op == 0) add<W>(z, x, y, 0u, rs);
+        else if (op == 1) add<W>(z, x, y, 1u, rs);
+        else if (op == 2) mul<W>(z, x, y, rs);
+        else {
+            if (y.e == EXP_ZERO) { dz = true; continue; }
+            div<W>(z, x, y, rs);
+        }
+        bad |= st<W>(z, R, 0, r, c, rs.L);
+    }
+    if (bad) flag(status, ST_RANGE);
+    if (dz) flag(status, ST_DIVZERO);
+}
+
+template <int W>
+__global__ void convert_kernel(BMat X, int px, BMat R, int pr, int64_t rows, int64_t cols,
+                               DevStatus *status)
+{
+    const RoundSpec rs = make_spec<W>(pr);
+    const int Lx = (px + 63) >> 6;
+    const int64_t total = rows * cols;
+    bool bad = false;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / cols, c = t % cols;
+        Mp<W> x;
+        ld<W>(x, X, 0, r, c, Lx);
+        if (x.e != EXP_ZERO) round_mant<W>(x.m, x.e, 0u, false, rs);
+        bad |= st<W>(x, R, 0, r, c, rs.L);
+    }
+    if (bad) flag(status, ST_RANGE);
+}
+
+// ---------------------------------------------------------- Simple (Eq. 1)
+// One thread per c_ij; operands read straight from global memory (through
+// the read-only cache), k ascending: c = RN(c + RN(a_ik b_kj)).
+template <int W>
+__global__ void __launch_bounds__(W <= 16 ? 256 : (W == 32 ? 128 : 64))
+gemm_simple_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p,
+                   DevStatus *status)
+{
+    const RoundSpec rs = make_spec<W>(p);
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = blockIdx.y * (int64_t)blockDim.y + threadIdx.y;
+    if (i >= m || j >= n) return;
+    Mp<W> c, a, b, t;
+    set_zero<W>(c, 0u);
+    for (int64_t k = 0; k < l; ++k) {
+        ld<W>(a, A, 0, i, k, rs.L);
+        ld<W>(b, B, 0, k, j, rs.L);
+        mul<W>(t, a, b, rs);
+        add<W>(c, c, t, 0u, rs);
+    }
+    if (st<W>(c, C, 0, i, j, rs.L)) flag(status, ST_RANGE);
+}
+
+// ---------------------------------------------------- Block (Eq. 2), batched
+// C_b = A_b B_b for a batch of equally shaped products (the leaves of the
+// Strassen/Winograd recursion, or one plain product).  Each CTA owns a
+// BM x BN tile of C (one element per thread) and walks k in slabs of BK:
+// the A and B slabs are staged in shared memory as limb planes, and every
+// c_ij still accumulates in k-ascending order, so the bits equal Simple's.
+template <int W> struct BlockCfg {
+    static constexpr int BN = 32;
+    static constexpr int BM = (W <= 16) ? 8 : (W == 32 ? 4 : 2);
+    static constexpr int BK = (W <= 8) ? 16 : 8;
+    static constexpr int THREADS = BM * BN;
+    static constexpr size_t smem(int L)
+    {
+        return (size_t)(BM * BK + BK * BN) * (size_t)(8 * L + 9);
+    }
+};
+
+template <int W>
+__global__ void __launch_bounds__(BlockCfg<W>::THREADS)
+gemm_block_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p,
+                  int64_t tiles_m, int64_t tiles_n, DevStatus *status)
+{
+    using Cfg = BlockCfg<W>;
+    constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const RoundSpec rs = make_spec<W>(p);
+    const int L = rs.L;
+    // shared layout: A limbs [L][BM][BK], B limbs [L][BK][BN], A exp, B exp, A sign, B sign
+    uint64_t *sAl = reinterpret_cast<uint64_t *>(smem_raw);
+    uint64_t *sBl = sAl + (size_t)L * BM * BK;
+    int64_t *sAe = reinterpret_cast<int64_t *>(sBl + (size_t)L * BK * BN);
+    int64_t *sBe = sAe + BM * BK;
+    int8_t *sAs = reinterpret_cast<int8_t *>(sBe + BK * BN);
+    int8_t *sBs = sAs + BM * BK;
+
+    const int64_t tile = blockIdx.x;
+    const int64_t b = tile / (tiles_m * tiles_n);
+    const int64_t tm = (tile / tiles_n) % tiles_m, tn = tile % tiles_n;
+    const int tx = threadIdx.x % BN, ty = threadIdx.x / BN;
+    const int64_t i = tm * BM + ty, j = tn * BN + tx;
+    const bool valid = (i < m) && (j < n);
+
+    Mp<W> c, a, bb, t;
+    set_zero<W>(c, 0u);
+    for (int64_t k0 = 0; k0 < l; k0 += BK) {
+        const int kc = (int)((l - k0) < BK ? (l - k0) : BK);
+        // stage the A slab (BM x kc) and the B slab (kc x BN)
+        for (int e = threadIdx.x; e < L * BM * BK; e += blockDim.x) {
+            const int kk = e % BK, rr = (e / BK) % BM, limb = e / (BK * BM);
+            const int64_t gi = tm * BM + rr, gk = k0 + kk;
+            sAl[e] = (gi < m && kk < kc)
+                         ? __ldg(A.limb + b * A.bs_limb + (int64_t)limb * A.plane + gi * A.ld + gk)
+                         : 0ull;
+        }
+        for (int e = threadIdx.x; e < L * BK * BN; e += blockDim.x) {
+            const int cc = e % BN, kk = (e / BN) % BK, limb = e / (BN * BK);
+            const int64_t gj = tn * BN + cc, gk = k0 + kk;
+            sBl[e] = (gj < n && kk < kc)
+                         ? __ldg(B.limb + b * B.bs_limb + (int64_t)limb * B.plane + gk * B.ld + gj)
+                         : 0ull;
+        }
+        for (int e = threadIdx.x; e < BM * BK; e += blockDim.x) {
+            const int kk = e % BK, rr = e / BK;
+            const int64_t gi = tm * BM + rr, gk = k0 + kk;
+            const bool ok = gi < m && kk < kc;
+            sAe[e] = ok ? __ldg(A.exp + b * A.bs_es + gi * A.ld + gk) : EXP_ZERO;
+            sAs[e] = ok ? __ldg(A.sign + b * A.bs_es + gi * A.ld + gk) : (int8_t)0;
+        }
+        for (int e = threadIdx.x; e < BK * BN; e += blockDim.x) {
+            const int cc = e % BN, kk = e / BN;
+            const int64_t gj = tn * BN + cc, gk = k0 + kk;
+            const bool ok = gj < n && kk < kc;
+            sBe[e] = ok ? __ldg(B.exp + b * B.bs_es + gk * B.ld + gj) : EXP_ZERO;
+            sBs[e] = ok ? __ldg(B.sign + b * B.bs_es + gk * B.ld + gj) : (int8_t)0;
+        }
+        __syncthreads();
+        if (valid) {
+            for (int kk = 0; kk < kc; ++kk) {
+#pragma unroll
+                for (int q = 0; q < W / 2; ++q) {
+                    const uint64_t va = (q < L) ? sAl[((size_t)q * BM + ty) * BK + kk] : 0ull;
+                    const uint64_t vb = (q < L) ? sBl[((size_t)q * BK + kk) * BN + tx] : 0ull;
+                    a.m[W - 1 - 2 * q] = (uint32_t)(va >> 32);
+                    a.m[W - 2 - 2 * q] = (uint32_t)va;
+                    bb.m[W - 1 - 2 * q] = (uint32_t)(vb >> 32);
+                    bb.m[W - 2 - 2 * q] = (uint32_t)vb;
+                }
+                a.e = sAe[ty * BK + kk];
+                a.s = (uint32_t)(sAs[ty * BK + kk] & 1);
+                bb.e = sBe[kk * BN + tx];
+                bb.s = (uint32_t)(sBs[kk * BN + tx] & 1);
+                mul<W>(t, a, bb, rs);
+                add<W>(c, c, t, 0u, rs);
+            }
+        }
+        __syncthreads();
+    }
+    if (valid && st<W>(c, C, b, i, j, L)) flag(status, ST_RANGE);
+}
+
+// ------------------------------------------- recursion: operand sums (Sec. 2)
+// Thread per (node, r < h, c < k).  Quadrant reads outside the parent's real
+// m x l are zero (padding); the even part never reaches a peeled last row
+// or column.  Children of node b are written at 7b + t, t = product index.
+template <int W>
+__global__ void operands_a_kernel(int algo, BMat P, BMat Ch, int64_t nodes, int64_t m,
+                                  int64_t l, int64_t h, int64_t k, int p)
+{
+    const RoundSpec rs = make_spec<W>(p);
+    const int64_t total = nodes * h * k;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = t % k, r = (t / k) % h, b = t / (h * k);
+        Mp<W> a11, a12, a21, a22, x, y;
+        ld_or_zero<W>(a11, r < m && c < l, P, b, r, c, rs.L);
+        ld_or_zero<W>(a12, r < m && c + k < l, P, b, r, c + k, rs.L);
+        ld_or_zero<W>(a21, r + h < m && c < l, P, b, r + h, c, rs.L);
+        ld_or_zero<W>(a22, r + h < m && c + k < l, P, b, r + h, c + k, rs.L);
+        const int64_t cb = 7 * b;
+        if (algo == 2) {   // Strassen: left operands of P1..P7
+            add<W>(x, a11, a22, 0u, rs); st<W>(x, Ch, cb + 0, r, c, rs.L);   // A11 + A22
+            add<W>(x, a21, a22, 0u, rs); st<W>(x, Ch, cb + 1, r, c, rs.L);   // A21 + A22
+            st<W>(a11, Ch, cb + 2, r, c, rs.L);                              // A11
+            st<W>(a22, Ch, cb + 3, r, c, rs.L);                              // A22
+            add<W>(x, a11, a12, 0u, rs); st<W>(x, Ch, cb + 4, r, c, rs.L);   // A11 + A12
+            add<W>(x, a21, a11, 1u, rs); st<W>(x, Ch, cb + 5, r, c, rs.L);   // A21 - A11
+            add<W>(x, a12, a22, 1u, rs); st<W>(x, Ch, cb + 6, r, c, rs.L);   // A12 - A22
+        } else {           // Winograd: left operands of M1..M7
+            add<W>(x, a21, a22, 0u, rs);                                     // S1 = A21 + A22
+            add<W>(y, x, a11, 1u, rs);                                       // S2 = S1 - A11
+            st<W>(y, Ch, cb + 0, r, c, rs.L);                                // M1: S2
+            st<W>(a11, Ch, cb + 1, r, c, rs.L);                              // M2: A11
+            st<W>(a12, Ch, cb + 2, r, c, rs.L);                              // M3: A12
+            st<W>(x, Ch, cb + 4, r, c, rs.L);                                // M5: S1
+            add<W>(x, a12, y, 1u, rs);                                       // S4 = A12 - S2
+            st<W>(x, Ch, cb + 5, r, c, rs.L);                                // M6: S4
+            add<W>(x, a11, a21, 1u, rs);                                     // S3 = A11 - A21
+            st<W>(x, Ch, cb + 3, r, c, rs.L);                                // M4: S3
+            st<W>(a22, Ch, cb + 6, r, c, rs.L);                              // M7: A22
+        }
+    }
+}
+
+template <int W>
+__global__ void operands_b_kernel(int algo, BMat P, BMat Ch, int64_t nodes, int64_t l,
+                                  int64_t n, int64_t k, int64_t w, int p)
+{
+    const RoundSpec rs = make_spec<W>(p);
+    const int64_t total = nodes * k * w;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = t % w, r = (t / w) % k, b = t / (k * w);
+        Mp<W> b11, b12, b21, b22, x, y;
+        ld_or_zero<W>(b11, r < l && c < n, P, b, r, c, rs.L);
+        ld_or_zero<W>(b12, r < l && c + w < n, P, b, r, c + w, rs.L);
+        ld_or_zero<W>(b21, r + k < l && c < n, P, b, r + k, c, rs.L);
+        ld_or_zero<W>(b22, r + k < l && c + w < n, P, b, r + k, c + w, rs.L);
+        const int64_t cb = 7 * b;
+        if (algo == 2) {   // Strassen: right operands of P1..P7
+            add<W>(x, b11, b22, 0u, rs); st<W>(x, Ch, cb + 0, r, c, rs.L);   // B11 + B22
+            st<W>(b11, Ch, cb + 1, r, c, rs.L);                              // B11
+            add<W>(x, b12, b22, 1u, rs); st<W>(x, Ch, cb + 2, r, c, rs.L);   // B12 - B22
+            add<W>(x, b21, b11, 1u, rs); st<W>(x, Ch, cb + 3, r, c, rs.L);   // B21 - B11
+            st<W>(b22, Ch, cb + 4, r, c, rs.L);                              // B22
+            add<W>(x, b11, b12, 0u, rs); st<W>(x, Ch, cb + 5, r, c, rs.L);   // B11 + B12
+            add<W>(x, b21, b22, 0u, rs); st<W>(x, Ch, cb + 6, r, c, rs.L);   // B21 + B22
+        } else {           // Winograd: right operands of M1..M7
+            add<W>(x, b12, b11, 1u, rs);                                     // S5 = B12 - B11
+            st<W>(x, Ch, cb + 4, r, c, rs.L);                                // M5: S5
+            add<W>(y, b22, x, 1u, rs);                                       // S6 = B22 - S5
+            st<W>(y, Ch, cb + 0, r, c, rs.L);                                // M1: S6
+            add<W>(x, y, b21, 1u, rs);                                       // S8 = S6 - B21
+            st<W>(x, Ch, cb + 6, r, c, rs.L);                                // M7: S8
+            add<W>(x, b22, b12, 1u, rs);                                     // S7 = B22 - B12
+            st<W>(x, Ch, cb + 3, r, c, rs.L);                                // M4: S7
+            st<W>(b11, Ch, cb + 1, r, c, rs.L);                              // M2: B11
+            st<W>(b21, Ch, cb + 2, r, c, rs.L);                              // M3: B21
+            st<W>(b22, Ch, cb + 5, r, c, rs.L);                              // M6: B22
+        }
+    }
+}
+
+// ------------------------------------------- recursion: C combination (Sec. 2)
+template <int W>
+__global__ void combine_kernel(int algo, BMat Ch, BMat C, int64_t nodes, int64_t h, int64_t w,
+                               int64_t mr, int64_t nr, int p, DevStatus *status)
+{
+    const RoundSpec rs = make_spec<W>(p);
+    const int64_t total = nodes * h * w;
+    bool bad = false;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = t % w, r = (t / w) % h, b = t / (h * w);
+        const int64_t cb = 7 * b;
+        const bool lo_r = r < mr, hi_r = r + h < mr, lo_c = c < nr, hi_c = c + w < nr;
+        Mp<W> x, y, z, u;
+        if (algo == 2) {
+            // C11 = P1 + P4 - P5 + P7 ; C12 = P3 + P5 ; C21 = P2 + P4 ; C22 = P1 + P3 - P2 + P6
+            Mp<W> p1, p4;
+            ld<W>(p1, Ch, cb + 0, r, c, rs.L);
+            ld<W>(p4, Ch, cb + 3, r, c, rs.L);
+            if (lo_r && lo_c) {
+                ld<W>(y, Ch, cb + 4, r, c, rs.L);
+                add<W>(x, p1, p4, 0u, rs);
+                add<W>(x, x, y, 1u, rs);
+                ld<W>(y, Ch, cb + 6, r, c, rs.L);
+                add<W>(x, x, y, 0u, rs);
+                bad |= st<W>(x, C, b, r, c, rs.L);
+            }
+            if (lo_r && hi_c) {
+                ld<W>(x, Ch, cb + 2, r, c, rs.L);
+                ld<W>(y, Ch, cb + 4, r, c, rs.L);
+                add<W>(x, x, y, 0u, rs);
+                bad |= st<W>(x, C, b, r, c + w, rs.L);
+            }
+            if (hi_r && lo_c) {
+                ld<W>(x, Ch, cb + 1, r, c, rs.L);
+                add<W>(x, x, p4, 0u, rs);
+                bad |= st<W>(x, C, b, r + h, c, rs.L);
+            }
+            if (hi_r && hi_c) {
+                ld<W>(y, Ch, cb + 2, r, c, rs.L);
+                add<W>(x, p1, y, 0u, rs);
+                ld<W>(y, Ch, cb + 1, r, c, rs.L);
+                add<W>(x, x, y, 1u, rs);
+                ld<W>(y, Ch, cb + 5, r, c, rs.L);
+                add<W>(x, x, y, 0u, rs);
+                bad |= st<W>(x, C, b + 0, r + h, c + w, rs.L);
+            }
+        } else {
+            // T1 = M1 + M2 ; T2 = T1 + M4 ; C11 = M2 + M3 ; C12 = T1 + M5 + M6 ;
+            // C21 = T2 - M7 ; C22 = T2 + M5
+            Mp<W> m2, t1, t2, m5;
+            ld<W>(x, Ch, cb + 0, r, c, rs.L);
+            ld<W>(m2, Ch, cb + 1, r, c, rs.L);
+            add<W>(t1, x, m2, 0u, rs);
+            ld<W>(x, Ch, cb + 3, r, c, rs.L);
+            add<W>(t2, t1, x, 0u, rs);
+            ld<W>(m5, Ch, cb + 4, r, c, rs.L);
+            if (lo_r && lo_c) {
+                ld<W>(x, Ch, cb + 2, r, c, rs.L);
+                add<W>(z, m2, x, 0u, rs);
+                bad |= st<W>(z, C, b, r, c, rs.L);
+            }
+            if (lo_r && hi_c) {
+                add<W>(z, t1, m5, 0u, rs);
+                ld<W>(x, Ch, cb + 5, r, c, rs.L);
+                add<W>(z, z, x, 0u, rs);
+                bad |= st<W>(z, C, b, r, c + w, rs.L);
+            }
+            if (hi_r && lo_c) {
+                ld<W>(x, Ch, cb + 6, r, c, rs.L);
+                add<W>(u, t2, x, 1u, rs);
+                bad |= st<W>(u, C, b, r + h, c, rs.L);
+            }
+            if (hi_r && hi_c) {
+                add<W>(u, t2, m5, 0u, rs);
+                bad |= st<W>(u, C, b, r + h, c + w, rs.L);
+            }
+        }
+    }
+    if (bad) flag(status, ST_RANGE);
+}
+
+// ------------------------------------------------- recursion: peel fix-ups
+// l peeled: c_ij = RN(c_ij + RN(a_{i,l-1} b_{l-1,j})) on the recursive part
+template <int W>
+__global__ void rank1_kernel(BMat A, BMat B, BMat C, int64_t nodes, int64_t mr, int64_t nr,
+                             int64_t l, int p, DevStatus *status)
+{
+    const RoundSpec rs = make_spec<W>(p);
+    const int64_t total = nodes * mr * nr;
+    bool bad = false;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = t % nr, r = (t / nr) % mr, b = t / (mr * nr);
+        Mp<W> x, a, bb, y;
+        ld_rw<W>(x, C, b, r, c, rs.L);
+        ld<W>(a, A, b, r, l - 1, rs.L);
+        ld<W>(bb, B, b, l - 1, c, rs.L);
+        mul<W>(y, a, bb, rs);
+        add<W>(x, x, y, 0u, rs);
+        bad |= st<W>(x, C, b, r, c, rs.L);
+    }
+    if (bad) flag(status, ST_RANGE);
+}
+
+// m peeled: last row by Simple over the whole l; n peeled: last column
+// (rows < mr) likewise.  Thread per output element.
+template <int W>
+__global__ void border_kernel(BMat A, BMat B, BMat C, int64_t nodes, int64_t m, int64_t l,
+                              int64_t n, int64_t mr, int last_row, int last_col, int p,
+                              DevStatus *status)
+{
+    const RoundSpec rs = make_spec<W>(p);
+    const int64_t per = (last_row ? n : 0) + (last_col ? mr : 0);
+    const int64_t total = nodes * per;
+    bool bad = false;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = t / per, q = t % per;
+        int64_t i, j;
+        if (last_row && q < n) { i = m - 1; j = q; }
+        else { i = q - (last_row ? n : 0); j = n - 1; }
+        Mp<W> c, a, bb, y;
+        set_zero<W>(c, 0u);
+        for (int64_t k = 0; k < l; ++k) {
+            ld<W>(a, A, b, i, k, rs.L);
+            ld<W>(bb, B, b, k, j, rs.L);
+            mul<W>(y, a, bb, rs);
+            add<W>(c, c, y, 0u, rs);
+        }
+        bad |= st<W>(c, C, b, i, j, rs.L);
+    }
+    if (bad) flag(status, ST_RANGE);
+}
+
+// ================================================================ launchers
+inline int grid_for(int64_t total, int threads)
+{
+    int64_t g = (total + threads - 1) / threads;
+    const int64_t cap = 152 * 64;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+template <int W>
+void launch_elementwise(int op, BMat X, BMat Y, BMat R, int64_t rows, int64_t cols, int p,
+                        DevStatus *st, cudaStream_t s)
+{
+    const int64_t total = rows * cols;
+    if (total <= 0) return;
+    elementwise_kernel<W><<<grid_for(total, 128), 128, 0, s>>>(op, X, Y, R, rows, cols, p, st);
+}
+
+template <int W>
+void launch_convert(BMat X, int px, BMat R, int pr, int64_t rows, int64_t cols, DevStatus *st,
+                    cudaStream_t s)
+{
+    const int64_t total = rows * cols;
+    if (total <= 0) return;
+    convert_kernel<W><<<grid_for(total, 128), 128, 0, s>>>(X, px, R, pr, rows, cols, st);
+}
+
+template <int W>
+void launch_gemm_simple(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p,
+                        DevStatus *st, cudaStream_t s)
+{
+    if (m <= 0 || n <= 0) return;
+    const int ty = (W <= 16) ? 8 : (W == 32 ? 4 : 2);
+    dim3 block(32, ty);
+    dim3 grid((unsigned)((n + 31) / 32), (unsigned)((m + ty - 1) / ty));
+    gemm_simple_kernel<W><<<grid, block, 0, s>>>(A, B, C, m, l, n, p, st);
+}
+
+template <int W>
+void launch_gemm_block(BMat A, BMat B, BMat C, int64_t batch, int64_t m, int64_t l, int64_t n,
+                       int p, DevStatus *st, cudaStream_t s)
+{
+    using Cfg = BlockCfg<W>;
+    if (batch <= 0 || m <= 0 || n <= 0) return;
+    const int L = (p + 63) >> 6;
+    const int64_t tm = (m + Cfg::BM - 1) / Cfg::BM, tn = (n + Cfg::BN - 1) / Cfg::BN;
+    const size_t sm = Cfg::smem(L);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(gemm_block_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Cfg::smem(W / 2));
+        attr_set = true;
+    }
+    gemm_block_kernel<W><<<(unsigned)(batch * tm * tn), Cfg::THREADS, sm, s>>>(
+        A, B, C, m, l, n, p, tm, tn, st);
+}
+
+template <int W>
+void launch_operands_a(int algo, BMat P, BMat Ch, int64_t nodes, int64_t m, int64_t l,
+                       int64_t h, int64_t k, int p, cudaStream_t s)
+{
+    const int64_t total = nodes * h * k;
+    if (total <= 0) return;
+    operands_a_kernel<W><<<grid_for(total, 128), 128, 0, s>>>(algo, P, Ch, nodes, m, l, h, k, p);
+}
+
+template <int W>
+void launch_operands_b(int algo, BMat P, BMat Ch, int64_t nodes, int64_t l, int64_t n,
+                       int64_t k, int64_t w, int p, cudaStream_t s)
+{
+    const int64_t total = nodes * k * w;
+    if (total <= 0) return;
+    operands_b_kernel<W><<<grid_for(total, 128), 128, 0, s>>>(algo, P, Ch, nodes, l, n, k, w, p);
+}
+
+template <int W>
+void launch_combine(int algo, BMat Ch, BMat C, int64_t nodes, int64_t h, int64_t w, int64_t mr,
+                    int64_t nr, int p, DevStatus *st, cudaStream_t s)
+{
+    const int64_t total = nodes * h * w;
+    if (total <= 0) return;
+    combine_kernel<W><<<grid_for(total, 128), 128, 0, s>>>(algo, Ch, C, nodes, h, w, mr, nr, p, st);
+}
+
+template <int W>
+void launch_rank1(BMat A, BMat B, BMat C, int64_t nodes, int64_t mr, int64_t nr, int64_t l,
+                  int p, DevStatus *st, cudaStream_t s)
+{
+    const int64_t total = nodes * mr * nr;
+    if (total <= 0) return;
+    rank1_kernel<W><<<grid_for(total, 128), 128, 0, s>>>(A, B, C, nodes, mr, nr, l, p, st);
+}
+
+template <int W>
+void launch_border(BMat A, BMat B, BMat C, int64_t nodes, int64_t m, int64_t l, int64_t n,
+                   int64_t mr, bool last_row, bool last_col, int p, DevStatus *st,
+                   cudaStream_t s)
+{
+    const int64_t per = (last_row ? n : 0) + (last_col ? mr : 0);
+    const int64_t total = nodes * per;
+    if (total <= 0) return;
+    border_kernel<W><<<grid_for(total, 64), 64, 0, s>>>(A, B, C, nodes, m, l, n, mr,
+                                                         last_row ? 1 : 0, last_col ? 1 : 0, p, st);
+}
+
+#define MPG_INSTANTIATE_GEMM(W)                                                                 \
+    template void launch_elementwise<W>(int, BMat, BMat, BMat, int64_t, int64_t, int,           \
+                                        DevStatus *, cudaStream_t);                             \
+    template void launch_convert<W>(BMat, int, BMat, int, int64_t, int64_t, DevStatus *,        \
+                                    cudaStream_t);                                              \
+    template void launch_gemm_simple<W>(BMat, BMat, BMat, int64_t, int64_t, int64_t, int,       \
+                                        DevStatus *, cudaStream_t);                             \
+    template void launch_gemm_block<W>(BMat, BMat, BMat, int64_t, int64_t, int64_t, int64_t,    \
+                                       int, DevStatus *, cudaStream_t);                         \
+    template void launch_rank1<W>(BMat, BMat, BMat, int64_t, int64_t, int64_t, int64_t, int,    \
+                                  DevStatus *, cudaStream_t);                                   \
+    template void launch_border<W>(BMat, BMat, BMat, int64_t, int64_t, int64_t, int64_t,        \
+                                   int64_t, bool, bool, int, DevStatus *, cudaStream_t);
+
+#define MPG_INSTANTIATE_REC(W)                                                                  \
+    template void launch_operands_a<W>(int, BMat, BMat, int64_t, int64_t, int64_t, int64_t,     \
+                                       int64_t, int, cudaStream_t);                             \
+    template void launch_operands_b<W>(int, BMat, BMat, int64_t, int64_t, int64_t, int64_t,     \
+                                       int64_t, int, cudaStream_t);                             \
+    template void launch_combine<W>(int, BMat, BMat, int64_t, int64_t, int64_t, int64_t,        \
+                                    int64_t, int, DevStatus *, cudaStream_t);
+
+}  // namespace mpg

@@ -1,0 +1,57 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol that
+include/mpgemm.h declares (no GPU needed: nothing is called that computes)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1410_1599_gb300 import binding
+from paper_1410_1599_gb300 import build as libbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    hdr = open(os.path.join(ROOT, "include", "mpgemm.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\**\s*(mp[a-z_0-9]*)\s*\(", hdr, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declarations_match_binding_list():
+    assert _declared() == sorted(binding.EXPORTS)
+
+
+def test_library_builds_and_exports_everything():
+    path = libbuild.build()
+    lib = ctypes.CDLL(path)
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_host_only_calls():
+    lib = binding.load_library()
+    assert lib.mp_version() == 100
+    assert lib.mp_strerror(-3) == b"zero pivot: matrix is singular"
+    assert lib.mp_set_odd_policy(7) == -1
+    assert lib.mp_set_lu(0, 0, 64) == -1
+    # Simple and Block need no workspace; the recursion does
+    assert lib.mpgemm_workspace_size(1024, 1024, 1024, 512, 0, 64) == 0
+    assert lib.mpgemm_workspace_size(1024, 1024, 1024, 512, 3, 64) > 0
+    assert lib.mpgemm_workspace_size(64, 64, 64, 512, 3, 64) == 0
+
+
+def test_argument_errors_without_gpu():
+    """Argument checks run on the host before any CUDA call."""
+    lib = binding.load_library()
+    bad = binding.MPMat(100000, 0, 2, 2, 2, 4, 1, 1, 1)      # precision out of range
+    assert lib.mpgemm(2, 2, 2, 100000, 0, 64, ctypes.byref(bad), ctypes.byref(bad),
+                      ctypes.byref(bad)) == -1
+    A = binding.MPMat(128, 0, 2, 3, 3, 6, 4096, 8192, 12288)
+    B = binding.MPMat(128, 0, 3, 2, 2, 6, 16384, 20480, 24576)
+    Cm = binding.MPMat(128, 0, 2, 2, 1, 4, 32768, 36864, 40960)  # ld < cols
+    assert lib.mpgemm(2, 3, 2, 128, 0, 64, ctypes.byref(A), ctypes.byref(B), ctypes.byref(Cm)) == -1
+    Cm = binding.MPMat(128, 0, 2, 2, 2, 4, 4096, 8192, 12288)    # aliases A
+    assert lib.mpgemm(2, 3, 2, 128, 0, 64, ctypes.byref(A), ctypes.byref(B), ctypes.byref(Cm)) == -1
+    assert lib.mpgemm(2, 3, 2, 128, 9, 64, ctypes.byref(A), ctypes.byref(B), ctypes.byref(A)) == -1

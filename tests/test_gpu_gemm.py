@@ -1,0 +1,90 @@
+"""GPU MP GEMM against the CPU oracle running the same algorithm, summation
+order, cutoff and odd-dimension policy: bit-exact (arXiv 1410.1599 Sec. 2).
+
+Oracle-sized cases span several leaf tiles and ragged tails; the full sizes
+of the benchmark (n in {1023, 1024, 2048} at 512 bits, cutoff 64) are
+checked on the closed sampled row/column sets the oracle can evaluate
+(oracle.orc_sampled.c), which cover every recursion path of those rows."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1410_1599_gb300 import binding as mp
+from paper_1410_1599_gb300 import inputs as gen
+from tests.gpu_util import assert_bits_equal, dev, gemm
+
+pytestmark = pytest.mark.gpu
+
+ALGOS = {"simple": mp.SIMPLE, "block": mp.BLOCK, "strassen": mp.STRASSEN, "winograd": mp.WINOGRAD}
+
+
+def test_config1_simple_64_256bit():
+    A = gen.uniform_pm1(64, 64, 256, 1)
+    B = gen.uniform_pm1(64, 64, 256, 2)
+    want = orc.gemm(orc.SIMPLE, A, B)
+    for algo in (mp.SIMPLE, mp.BLOCK):
+        assert_bits_equal(gemm(A, B, algo), want, "config1 algo %d" % algo)
+
+
+@pytest.mark.parametrize("p", [128, 200, 256, 512, 1024, 2048])
+@pytest.mark.parametrize("algo", ["simple", "block"])
+def test_simple_block_ragged(algo, p):
+    m, l, n = (37, 29, 45) if p >= 1024 else (67, 45, 83)
+    A = gen.uniform_pm1(m, l, p, 11, -16, 16)
+    B = gen.uniform_pm1(l, n, p, 12, -16, 16)
+    want = orc.gemm(orc.SIMPLE, A, B)
+    assert_bits_equal(gemm(A, B, ALGOS[algo]), want, "%s p=%d" % (algo, p))
+
+
+@pytest.mark.parametrize("policy", [mp.PEEL, mp.MIXED])
+@pytest.mark.parametrize("algo", ["strassen", "winograd"])
+@pytest.mark.parametrize("dims,cutoff,p", [((130, 97, 71), 16, 256), ((128, 128, 128), 16, 512),
+                                           ((67, 99, 35), 8, 128), ((33, 33, 33), 4, 1024),
+                                           ((150, 151, 149), 32, 512), ((27, 19, 23), 3, 2048)])
+def test_recursion_matches_oracle(algo, policy, dims, cutoff, p):
+    m, l, n = dims
+    A = gen.uniform_pm1(m, l, p, 21, -16, 16)
+    B = gen.uniform_pm1(l, n, p, 22, -16, 16)
+    want = orc.gemm(ALGOS[algo], A, B, cutoff=cutoff, policy=policy)
+    mp.set_odd_policy(policy)
+    try:
+        got = gemm(A, B, ALGOS[algo], cutoff)
+    finally:
+        mp.set_odd_policy(mp.PEEL)
+    assert_bits_equal(got, want, "%s %s" % (algo, dims))
+
+
+@pytest.mark.parametrize("algo", list(ALGOS))
+def test_degenerate_shapes(algo):
+    p = 256
+    for m, l, n in ((1, 1, 1), (1, 7, 1), (5, 0, 3), (2, 3, 5), (65, 1, 65), (1, 130, 129)):
+        A = gen.uniform_pm1(m, l, p, 31)
+        B = gen.uniform_pm1(l, n, p, 32)
+        want = orc.gemm(ALGOS[algo], A, B, cutoff=1)
+        assert_bits_equal(gemm(A, B, ALGOS[algo], 1), want, "%s %s" % (algo, (m, l, n)))
+
+
+def test_integer_inputs_all_algorithms_equal():
+    A = gen.small_ints(96, 96, 512, 41, bits=20)
+    B = gen.small_ints(96, 96, 512, 42, bits=20)
+    ref = gemm(A, B, mp.SIMPLE)
+    for algo in (mp.BLOCK, mp.STRASSEN, mp.WINOGRAD):
+        assert_bits_equal(gemm(A, B, algo, 8), ref, "integers algo %d" % algo)
+
+
+@pytest.mark.parametrize("n", [1023, 1024, 2048])
+@pytest.mark.parametrize("algo", ["winograd", "strassen", "simple"])
+def test_full_size_sampled(algo, n):
+    """The benchmark workload: 512-bit, entries U[-1,1) * 2^e, e in [-16, 16],
+    cutoff 64, odd sizes peeled, in the launch configuration bench.py times."""
+    p, cutoff = 512, 64
+    A = gen.uniform_pm1(n, n, p, 3, -16, 16)
+    B = gen.uniform_pm1(n, n, p, 4, -16, 16)
+    got = gemm(A, B, ALGOS[algo], cutoff)
+    rng = np.random.default_rng(n)
+    seeds = [(0, n - 1), (n - 1, 0), tuple(rng.integers(0, n, 2))]
+    for i0, j0 in seeds:
+        rows = orc.sample_set(0, ALGOS[algo], n, n, n, cutoff, orc.PEEL, int(i0))
+        cols = orc.sample_set(1, ALGOS[algo], n, n, n, cutoff, orc.PEEL, int(j0))
+        want = orc.gemm_sampled(ALGOS[algo], A, B, rows, cols, cutoff=cutoff)
+        assert_bits_equal(got.sub(rows, cols), want, "%s n=%d sample (%d,%d)" % (algo, n, i0, j0))
