@@ -113,11 +113,14 @@ int orc_lu(orc_mat *A, int64_t *piv, int panel, int algo, int cutoff, int policy
 }
 
 /*
- * Solve LU x = P b with the factors of orc_lu:
- *   y = P b (the row exchanges of the factorisation, in order),
- *   y_i = RN(y_i - RN(l_ij y_j)) for j = 0 .. i-1 ascending (unit lower),
- *   x_i = RN(RN(y_i - sum_{j>i} RN(u_ij x_j)) / u_ii), j = i+1 .. n-1 ascending,
- *         for i = n-1 down to 0.
+ * Solve LU x = P b with the factors of orc_lu (the paper does not fix the
+ * order of the substitutions; both are taken column by column):
+ *   y = P b (the row exchanges of the factorisation, in order);
+ *   forward, j = 0 .. n-1:      y_i = RN(y_i - RN(l_ij y_j)) for all i > j
+ *                               (each y_i sees its terms in ascending j);
+ *   backward, j = n-1 .. 0:     x_j = RN(y_j / u_jj), then
+ *                               y_i = RN(y_i - RN(u_ij x_j)) for all i < j
+ *                               (each y_i sees its terms in descending j).
  * b and x are n x 1.  Returns 0, or -1 on a zero diagonal.
  */
 int orc_lu_solve(const orc_mat *LU, const int64_t *piv, const orc_mat *b, orc_mat *x)
@@ -129,21 +132,21 @@ int orc_lu_solve(const orc_mat *LU, const int64_t *piv, const orc_mat *b, orc_ma
     for (int64_t i = 0; i < n; ++i) orc_get(b, i, 0, &v[i]);
     for (int64_t k = 0; k < n; ++k)
         if (piv[k] != k) { orc_num s = v[k]; v[k] = v[piv[k]]; v[piv[k]] = s; }
-    for (int64_t i = 0; i < n; ++i)
-        for (int64_t j = 0; j < i; ++j) {
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = j + 1; i < n; ++i) {
             orc_get(LU, i, j, &a);
             orc_mul(&t, &a, &v[j], p);
             orc_sub(&v[i], &v[i], &t, p);
         }
-    for (int64_t i = n - 1; i >= 0; --i) {
-        for (int64_t j = i + 1; j < n; ++j) {
+    for (int64_t j = n - 1; j >= 0; --j) {
+        orc_get(LU, j, j, &u);
+        if (orc_div(&t, &v[j], &u, p)) { free(v); return -1; }
+        v[j] = t;
+        for (int64_t i = 0; i < j; ++i) {
             orc_get(LU, i, j, &a);
             orc_mul(&t, &a, &v[j], p);
             orc_sub(&v[i], &v[i], &t, p);
         }
-        orc_get(LU, i, i, &u);
-        if (orc_div(&t, &v[i], &u, p)) { free(v); return -1; }
-        v[i] = t;
     }
     orc_mat_alloc(x, n, 1, p);
     for (int64_t i = 0; i < n; ++i) orc_put(x, i, 0, &v[i]);

@@ -157,13 +157,13 @@ def test_replay_solve():
     v = [entry_mpf(b, i, 0) for i in range(n)]
     for k, pk in enumerate(piv):
         v[k], v[pk] = v[pk], v[k]
-    for i in range(n):
-        for j in range(i):
+    for j in range(n):                    # forward, column by column
+        for i in range(j + 1, n):
             v[i] = mp_sub(v[i], mp_mul(Fm[i][j], v[j], p), p)
-    for i in range(n - 1, -1, -1):
-        for j in range(i + 1, n):
+    for j in range(n - 1, -1, -1):        # backward, column by column
+        v[j] = mp_div(v[j], Fm[j][j], p)
+        for i in range(j):
             v[i] = mp_sub(v[i], mp_mul(Fm[i][j], v[j], p), p)
-        v[i] = mp_div(v[i], Fm[i][i], p)
     assert [entry_mpf(x, i, 0) for i in range(n)] == v
 
 
