@@ -262,35 +262,34 @@ def run_ours(a, rank, world, local):
 
 def cpu_baseline(A, B, seconds):
     """The oracle (plain C, all host threads) computing a sample of outputs of
-    the same product by Simple dots: eff GFLOP/s = 2 l outputs / t."""
+    the same product by Simple dot products: eff GFLOP/s = 2 l outputs / t.
+    Only the sampled rows of A and the one column of B are handed over."""
     import numpy as np
 
     from oracle import oracle as orc
 
-    n = A.shape[0]
+    n, l = A.shape
     threads = orc.max_threads()
     rng = np.random.default_rng(0)
-    count, t = 8, 0.0
-    while True:
+    col = B.sub(np.arange(l), [int(rng.integers(0, B.shape[1]))])
+
+    def run(count):
         rows = np.sort(rng.choice(n, size=count, replace=False))
-        cols = rng.choice(n, size=1)
+        Asub = A.sub(rows, np.arange(l))
         t0 = time.perf_counter()
-        orc.gemm_sampled(orc.SIMPLE, A, B, rows, cols, cutoff=64)
-        t = time.perf_counter() - t0
-        if t > seconds / 4 or count >= n:
-            break
+        orc.gemm(orc.SIMPLE, Asub, col)
+        return time.perf_counter() - t0
+
+    count, t = threads, run(threads)
+    while t < seconds / 8 and count < n:
         count = min(n, count * 4)
-    # scale to ~seconds of work: one more run at the size that fits
-    per = t / count
-    final = int(max(8, min(n, seconds / max(per, 1e-9))))
-    rows = np.sort(rng.choice(n, size=final, replace=False))
-    t0 = time.perf_counter()
-    orc.gemm_sampled(orc.SIMPLE, A, B, rows, np.array([0]), cutoff=64)
-    t = time.perf_counter() - t0
-    return {"value": round(2.0 * A.shape[1] * final / t / 1e9, 6), "unit": "GFLOP/s",
+        t = run(count)
+    final = int(max(threads, min(n, count * seconds / max(t, 1e-9))))
+    t = run(final)
+    return {"value": round(2.0 * l * final / t / 1e9, 6), "unit": "GFLOP/s",
             "cores": threads, "kind": "oracle",
             "sample": "%d outputs of C by Simple dot products (l=%d), oracle C code, %d threads"
-                      % (final, A.shape[1], threads), "seconds": round(t, 2)}
+                      % (final, l, threads), "seconds": round(t, 2)}
 
 
 # ----------------------------------------------------------- reference arm
@@ -306,14 +305,17 @@ def run_reference(a, rank, world):
 
     from oracle import oracle as orc
     threads = orc.max_threads()
-    per_step = max(16, int(64 * 512 / p))
+    per_step = max(threads, int(256 * 512 / p))
     rng = np.random.default_rng(1)
-    for _ in range(a.warmup):
-        orc.gemm_sampled(orc.SIMPLE, A, B, np.arange(2), np.array([0]), cutoff=64)
+    subs = []
+    for s in range(a.warmup + a.steps):
+        rows = np.sort(rng.choice(n, size=per_step, replace=False))
+        subs.append((A.sub(rows, np.arange(n)), B.sub(np.arange(n), [s % n])))
+    for s in range(a.warmup):
+        orc.gemm(orc.SIMPLE, *subs[s])
     t0 = time.perf_counter()
     for s in range(a.steps):
-        rows = np.sort(rng.choice(n, size=per_step, replace=False))
-        orc.gemm_sampled(orc.SIMPLE, A, B, rows, np.array([s % n]), cutoff=64)
+        orc.gemm(orc.SIMPLE, *subs[a.warmup + s])
     t = (time.perf_counter() - t0) / a.steps
     value = 2.0 * n * per_step / t / 1e9
     line = {"impl": "reference", "metric": "eff. MP GFLOP/s (2mln/t)", "value": round(value, 6),

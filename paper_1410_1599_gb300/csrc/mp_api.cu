@@ -36,7 +36,7 @@ DevStatus *status_ptr()
     if (!g_status[dev]) {
         DevStatus *p = nullptr;
         if (cudaMalloc(&p, sizeof(DevStatus)) != cudaSuccess) return nullptr;
-        DevStatus init{0u, 0u, -1};
+        DevStatus init{0u, 0u, INT64_MAX};
         cudaMemcpy(p, &init, sizeof init, cudaMemcpyHostToDevice);
         g_status[dev] = p;
     }
@@ -201,6 +201,8 @@ struct Workspace {
         used = off + bytes;
         return base + off;
     }
+    size_t mark() const { return used; }
+    void reset(size_t m) { used = m; }
     ~Workspace()
     {
         if (owned && base) cudaFreeAsync(base, s);
@@ -346,6 +348,60 @@ int run_recursion(int algo, const std::vector<LevelDims> &lv, int p, BMat A0, BM
     return launch_status();
 }
 
+// C := A B for (possibly strided) views, with the recursion's buffers carved
+// from ws (which must hold gemm_ws_bytes(...)).  Stream-ordered.
+size_t gemm_ws_bytes(int algo, int64_t m, int64_t l, int64_t n, int cutoff, int policy, int L)
+{
+    if (algo != MP_STRASSEN && algo != MP_WINOGRAD) return 0;
+    if (m <= 0 || l <= 0 || n <= 0) return 0;
+    auto lv = plan(m, l, n, cutoff, policy);
+    return lv.size() <= 1 ? 0 : recursion_bytes(lv, L);
+}
+
+int gemm_core(int algo, int cutoff, int policy, int64_t m, int64_t l, int64_t n, int p, BMat A,
+              BMat B, BMat C, Workspace &ws, DevStatus *st, cudaStream_t s)
+{
+    if (m == 0 || n == 0) return MP_OK;
+    const int L = limbs_of(p);
+    if (l == 0) {
+        Prof pr(MP_K_ELEMENTWISE, (double)m * n, s);
+        fill_zero_kernel<<<(unsigned)std::min<int64_t>((m * n + 127) / 128, 152 * 32), 128, 0, s>>>(
+            C, m, n, L);
+        return launch_status();
+    }
+    if (algo == MP_SIMPLE) {
+        Prof pr(MP_K_SIMPLE, (double)m * l * n, s);
+        dispatch(p, [&](auto w) {
+            launch_gemm_simple<decltype(w)::value>(A, B, C, m, l, n, p, st, s);
+        });
+        return launch_status();
+    }
+    auto lv = plan(m, l, n, cutoff, policy);
+    if (algo == MP_BLOCK || lv.size() <= 1) {
+        Prof pr(MP_K_LEAF, (double)m * l * n, s);
+        dispatch(p, [&](auto w) {
+            launch_gemm_block<decltype(w)::value>(A, B, C, 1, m, l, n, p, st, s);
+        });
+        return launch_status();
+    }
+    int rc = MP_OK;
+    const size_t mk = ws.mark();
+    dispatch(p, [&](auto w) {
+        rc = run_recursion<decltype(w)::value>(algo, lv, p, A, B, C, ws, st, s);
+    });
+    ws.reset(mk);
+    return rc;
+}
+
+BMat sub_view(BMat M, int64_t r0, int64_t c0)
+{
+    BMat v = M;
+    v.limb += r0 * M.ld + c0;
+    v.exp += r0 * M.ld + c0;
+    v.sign += r0 * M.ld + c0;
+    return v;
+}
+
 }  // namespace
 
 // ======================================================================= ABI
@@ -406,10 +462,10 @@ int mp_sync_status(void)
     DevStatus h{};
     if (cudaMemcpy(&h, st, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess) return MP_ERR_CUDA;
     if (h.flags) {
-        DevStatus init{0u, 0u, -1};
+        DevStatus init{0u, 0u, INT64_MAX};
         cudaMemcpy(st, &init, sizeof init, cudaMemcpyHostToDevice);
     }
-    g_ts.singular_col = h.singular_col;
+    g_ts.singular_col = (h.singular_col == INT64_MAX) ? -1 : h.singular_col;
     if (h.flags & ST_TIMEOUT) return MP_ERR_TIMEOUT;
     if (h.flags & ST_SINGULAR) return MP_ERR_SINGULAR;
     if (h.flags & ST_DIVZERO) return MP_ERR_ARG;
@@ -511,48 +567,89 @@ int mpgemm(int64_t m, int64_t l, int64_t n, int32_t prec, int32_t algo, int32_t 
     cudaStream_t s = g_ts.stream;
     DevStatus *st = status_ptr();
     if (!st) return MP_ERR_CUDA;
-    const int L = limbs_of(prec);
-    if (l == 0) {
-        Prof pr(MP_K_ELEMENTWISE, (double)m * n, s);
-        fill_zero_kernel<<<(unsigned)std::min<int64_t>((m * n + 127) / 128, 152 * 32), 128, 0, s>>>(
-            bmat(C), m, n, L);
-        return launch_status();
-    }
-    if (algo == MP_SIMPLE) {
-        Prof pr(MP_K_SIMPLE, (double)m * l * n, s);
-        dispatch(prec, [&](auto w) {
-            launch_gemm_simple<decltype(w)::value>(bmat(A), bmat(B), bmat(C), m, l, n, prec, st, s);
-        });
-        return launch_status();
-    }
-    auto lv = plan(m, l, n, cutoff, g_ts.odd_policy);
-    if (algo == MP_BLOCK || lv.size() <= 1) {
-        Prof pr(MP_K_LEAF, (double)m * l * n, s);
-        dispatch(prec, [&](auto w) {
-            launch_gemm_block<decltype(w)::value>(bmat(A), bmat(B), bmat(C), 1, m, l, n, prec, st, s);
-        });
-        return launch_status();
-    }
     Workspace ws;
-    int rc = ws.acquire(recursion_bytes(lv, L), s);
+    int rc = ws.acquire(gemm_ws_bytes(algo, m, l, n, cutoff, g_ts.odd_policy, limbs_of(prec)), s);
     if (rc != MP_OK) return rc;
-    dispatch(prec, [&](auto w) {
-        rc = run_recursion<decltype(w)::value>(algo, lv, prec, bmat(A), bmat(B), bmat(C), ws, st, s);
-    });
-    return rc;
+    return gemm_core(algo, cutoff, g_ts.odd_policy, m, l, n, prec, bmat(A), bmat(B), bmat(C), ws,
+                     st, s);
+}
+
+static size_t lu_ws_bytes(int64_t n, int p, int panel, int algo, int cutoff, int policy)
+{
+    const int L = limbs_of(p);
+    const int64_t K = std::min<int64_t>(panel, n);
+    const int64_t nt = n - K;                              // largest trailing block
+    size_t b = mat_bytes(1, nt, nt, L) + mat_bytes(1, n, 1, L) + padded((size_t)n * 8);
+    b += gemm_ws_bytes(algo, nt, K, nt, cutoff, policy, L) + 512;
+    return b;
 }
 
 size_t mplu_workspace_size(int64_t n, int32_t prec)
 {
-    (void)n;
-    (void)prec;
-    return 0;
+    if (n <= 0 || !valid_prec(prec)) return 0;
+    return lu_ws_bytes(n, prec, g_ts.lu_panel, g_ts.lu_algo, g_ts.lu_cutoff, g_ts.odd_policy);
 }
 
 int mplu(int64_t n, int32_t prec, mpmat_t *A, int64_t *piv, const mpmat_t *b, mpmat_t *x)
 {
-    (void)n; (void)prec; (void)A; (void)piv; (void)b; (void)x;
-    return MP_ERR_UNSUPPORTED;
+    if (!valid_prec(prec) || n < 0 || !valid_mat(A, n, n, prec)) return MP_ERR_ARG;
+    if (n > 0 && !piv) return MP_ERR_ARG;
+    if (x) {
+        if (!b || !valid_mat(b, n, 1, prec) || !valid_mat(x, n, 1, prec)) return MP_ERR_ARG;
+        if (overlaps(x, A) || overlaps(x, b) || overlaps(b, A)) return MP_ERR_ARG;
+    }
+    if (n == 0) return MP_OK;
+    cudaStream_t s = g_ts.stream;
+    DevStatus *st = status_ptr();
+    if (!st) return MP_ERR_CUDA;
+    const int K = g_ts.lu_panel, algo = g_ts.lu_algo, cutoff = g_ts.lu_cutoff;
+    const int policy = g_ts.odd_policy;
+    const int L = limbs_of(prec);
+    Workspace ws;
+    int rc = ws.acquire(lu_ws_bytes(n, prec, K, algo, cutoff, policy), s);
+    if (rc != MP_OK) return rc;
+    const int64_t nt0 = n - std::min<int64_t>(K, n);
+    BMat T = carve(ws, 1, nt0, nt0, L);                    // trailing product, ld = nt0
+    BMat y = carve(ws, 1, n, 1, L);
+    int64_t *perm = (int64_t *)ws.take((size_t)n * 8);
+    const BMat A0 = bmat(A);
+    dispatch(prec, [&](auto w) {
+        constexpr int WW = decltype(w)::value;
+        for (int64_t j0 = 0; j0 < n && rc == MP_OK; j0 += K) {
+            const int64_t je = std::min<int64_t>(j0 + K, n);
+            {
+                Prof pr(MP_K_LU, (double)(je - j0) * (n - j0), s);
+                for (int64_t k = j0; k < je; ++k) {
+                    launch_lu_pivot<WW>(A0, n, k, piv, prec, st, s);
+                    launch_lu_divide<WW>(A0, n, k, prec, s);
+                    launch_lu_rank1<WW>(A0, k, k + 1, n, k + 1, je, prec, st, s);
+                }
+            }
+            if (je >= n) break;
+            {
+                Prof pr(MP_K_LU, (double)(je - j0) * (je - j0) * (n - je) / 2, s);
+                for (int64_t r = j0; r + 1 < je; ++r)          // U12 = L11^-1 A12
+                    launch_lu_rank1<WW>(A0, r, r + 1, je, je, n, prec, st, s);
+            }
+            const int64_t nt = n - je;
+            BMat Tv = T;
+            Tv.ld = nt;
+            Tv.plane = nt * nt;
+            rc = gemm_core(algo, cutoff, policy, nt, je - j0, nt, prec, sub_view(A0, je, j0),
+                           sub_view(A0, j0, je), Tv, ws, st, s);
+            {
+                Prof pr(MP_K_LU, (double)nt * nt, s);
+                const BMat A22 = sub_view(A0, je, je);
+                launch_elementwise<WW>(1, A22, Tv, A22, nt, nt, prec, st, s);
+            }
+        }
+        if (rc == MP_OK && x) {
+            Prof pr(MP_K_LU, (double)n * n, s);
+            launch_lu_solve<WW>(A0, n, piv, bmat(b), y, bmat(x), perm, prec, st, s);
+        }
+    });
+    if (rc != MP_OK) return rc;
+    return launch_status();
 }
 
 }  // extern "C"

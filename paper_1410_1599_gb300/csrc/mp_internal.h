@@ -70,4 +70,18 @@ void launch_border(BMat A, BMat B, BMat C, int64_t nodes, int64_t m, int64_t l, 
                    int64_t mr, bool last_row, bool last_col, int p, DevStatus *st,
                    cudaStream_t s);
 
+// LU (Sec. 4): pivot search + row exchange of column k; l_ik = a_ik / a_kk;
+// one elimination step a_ij -= a_ik a_kj on [r0, r1) x [c0, c1); solves
+template <int W>
+void launch_lu_pivot(BMat A, int64_t n, int64_t k, int64_t *piv, int p, DevStatus *st,
+                     cudaStream_t s);
+template <int W>
+void launch_lu_divide(BMat A, int64_t n, int64_t k, int p, cudaStream_t s);
+template <int W>
+void launch_lu_rank1(BMat A, int64_t k, int64_t r0, int64_t r1, int64_t c0, int64_t c1, int p,
+                     DevStatus *st, cudaStream_t s);
+template <int W>
+void launch_lu_solve(BMat LU, int64_t n, const int64_t *piv, BMat b, BMat y, BMat x,
+                     int64_t *perm, int p, DevStatus *st, cudaStream_t s);
+
 }  // namespace mpg
