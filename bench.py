@@ -76,6 +76,14 @@ class ClockSampler:
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            return
+        # nvidia-smi's start-up can stall the driver: wait for its first sample
+        t0 = time.time()
+        while time.time() - t0 < 10.0:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.05)
+        time.sleep(0.3)
 
     def stop(self):
         if self.proc is None:
@@ -151,7 +159,6 @@ def run_ours(a, rank, world, local):
     barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    time.sleep(0.3)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)

@@ -124,32 +124,42 @@ template <int W>
 MP_DEV void round_mant(uint32_t (&m)[W], int64_t &e, uint32_t below, bool sticky,
                        const RoundSpec &rs)
 {
-    uint32_t rbit, st;
     if (rs.r == 0) {
-        rbit = below >> 31;
-        st = (below << 1) | (sticky ? 1u : 0u);
-    } else {
-        // round bit is bit r-1 of m; sticky is everything under it
-        const int q = rs.r - 1;
-        const int qw = q >> 5, qb = q & 31;
-        rbit = 0u;
-        st = below | (sticky ? 1u : 0u);
+        // p = 32 W: the kept LSB is bit 0 of m[0]; the round bit tops `below`
+        const uint32_t rbit = below >> 31;
+        const uint32_t st = (below << 1) | (sticky ? 1u : 0u);
+        const uint32_t up = rbit & ((st != 0u) | (m[0] & 1u));
+        m[0] = add_cc(m[0], up);
 #pragma unroll
-        for (int i = 0; i < W; ++i) {
-            uint32_t w = m[i];
-            if (i == qw) {
-                rbit = (w >> qb) & 1u;
-                st |= w & ((1u << qb) - 1u);
-            } else if (i < qw) {
-                st |= w;
-            }
+        for (int i = 1; i < W; ++i) m[i] = addc_cc(m[i], 0u);
+        const uint32_t c = addc(0u, 0u);
+        if (c) {   // carried out of the top: m was all ones
+            m[W - 1] = 0x80000000u;
+            e += 1;
         }
-        // clear the bits under the kept LSB (bit r)
+        return;
+    }
+    uint32_t rbit, st;
+    // round bit is bit r-1 of m; sticky is everything under it
+    const int q = rs.r - 1;
+    const int qw = q >> 5, qb = q & 31;
+    rbit = 0u;
+    st = below | (sticky ? 1u : 0u);
 #pragma unroll
-        for (int i = 0; i < W; ++i) {
-            if (i < rs.rw) m[i] = 0u;
-            else if (i == rs.rw) m[i] &= ~((1u << rs.rb) - 1u);
+    for (int i = 0; i < W; ++i) {
+        uint32_t w = m[i];
+        if (i == qw) {
+            rbit = (w >> qb) & 1u;
+            st |= w & ((1u << qb) - 1u);
+        } else if (i < qw) {
+            st |= w;
         }
+    }
+    // clear the bits under the kept LSB (bit r)
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        if (i < rs.rw) m[i] = 0u;
+        else if (i == rs.rw) m[i] &= ~((1u << rs.rb) - 1u);
     }
     uint32_t lsb = 0u;
 #pragma unroll
@@ -258,18 +268,21 @@ MP_DEV void mul_impl(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, const RoundSpec &
     if constexpr (W <= 16) {
         uint32_t P[2 * W];
         mul_full<W>(P, a.m, b.m);
-        if (!(P[2 * W - 1] >> 31)) {          // product in [1/4, 1/2): shift left one
-#pragma unroll
-            for (int i = 2 * W - 1; i > 0; --i) P[i] = (P[i] << 1) | (P[i - 1] >> 31);
-            P[0] <<= 1;
-            e -= 1;
-        }
         uint32_t low = 0u;
 #pragma unroll
-        for (int i = 0; i < W - 1; ++i) low |= P[i];
+        for (int i = 0; i < W - 2; ++i) low |= P[i];
+        uint32_t below = P[W - 1], below2 = P[W - 2];
+        if (!(P[2 * W - 1] >> 31)) {          // product in [1/4, 1/2): shift left one
+#pragma unroll
+            for (int i = 2 * W - 1; i > W; --i) P[i] = __funnelshift_l(P[i - 1], P[i], 1);
+            P[W] = __funnelshift_l(below, P[W], 1);
+            below = __funnelshift_l(below2, below, 1);
+            below2 <<= 1;
+            e -= 1;
+        }
 #pragma unroll
         for (int i = 0; i < W; ++i) r.m[i] = P[W + i];
-        round_mant<W>(r.m, e, P[W - 1], low != 0u, rs);
+        round_mant<W>(r.m, e, below, (low | below2) != 0u, rs);
     } else {
         uint32_t pw1, pw2;
         bool low_nz;
@@ -289,21 +302,31 @@ MP_DEV void mul_impl(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, const RoundSpec &
 }
 
 // --------------------------------------------------------------- add / sub
+// largest value of v among the converged lanes (a warp-uniform bound)
+MP_DEV int warp_max(int v)
+{
+    return (int)__reduce_max_sync(__activemask(), (unsigned)v);
+}
+
 // x (N words) >>= sh bits, 0 <= sh <= 32N; returns the OR of the bits
-// shifted out.  Branch-free: a select network over the word shift.
+// shifted out.  A select network over the word shift; stages no lane of the
+// warp needs are skipped (warp-uniform branch).
 template <int N>
 MP_DEV uint32_t shr_sticky(uint32_t (&x)[N], int sh)
 {
     const int q = sh >> 5, b = sh & 31;
+    const int qmax = warp_max(q);
     uint32_t st = 0u;
 #pragma unroll
     for (int j = 0; (1 << j) <= N; ++j) {
         const int d = 1 << j;
-        const bool on = (q >> j) & 1;
+        if (qmax >= d) {
+            const bool on = (q >> j) & 1;
 #pragma unroll
-        for (int i = 0; i < d && i < N; ++i) st |= on ? x[i] : 0u;
+            for (int i = 0; i < d && i < N; ++i) st |= on ? x[i] : 0u;
 #pragma unroll
-        for (int i = 0; i < N; ++i) x[i] = on ? ((i + d < N) ? x[i + d] : 0u) : x[i];
+            for (int i = 0; i < N; ++i) x[i] = on ? ((i + d < N) ? x[i + d] : 0u) : x[i];
+        }
     }
     st |= x[0] & ((1u << b) - 1u);
 #pragma unroll
@@ -317,12 +340,15 @@ template <int N>
 MP_DEV void shl(uint32_t (&x)[N], int sh)
 {
     const int q = sh >> 5, b = sh & 31;
+    const int qmax = warp_max(q);
 #pragma unroll
     for (int j = 0; (1 << j) < N; ++j) {
         const int d = 1 << j;
-        const bool on = (q >> j) & 1;
+        if (qmax >= d) {
+            const bool on = (q >> j) & 1;
 #pragma unroll
-        for (int i = N - 1; i >= 0; --i) x[i] = on ? ((i - d >= 0) ? x[i - d] : 0u) : x[i];
+            for (int i = N - 1; i >= 0; --i) x[i] = on ? ((i - d >= 0) ? x[i - d] : 0u) : x[i];
+        }
     }
 #pragma unroll
     for (int i = N - 1; i > 0; --i) x[i] = __funnelshift_l(x[i - 1], x[i], b);
@@ -333,6 +359,7 @@ MP_DEV void shl(uint32_t (&x)[N], int sh)
 template <int N>
 MP_DEV int clz_words(const uint32_t (&x)[N])
 {
+    if (__all_sync(__activemask(), x[N - 1] != 0u)) return __clz(x[N - 1]);
     int lz = 0;
     bool found = false;
 #pragma unroll
@@ -346,6 +373,14 @@ MP_DEV int clz_words(const uint32_t (&x)[N])
 }
 
 // r = RN_p(x + (-1)^neg_y * y).  r may alias x or y.
+//
+// X is the operand of larger magnitude (exponent, then mantissa), so the
+// effective subtraction never goes negative.  Y is aligned to X with a guard
+// word and a sticky bit.  One carry chain serves both cases: the effective
+// subtraction adds the complement of Y with carry-in 1 - sticky (the sticky
+// borrow stands for the nonzero bits of Y below the guard word).  The result
+// is renormalised by one bit to the right (carry out of an addition) or by
+// the leading-zero count to the left (cancellation), then rounded once.
 template <int W>
 MP_DEV void add_impl(Mp<W> &r, const Mp<W> &x, const Mp<W> &y, uint32_t neg_y, const RoundSpec &rs)
 {
@@ -366,8 +401,13 @@ MP_DEV void add_impl(Mp<W> &r, const Mp<W> &x, const Mp<W> &y, uint32_t neg_y, c
         }
         return;
     }
-    // X: the operand with the larger exponent
-    const bool sw = y.e > x.e;
+    // |y| > |x| ?  exponents first, mantissas on a tie (borrow of x.m - y.m)
+    uint32_t t = sub_cc(x.m[0], y.m[0]);
+#pragma unroll
+    for (int i = 1; i < W; ++i) t = subc_cc(x.m[i], y.m[i]);
+    const uint32_t mlt = subc(0u, 0u);           // all ones if x.m < y.m
+    (void)t;
+    const bool sw = (y.e > x.e) || (y.e == x.e && mlt != 0u);
     uint32_t X[W + 1], Y[W + 1];
     X[0] = 0u;
     Y[0] = 0u;
@@ -376,53 +416,31 @@ MP_DEV void add_impl(Mp<W> &r, const Mp<W> &x, const Mp<W> &y, uint32_t neg_y, c
         X[i + 1] = sw ? y.m[i] : x.m[i];
         Y[i + 1] = sw ? x.m[i] : y.m[i];
     }
-    const int64_t ex = sw ? y.e : x.e;
+    int64_t e = sw ? y.e : x.e;
     const int64_t d64 = sw ? (y.e - x.e) : (x.e - y.e);
-    uint32_t sx = sw ? ys : x.s;
-    const uint32_t sy = sw ? x.s : ys;
+    const uint32_t sx = sw ? ys : x.s;
+    const uint32_t eff_sub = (x.s ^ ys) & 1u;
     const int d = d64 > 32 * (W + 1) ? 32 * (W + 1) : (int)d64;
     const uint32_t st = shr_sticky<W + 1>(Y, d);
-    int64_t e = ex;
+    // S = X + (Y ^ mask) + cin; the first add only loads cin into the carry flag
+    const uint32_t mask = 0u - eff_sub;
+    const uint32_t cin = eff_sub & (st == 0u ? 1u : 0u);
     uint32_t S[W + 1];
-    if (sx == sy) {
-        S[0] = add_cc(X[0], Y[0]);
+    (void)add_cc(cin, 0xffffffffu);
 #pragma unroll
-        for (int i = 1; i <= W; ++i) S[i] = addc_cc(X[i], Y[i]);
-        const uint32_t carry = addc(0u, 0u);
-        bool sticky = st != 0u;
-        if (carry) {
-            sticky |= (S[0] & 1u) != 0u;
+    for (int i = 0; i <= W; ++i) S[i] = addc_cc(X[i], Y[i] ^ mask);
+    const uint32_t carry = addc(0u, 0u);
+    // effective addition with a carry out: shift right by one
+    const uint32_t rsh = (eff_sub ^ 1u) & carry & 1u;
+    bool sticky = st != 0u;
+    sticky |= (rsh & S[0] & 1u) != 0u;
 #pragma unroll
-            for (int i = 0; i < W; ++i) S[i] = __funnelshift_r(S[i], S[i + 1], 1);
-            S[W] = (S[W] >> 1) | 0x80000000u;
-            e += 1;
-        }
-#pragma unroll
-        for (int i = 0; i < W; ++i) r.m[i] = S[i + 1];
-        round_mant<W>(r.m, e, S[0], sticky, rs);
-        r.e = e;
-        r.s = sx;
-        return;
-    }
-    // effective subtraction: S = X - Y - [sticky]; the sticky borrow stands for
-    // the nonzero bits of y shifted out below the guard word
-    S[0] = sub_cc(X[0], Y[0]);
-#pragma unroll
-    for (int i = 1; i <= W; ++i) S[i] = subc_cc(X[i], Y[i]);
-    const uint32_t borrow = subc(0u, 0u);     // 0xffffffff if X < Y (only when d == 0)
-    if (st) {
-        S[0] = sub_cc(S[0], 1u);
-#pragma unroll
-        for (int i = 1; i <= W; ++i) S[i] = subc_cc(S[i], 0u);
-    }
-    if (borrow) {                             // |y| > |x| at equal exponents: negate
-        S[0] = sub_cc(0u, S[0]);
-#pragma unroll
-        for (int i = 1; i <= W; ++i) S[i] = subc_cc(0u, S[i]);
-        sx ^= 1u;
-    }
+    for (int i = 0; i < W; ++i) S[i] = __funnelshift_r(S[i], S[i + 1], rsh);
+    S[W] = __funnelshift_r(S[W], rsh, rsh);      // the carry bit enters at the top
+    e += rsh;
+    // cancellation shifts left (an effective addition has lz = 0 here)
     const int lz = clz_words<W + 1>(S);
-    if (lz == 32 * (W + 1)) {                 // exact cancellation: +0
+    if (lz == 32 * (W + 1)) {                     // exact cancellation: +0
         set_zero<W>(r, 0u);
         return;
     }
@@ -430,7 +448,7 @@ MP_DEV void add_impl(Mp<W> &r, const Mp<W> &x, const Mp<W> &y, uint32_t neg_y, c
     e -= lz;
 #pragma unroll
     for (int i = 0; i < W; ++i) r.m[i] = S[i + 1];
-    round_mant<W>(r.m, e, S[0], st != 0u, rs);
+    round_mant<W>(r.m, e, S[0], sticky, rs);
     r.e = e;
     r.s = sx;
 }
