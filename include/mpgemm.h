@@ -85,7 +85,8 @@ enum {
     MP_ERR_TIMEOUT     = -4,   /* a device-side wait gave up */
     MP_ERR_CUDA        = -5,   /* a CUDA runtime call failed */
     MP_ERR_RANGE       = -6,   /* an exponent left [-2^62, 2^62] */
-    MP_ERR_UNSUPPORTED = -7
+    MP_ERR_UNSUPPORTED = -7,
+    MP_ERR_SCRATCH     = -8    /* mpgemm_noalloc: needs more than the static scratch */
 };
 
 /* ---- per-thread settings ------------------------------------------------ */
@@ -135,6 +136,37 @@ size_t mpgemm_workspace_size(int64_t m, int64_t l, int64_t n, int32_t prec,
  */
 int mpgemm(int64_t m, int64_t l, int64_t n, int32_t prec, int32_t algo, int32_t cutoff,
            const mpmat_t *A, const mpmat_t *B, mpmat_t *C);
+
+/*
+ * mpgemm_noalloc -- the same product as mpgemm, for callers that cannot
+ * allocate device memory when they multiply (work issued while a stream is
+ * being captured into a CUDA graph, serving loops that must not touch an
+ * allocator, hosts whose device memory is owned elsewhere).  The paper has
+ * no counterpart: it is a deployment variant, not part of the method.
+ *
+ * It allocates nothing: Strassen/Winograd temporaries live in one
+ * file-scope static device array of MP_NOALLOC_SCRATCH_BYTES (64 MiB), which
+ * every GPU that loads the library holds until the process exits; Simple
+ * and Block need none.  Arguments, results and the per-thread stream and
+ * odd-dimension policy are those of mpgemm; the caller still provides A, B
+ * and C.
+ *   - A product whose recursion needs more than the array holds is rejected
+ *     with MP_ERR_SCRATCH before anything is launched (Winograd with cutoff
+ *     64 fits n = 200 at 512 bits and n = 256 at 256 bits, not n = 256 at
+ *     512 bits).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) once; make that first call before any stream
+ *     capture.
+ *   - Every call uses the same array and leaves its contents behind; the
+ *     recursion writes every temporary before reading it.  Calls whose work
+ *     overlaps on the GPU (other streams, other host threads) race on the
+ *     array: serialise them.
+ *   - Exponent-range overflow is not recorded for mp_sync_status() by this
+ *     entry point (the status word would need allocated memory).
+ */
+#define MP_NOALLOC_SCRATCH_BYTES (64u << 20)
+int mpgemm_noalloc(int64_t m, int64_t l, int64_t n, int32_t prec, int32_t algo, int32_t cutoff,
+                   const mpmat_t *A, const mpmat_t *B, mpmat_t *C);
 
 /* ---- LU decomposition and solve (Sec. 4) -------------------------------- */
 

@@ -23,13 +23,15 @@ OP_ADD, OP_SUB, OP_MUL, OP_DIV = 0, 1, 2, 3
 
 MP_OK = 0
 ERRORS = {-1: "MP_ERR_ARG", -2: "MP_ERR_NOMEM", -3: "MP_ERR_SINGULAR", -4: "MP_ERR_TIMEOUT",
-          -5: "MP_ERR_CUDA", -6: "MP_ERR_RANGE", -7: "MP_ERR_UNSUPPORTED"}
+          -5: "MP_ERR_CUDA", -6: "MP_ERR_RANGE", -7: "MP_ERR_UNSUPPORTED", -8: "MP_ERR_SCRATCH"}
+NOALLOC_SCRATCH_BYTES = 64 << 20
 
 # every symbol include/mpgemm.h declares
 EXPORTS = ["mp_set_stream", "mp_set_workspace", "mp_set_odd_policy", "mp_set_lu",
            "mp_elementwise", "mp_convert", "mpgemm_workspace_size", "mpgemm",
            "mplu_workspace_size", "mplu", "mp_sync_status", "mp_singular_column",
-           "mp_strerror", "mp_version", "mp_profile_enable", "mp_profile_read"]
+           "mp_strerror", "mp_version", "mp_profile_enable", "mp_profile_read",
+           "mpgemm_noalloc"]
 
 K_LEAF, K_SIMPLE, K_OPERANDS, K_COMBINE, K_FIXUP, K_ELEMENTWISE, K_LU = range(7)
 K_NAMES = ["leaf_gemm", "simple_gemm", "operands", "combine", "fixup", "elementwise", "lu"]
@@ -66,6 +68,9 @@ def load_library(path: str = LIB_PATH):
             lib.mplu_workspace_size.argtypes = [C.c_int64, C.c_int32]
             lib.mpgemm.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.c_int32, C.c_int32,
                                    C.c_int32, C.POINTER(MPMat), C.POINTER(MPMat), C.POINTER(MPMat)]
+            lib.mpgemm_noalloc.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.c_int32, C.c_int32,
+                                           C.c_int32, C.POINTER(MPMat), C.POINTER(MPMat),
+                                           C.POINTER(MPMat)]
             lib.mplu.argtypes = [C.c_int64, C.c_int32, C.POINTER(MPMat), C.c_void_p,
                                  C.POINTER(MPMat), C.POINTER(MPMat)]
             lib.mp_elementwise.argtypes = [C.c_int, C.POINTER(MPMat), C.POINTER(MPMat),
@@ -207,6 +212,15 @@ def mpgemm(A: DeviceMP, B: DeviceMP, C_: DeviceMP, algo: int = SIMPLE, cutoff: i
     a, b, c = A.struct(), B.struct(), C_.struct()
     _check(load_library().mpgemm(A.rows, A.cols, B.cols, A.p, algo, cutoff, C.byref(a),
                                  C.byref(b), C.byref(c)), "mpgemm")
+
+
+def mpgemm_noalloc(A: DeviceMP, B: DeviceMP, C_: DeviceMP, algo: int = WINOGRAD,
+                   cutoff: int = 64) -> None:
+    """mpgemm with the recursion's temporaries in the library's static device
+    scratch (no allocation); see include/mpgemm.h."""
+    a, b, c = A.struct(), B.struct(), C_.struct()
+    _check(load_library().mpgemm_noalloc(A.rows, A.cols, B.cols, A.p, algo, cutoff, C.byref(a),
+                                         C.byref(b), C.byref(c)), "mpgemm_noalloc")
 
 
 def mplu(A: DeviceMP, piv, b: DeviceMP | None, x: DeviceMP | None) -> None:

@@ -404,6 +404,44 @@ BMat sub_view(BMat M, int64_t r0, int64_t c0)
 
 }  // namespace
 
+namespace mpg {
+// C := A B with the recursion's buffers carved from a caller-supplied device
+// block [base, base + bytes); nothing is allocated.  Returns MP_ERR_NOMEM if
+// the block is too small.  Used by the static-scratch entry point.
+int gemm_in_block(int algo, int cutoff, int policy, int64_t m, int64_t l, int64_t n, int p,
+                  const mpmat_t *A, const mpmat_t *B, mpmat_t *C, void *base, size_t bytes,
+                  cudaStream_t s)
+{
+    const size_t need = gemm_ws_bytes(algo, m, l, n, cutoff, policy, limbs_of(p));
+    if (need > bytes) return MP_ERR_NOMEM;
+    Workspace ws;
+    ws.base = (char *)base;
+    ws.size = bytes;
+    ws.used = 0;
+    ws.s = s;
+    return gemm_core(algo, cutoff, policy, m, l, n, p, bmat(A), bmat(B), bmat(C), ws, nullptr, s);
+}
+
+size_t gemm_scratch_bytes(int algo, int64_t m, int64_t l, int64_t n, int cutoff, int policy, int p)
+{
+    return gemm_ws_bytes(algo, m, l, n, cutoff, policy, limbs_of(p));
+}
+
+bool gemm_args_ok(int64_t m, int64_t l, int64_t n, int32_t prec, int32_t algo, int32_t cutoff,
+                  const mpmat_t *A, const mpmat_t *B, const mpmat_t *C)
+{
+    if (!valid_prec(prec) || m < 0 || l < 0 || n < 0) return false;
+    if (algo < MP_SIMPLE || algo > MP_WINOGRAD) return false;
+    if ((algo == MP_STRASSEN || algo == MP_WINOGRAD) && cutoff < 1) return false;
+    if (!valid_mat(A, m, l, prec) || !valid_mat(B, l, n, prec) || !valid_mat(C, m, n, prec))
+        return false;
+    return !(overlaps(C, A) || overlaps(C, B));
+}
+
+cudaStream_t current_stream() { return g_ts.stream; }
+int current_odd_policy() { return g_ts.odd_policy; }
+}  // namespace mpg
+
 // ======================================================================= ABI
 extern "C" {
 
@@ -449,6 +487,7 @@ const char *mp_strerror(int status)
     case MP_ERR_CUDA: return "CUDA runtime error";
     case MP_ERR_RANGE: return "exponent out of range";
     case MP_ERR_UNSUPPORTED: return "unsupported";
+    case MP_ERR_SCRATCH: return "product needs more than the static scratch array holds";
     default: return "unknown status";
     }
 }
