@@ -40,6 +40,9 @@ def parse():
     ap.add_argument("--cutoff", type=int, default=64)
     ap.add_argument("--no-extras", action="store_true", help="skip the other algorithms and the CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--lu-n", type=int, default=1024)
+    ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--serve", action="store_true", help="only the serving run (its own JSON line)")
     return ap.parse_args()
 
 
@@ -214,7 +217,7 @@ def run_ours(a, rank, world, local):
     e2e_ms = allmax(e0.elapsed_time(e1) / e2e_steps)
     mp.check_status("e2e")
 
-    extras = {}
+    extras, extras_lu, serving = {}, None, None
     if not a.no_extras and rank == 0:
         for name in ("simple", "block", "strassen", "winograd"):
             if name == a.algo:
@@ -232,6 +235,10 @@ def run_ours(a, rank, world, local):
             torch.cuda.synchronize()
             extras[name] = round(flops / (e0.elapsed_time(e1) * 1e-3) / 1e9, 3)
         mp.check_status("extras")
+        extras_lu = [lu_run(a.lu_n, 256, mp.WINOGRAD), lu_run(a.lu_n, 256, mp.SIMPLE)]
+        mp.set_stream(stream)
+        serving = serve_run(a.serve_requests)
+        mp.set_stream(stream)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_extras:
@@ -261,10 +268,168 @@ def run_ours(a, rank, world, local):
             line["speedup_vs_simple"] = round(extras.get(a.algo, value) / extras["simple"], 3)
         if cpu:
             line["cpu_baseline"] = cpu
+        if extras_lu:
+            line["lu"] = extras_lu
+        if serving:
+            line["serving"] = serving
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def lu_run(n, p, algo, panel=128, cutoff=64, kind="well"):
+    """One MP LU solve of A x = b, b = A * ones (Simple product), on the GPU:
+    seconds, and the backward / forward errors computed by the library at 2p."""
+    import numpy as np
+    import torch
+
+    from paper_1410_1599_gb300 import binding as mp
+    from paper_1410_1599_gb300 import inputs as gen
+
+    A = gen.well_conditioned(n, p, 5) if kind == "well" else gen.lotkin(n, p)
+    dA = mp.DeviceMP.from_host(A)
+    dA0 = mp.DeviceMP.from_host(A)
+    ones = mp.DeviceMP.from_host(gen.ones(n, 1, p))
+    db = mp.DeviceMP.empty(n, 1, p)
+    mp.mpgemm(dA0, ones, db, mp.SIMPLE)
+    dx = mp.DeviceMP.empty(n, 1, p)
+    piv = torch.zeros(n, dtype=torch.int64, device="cuda")
+    mp.set_lu(panel, algo, cutoff)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mp.mplu(dA, piv, db, dx)
+    rc = mp.sync_status()
+    t = time.perf_counter() - t0
+    mp.set_lu(128, mp.SIMPLE, 64)
+    # residual r = b - A x at 2p (exact widening, Simple product, one subtraction)
+    q = 2 * p
+    wA, wx, wb = (mp.DeviceMP.empty(r, c, q) for r, c in ((n, n), (n, 1), (n, 1)))
+    mp.convert(dA0, wA)
+    mp.convert(dx, wx)
+    mp.convert(db, wb)
+    Ax = mp.DeviceMP.empty(n, 1, q)
+    mp.mpgemm(wA, wx, Ax, mp.SIMPLE)
+    r = mp.DeviceMP.empty(n, 1, q)
+    mp.elementwise(mp.OP_SUB, wb, Ax, r)
+    one = mp.DeviceMP.from_host(gen.ones(n, 1, q))
+    fe = mp.DeviceMP.empty(n, 1, q)
+    mp.elementwise(mp.OP_SUB, wx, one, fe)
+    mp.check_status("lu residual")
+
+    def dbl(M):
+        H = M.to_host()
+        f = H.limb[0].astype(np.float64) * 2.0 ** -64
+        e = np.where(H.exp == gen.EXP_ZERO, -10 ** 6, H.exp).clip(-1000, 1000)
+        v = f * np.exp2(e.astype(np.float64))
+        return np.where(H.sign == 1, -v, v)
+
+    a = np.abs(dbl(dA0)).sum(axis=1).max()
+    xn = np.abs(dbl(dx)).max()
+    bn = np.abs(dbl(db)).max()
+    back = float(np.abs(dbl(r)).max() / (a * xn + bn))
+    fwd = float(np.abs(dbl(fe)).max())
+    return {"n": n, "prec": p, "algo": {0: "simple", 1: "block", 2: "strassen", 3: "winograd"}[algo],
+            "panel": panel, "matrix": kind, "seconds": round(t, 4), "status": rc,
+            "eff_gflops": round((2.0 / 3.0) * n ** 3 / t / 1e9, 4),
+            "backward_error": back, "forward_error": fwd}
+
+
+def serve_run(n_req, seed=11, slots=8, budget=150 << 30):
+    """Config-5 style request stream through the library's serving loop:
+    70% GEMM (m, l, n ~ U{16..2048}), 30% LU solve (n ~ U{64..1024}),
+    precision ~ U{128, 256, 512, 1024, 2048}; operands are tiles of per-precision
+    pools of seeded U[-1,1)*2^e entries.  Phase 1 submits everything at once
+    (capacity, requests/s); phase 2 replays a Poisson stream at 0.7 x capacity
+    and reports latency percentiles."""
+    import numpy as np
+
+    from paper_1410_1599_gb300 import binding as mp
+    from paper_1410_1599_gb300 import inputs as gen
+
+    rng = np.random.default_rng(seed)
+    precs = [128, 256, 512, 1024, 2048]
+    pool = {p: gen.uniform_pm1(512, 512, p, 77 + p, -16, 16) for p in precs}
+
+    def tile(p, rows, cols, off):
+        P = pool[p]
+        ri = (np.arange(rows) + off) % 512
+        ci = (np.arange(cols) + 3 * off) % 512
+        return P.sub(ri, ci)
+
+    specs = []
+    for i in range(n_req):
+        p = int(rng.choice(precs))
+        if rng.random() < 0.7:
+            m, l, n = (int(x) for x in rng.integers(16, 2049, 3))
+            algo = mp.WINOGRAD if min(m, l, n) > 128 else mp.BLOCK
+            specs.append(("gemm", i, p, (m, l, n), algo, int(rng.integers(0, 512))))
+        else:
+            n = int(rng.integers(64, 1025))
+            specs.append(("lu", i, p, (n,), mp.WINOGRAD if n > 256 else mp.SIMPLE, int(rng.integers(0, 512))))
+
+    def make(spec):
+        kind, i, p, dims, algo, off = spec
+        if kind == "gemm":
+            m, l, n = dims
+            return tile(p, m, l, off), tile(p, l, n, off + 7)
+        n = dims[0]
+        A = tile(p, n, n, off)
+        q = p - n.bit_length() - 2          # diagonal n + v exact in p bits (as well_conditioned)
+        D = gen.from_exact_ints([((n << q) + k < 0, abs((n << q) + k), q) for k in
+                                 (gen.rand_bits(seed + i, j, q + 1) - (1 << q) for j in range(n))], p, (1, n))
+        for j in range(n):
+            A.limb[:, j, j] = D.limb[:, 0, j]
+            A.exp[j, j] = D.exp[0, j]
+            A.sign[j, j] = D.sign[0, j]
+        return A, tile(p, n, 1, off + 11)
+
+    inputs = [make(s) for s in specs]
+    flops = [2.0 * s[3][0] * s[3][1] * s[3][2] if s[0] == "gemm" else (2.0 / 3.0) * s[3][0] ** 3
+             for s in specs]
+
+    def submit(srv, s, X, Y):
+        kind, i, p, dims, algo, off = s
+        if kind == "gemm":
+            return srv.submit_gemm(i, X, Y, algo=algo, cutoff=64)
+        return srv.submit_lu(i, X, Y, algo=algo, cutoff=64, panel=128)
+
+    # phase 1: closed loop, all at once
+    srv = mp.Server(budget_bytes=budget, slots=slots)
+    t0 = time.perf_counter()
+    for s, (X, Y) in zip(specs, inputs):
+        assert submit(srv, s, X, Y) == 0
+    srv.drain()
+    t_cap = time.perf_counter() - t0
+    st1 = srv.stats()
+    srv.close()
+    cap = n_req / t_cap
+    # phase 2: Poisson arrivals at 0.7 x capacity
+    lam = 0.7 * cap
+    gaps = rng.exponential(1.0 / lam, n_req)
+    srv = mp.Server(budget_bytes=budget, slots=slots)
+    t0 = time.perf_counter()
+    due = t0
+    for s, (X, Y), g in zip(specs, inputs, gaps):
+        due += g
+        while time.perf_counter() < due:
+            time.sleep(min(0.002, max(0.0, due - time.perf_counter())))
+        assert submit(srv, s, X, Y) == 0
+    srv.drain()
+    t_run = time.perf_counter() - t0
+    st2 = srv.stats()
+    lat = np.array([srv.results[i][1] for i in range(n_req)])
+    ok = all(srv.results[i][0] == mp.REQ_DONE for i in range(n_req))
+    srv.close()
+    return {"requests": n_req, "mix": "70% GEMM m,l,n~U{16..2048}, 30% LU n~U{64..1024}, p~U{128..2048}",
+            "slots": slots, "budget_gb": budget / 2 ** 30, "all_done": ok,
+            "capacity_req_per_s": round(cap, 3), "offered_req_per_s": round(lam, 3),
+            "throughput_req_per_s": round(n_req / t_run, 3),
+            "eff_gflops_closed_loop": round(sum(flops) / t_cap / 1e9, 3),
+            "p50_ms": round(float(np.percentile(lat, 50)), 2),
+            "p99_ms": round(float(np.percentile(lat, 99)), 2),
+            "batches": st1["batches"], "batched_requests": st1["batched_requests"],
+            "peak_gb": round(max(st1["peak_bytes"], st2["peak_bytes"]) / 2 ** 30, 3)}
 
 
 def cpu_baseline(A, B, seconds):
@@ -341,6 +506,13 @@ def run_reference(a, rank, world):
 def main():
     a = parse()
     rank, world, local = dist_env()
+    if a.serve:
+        import torch
+        from paper_1410_1599_gb300 import build as libbuild
+        libbuild.build()
+        torch.cuda.set_device(local)
+        print(json.dumps({"serving": serve_run(a.serve_requests)}), flush=True)
+        return
     if a.impl == "reference":
         run_reference(a, rank, world)
     else:

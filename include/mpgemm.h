@@ -68,7 +68,10 @@ enum {
     MP_SIMPLE   = 0,   /* Eq. 1: c_ij = sum_k a_ik b_kj, k ascending */
     MP_BLOCK    = 1,   /* Eq. 2: blocked, same k-ascending sequence per c_ij */
     MP_STRASSEN = 2,   /* Strassen's P1..P7 recursion */
-    MP_WINOGRAD = 3    /* Winograd's variant, S1..S8 / M1..M7 / T1, T2 */
+    MP_WINOGRAD = 3,   /* Winograd's variant, S1..S8 / M1..M7 / T1, T2 */
+    MP_EXACT    = 4    /* every c_ij the exact dot product, rounded once (the
+                          accuracy reference of Sec. 3's error tables; the
+                          result of the split form) */
 };
 
 /* handling of odd dimensions in the recursion (Sec. 2, last paragraph) */
@@ -126,12 +129,16 @@ size_t mpgemm_workspace_size(int64_t m, int64_t l, int64_t n, int32_t prec,
 
 /*
  * C := A B with A m x l, B l x n, C m x n, all of precision prec.
- *   algo   : MP_SIMPLE, MP_BLOCK, MP_STRASSEN or MP_WINOGRAD;
+ *   algo   : MP_SIMPLE, MP_BLOCK, MP_STRASSEN, MP_WINOGRAD or MP_EXACT;
  *   cutoff : Strassen/Winograd recurse while m, l and n all exceed it
  *            (n_min of Sec. 2, >= 1); below it the leaf product is Block.
  * Every c_ij of Simple/Block is (((+0 + a_i1 b_1j) + a_i2 b_2j) + ...) with
  * each product and sum rounded; Strassen/Winograd evaluate the printed
  * formulas left to right with one rounding per matrix add/sub element.
+ * MP_EXACT forms each dot product exactly in a fixed-point accumulator and
+ * rounds once; an exact zero sum is +0; a row/column pair whose products'
+ * exponents spread wider than the accumulator (about 2p bits) is left +0 and
+ * mp_sync_status() returns MP_ERR_UNSUPPORTED.
  * C must not overlap A or B (MP_ERR_ARG).  l = 0 gives C = +0.
  */
 int mpgemm(int64_t m, int64_t l, int64_t n, int32_t prec, int32_t algo, int32_t cutoff,
@@ -184,6 +191,74 @@ size_t mplu_workspace_size(int64_t n, int32_t prec);
  * A zero pivot makes mp_sync_status() return MP_ERR_SINGULAR.
  */
 int mplu(int64_t n, int32_t prec, mpmat_t *A, int64_t *piv, const mpmat_t *b, mpmat_t *x);
+
+/* ---- serving: continuous batching of GEMM and LU-solve requests ---------- */
+
+/*
+ * A request loop for mixed MP GEMM and LU-solve requests (sizes and
+ * precisions vary per request).  Requests are queued as they arrive and
+ * admitted while the device memory they need fits the server's budget and a
+ * slot (a CUDA stream) is free; admitted work from different requests runs
+ * concurrently.  Small GEMMs of the same precision and size bucket (all of
+ * m, l, n <= 512; bucket = next of 64/128/256/512) that ask for Simple or
+ * Block are batched into one grouped Block launch, zero-padded to the
+ * bucket: the padding only appends exact zero products after each c_ij's
+ * k-ascending sequence, so a request's result is the same alone or batched.
+ * Every request's result depends only on the request (never on the mix).
+ *
+ * Host buffers use the interchange layout, contiguous: limb[L][rows][cols]
+ * (limb 0 most significant), exp[rows][cols], sign[rows][cols]; they must
+ * stay valid until the request completes.  Page-locked host memory gives
+ * asynchronous copies.
+ */
+typedef struct mp_server mp_server_t;
+
+enum { MP_REQ_GEMM = 0, MP_REQ_LU_SOLVE = 1 };
+enum { MP_REQ_DONE = 0, MP_REQ_PENDING = 1, MP_REQ_RUNNING = 2, MP_REQ_CANCELLED = 3,
+       MP_REQ_FAILED = 4 };
+
+typedef struct mp_request {
+    int64_t  id;          /* caller's tag, returned by mp_server_poll */
+    int32_t  kind;        /* MP_REQ_GEMM: C = A B (A m x l, B l x n);
+                             MP_REQ_LU_SOLVE: x = A^-1 b (A m x m, b m x 1; l, n ignored) */
+    int32_t  prec;
+    int64_t  m, l, n;
+    int32_t  algo;        /* GEMM algorithm, or the LU trailing-update algorithm */
+    int32_t  cutoff;
+    int32_t  lu_panel;    /* LU panel width (0: 128) */
+    int32_t  reserved;
+    const uint64_t *a_limb; const int64_t *a_exp; const int8_t *a_sign;
+    const uint64_t *b_limb; const int64_t *b_exp; const int8_t *b_sign;
+    uint64_t *c_limb; int64_t *c_exp; int8_t *c_sign;      /* C, or x for LU */
+} mp_request_t;
+
+/* A server on the current device with a device-memory budget (bytes) and a
+ * number of slots (concurrent streams, 1..64).  NULL on failure. */
+mp_server_t *mp_server_create(size_t budget_bytes, int slots);
+
+/* Queue a request (thread safe).  MP_ERR_ARG for a malformed request,
+ * MP_ERR_NOMEM if it could never fit the budget. */
+int mp_server_submit(mp_server_t *srv, const mp_request_t *req);
+
+/* Cancel a queued request that has not been admitted yet: MP_OK, or
+ * MP_ERR_ARG if it is unknown, running or finished. */
+int mp_server_cancel(mp_server_t *srv, int64_t id);
+
+/* Up to max finished requests since the last poll: ids, final status
+ * (MP_REQ_DONE / _CANCELLED / _FAILED) and latency in milliseconds from
+ * submission to completion.  Returns how many were written. */
+int mp_server_poll(mp_server_t *srv, int64_t *ids, int32_t *status, double *latency_ms, int max);
+
+/* Block until every submitted request has finished. */
+int mp_server_drain(mp_server_t *srv);
+
+/* Counters: [0] submitted, [1] completed, [2] batches launched, [3] requests
+ * that ran inside a multi-request batch, [4] peak device bytes in use,
+ * [5] budget, [6] currently running, [7] currently queued. */
+int mp_server_stats(mp_server_t *srv, int64_t out[8]);
+
+/* Drain, stop the scheduler thread and free the server. */
+void mp_server_destroy(mp_server_t *srv);
 
 /* ---- tracing -------------------------------------------------------------- */
 

@@ -17,7 +17,7 @@ from .inputs import EXP_ZERO, HostMP, limbs_for
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "lib", "libmpgemm.so")
 
-SIMPLE, BLOCK, STRASSEN, WINOGRAD = 0, 1, 2, 3
+SIMPLE, BLOCK, STRASSEN, WINOGRAD, EXACT = 0, 1, 2, 3, 4
 PEEL, MIXED = 0, 1
 OP_ADD, OP_SUB, OP_MUL, OP_DIV = 0, 1, 2, 3
 
@@ -31,7 +31,11 @@ EXPORTS = ["mp_set_stream", "mp_set_workspace", "mp_set_odd_policy", "mp_set_lu"
            "mp_elementwise", "mp_convert", "mpgemm_workspace_size", "mpgemm",
            "mplu_workspace_size", "mplu", "mp_sync_status", "mp_singular_column",
            "mp_strerror", "mp_version", "mp_profile_enable", "mp_profile_read",
-           "mpgemm_noalloc"]
+           "mpgemm_noalloc", "mp_server_create", "mp_server_submit", "mp_server_cancel",
+           "mp_server_poll", "mp_server_drain", "mp_server_stats", "mp_server_destroy"]
+
+REQ_GEMM, REQ_LU_SOLVE = 0, 1
+REQ_DONE, REQ_PENDING, REQ_RUNNING, REQ_CANCELLED, REQ_FAILED = 0, 1, 2, 3, 4
 
 K_LEAF, K_SIMPLE, K_OPERANDS, K_COMBINE, K_FIXUP, K_ELEMENTWISE, K_LU = range(7)
 K_NAMES = ["leaf_gemm", "simple_gemm", "operands", "combine", "fixup", "elementwise", "lu"]
@@ -47,6 +51,16 @@ class MPMat(C.Structure):
     _fields_ = [("prec", C.c_int32), ("reserved", C.c_int32), ("rows", C.c_int64),
                 ("cols", C.c_int64), ("ld", C.c_int64), ("plane", C.c_int64),
                 ("limb", C.c_void_p), ("exp", C.c_void_p), ("sign", C.c_void_p)]
+
+
+class MPRequest(C.Structure):
+    _fields_ = [("id", C.c_int64), ("kind", C.c_int32), ("prec", C.c_int32),
+                ("m", C.c_int64), ("l", C.c_int64), ("n", C.c_int64),
+                ("algo", C.c_int32), ("cutoff", C.c_int32), ("lu_panel", C.c_int32),
+                ("reserved", C.c_int32),
+                ("a_limb", C.c_void_p), ("a_exp", C.c_void_p), ("a_sign", C.c_void_p),
+                ("b_limb", C.c_void_p), ("b_exp", C.c_void_p), ("b_sign", C.c_void_p),
+                ("c_limb", C.c_void_p), ("c_exp", C.c_void_p), ("c_sign", C.c_void_p)]
 
 
 _lib = None
@@ -80,6 +94,14 @@ def load_library(path: str = LIB_PATH):
             lib.mp_set_workspace.argtypes = [C.c_void_p, C.c_size_t]
             lib.mp_singular_column.restype = C.c_int64
             lib.mp_strerror.restype = C.c_char_p
+            lib.mp_server_create.restype = C.c_void_p
+            lib.mp_server_create.argtypes = [C.c_size_t, C.c_int]
+            lib.mp_server_submit.argtypes = [C.c_void_p, C.POINTER(MPRequest)]
+            lib.mp_server_cancel.argtypes = [C.c_void_p, C.c_int64]
+            lib.mp_server_poll.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+            lib.mp_server_drain.argtypes = [C.c_void_p]
+            lib.mp_server_stats.argtypes = [C.c_void_p, C.c_void_p]
+            lib.mp_server_destroy.argtypes = [C.c_void_p]
             lib.mp_profile_read.argtypes = [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                             C.POINTER(C.c_double)]
             _lib = lib
@@ -230,3 +252,106 @@ def mplu(A: DeviceMP, piv, b: DeviceMP | None, x: DeviceMP | None) -> None:
     _check(load_library().mplu(A.rows, A.p, C.byref(a), C.c_void_p(piv.data_ptr()),
                                C.byref(bs) if bs is not None else None,
                                C.byref(xs) if xs is not None else None), "mplu")
+
+
+# ------------------------------------------------------------------ serving
+def _host_arrays(M, pinned: bool):
+    """Contiguous interchange arrays of a HostMP, and the objects owning their
+    memory (page-locked torch tensors when pinned)."""
+    arrs = [np.ascontiguousarray(M.limb, dtype=np.uint64), np.ascontiguousarray(M.exp, dtype=np.int64),
+            np.ascontiguousarray(M.sign, dtype=np.int8)]
+    if not pinned:
+        return arrs, arrs
+    import torch
+    views, owners = [], []
+    for a in arrs:
+        t = torch.empty(a.shape, dtype=torch.int8 if a.dtype == np.int8 else torch.int64,
+                        pin_memory=True)
+        v = t.numpy().view(a.dtype)
+        v[...] = a
+        views.append(v)
+        owners.append(t)
+    return views, owners
+
+
+class Server:
+    """Continuous-batching request loop of the library (mp_server_*)."""
+
+    def __init__(self, budget_bytes: int, slots: int = 8, pinned: bool = True):
+        self.lib = load_library()
+        self.h = self.lib.mp_server_create(C.c_size_t(budget_bytes), slots)
+        if not self.h:
+            raise MPError(-5, "mp_server_create")
+        self.pinned = pinned
+        self.live = {}            # id -> buffers kept alive until completion
+        self.results = {}         # id -> (status, latency_ms, output HostMP)
+
+    def _req(self, rid, kind, prec, m, l, n, algo, cutoff, panel, A, B, out):
+        a, ka = _host_arrays(A, self.pinned)
+        b, kb = _host_arrays(B, self.pinned)
+        o, ko = _host_arrays(out, self.pinned)
+        ptr = lambda x: x.ctypes.data_as(C.c_void_p)
+        r = MPRequest(rid, kind, prec, m, l, n, algo, cutoff, panel, 0,
+                      ptr(a[0]), ptr(a[1]), ptr(a[2]), ptr(b[0]), ptr(b[1]), ptr(b[2]),
+                      ptr(o[0]), ptr(o[1]), ptr(o[2]))
+        self.live[rid] = (a, b, o, prec, (ka, kb, ko))
+        rc = self.lib.mp_server_submit(self.h, C.byref(r))
+        if rc != MP_OK:
+            del self.live[rid]
+        return rc
+
+    def submit_gemm(self, rid, A, B, algo=BLOCK, cutoff=64):
+        m, l = A.shape
+        n = B.shape[1]
+        out = HostMP.zeros(m, n, A.p)
+        return self._req(rid, REQ_GEMM, A.p, m, l, n, algo, cutoff, 0, A, B, out)
+
+    def submit_lu(self, rid, A, b, algo=SIMPLE, cutoff=64, panel=128):
+        n = A.shape[0]
+        out = HostMP.zeros(n, 1, A.p)
+        return self._req(rid, REQ_LU_SOLVE, A.p, n, n, 1, algo, cutoff, panel, A, b, out)
+
+    def cancel(self, rid) -> int:
+        return self.lib.mp_server_cancel(self.h, rid)
+
+    def poll(self, max_n: int = 4096):
+        ids = np.zeros(max_n, np.int64)
+        st = np.zeros(max_n, np.int32)
+        ms = np.zeros(max_n, np.float64)
+        k = self.lib.mp_server_poll(self.h, ids.ctypes.data_as(C.c_void_p), st.ctypes.data_as(C.c_void_p),
+                                    ms.ctypes.data_as(C.c_void_p), max_n)
+        done = []
+        for i in range(k):
+            rid = int(ids[i])
+            bufs = self.live.pop(rid, None)
+            out = None
+            if bufs is not None:
+                o, prec = bufs[2], bufs[3]
+                out = HostMP(o[0].copy(), o[1].copy(), o[2].copy(), prec)
+            self.results[rid] = (int(st[i]), float(ms[i]), out)
+            done.append(rid)
+        return done
+
+    def drain(self):
+        _check(self.lib.mp_server_drain(self.h), "drain")
+        self.poll()
+
+    def stats(self) -> dict:
+        out = np.zeros(8, np.int64)
+        _check(self.lib.mp_server_stats(self.h, out.ctypes.data_as(C.c_void_p)))
+        keys = ["submitted", "completed", "batches", "batched_requests", "peak_bytes", "budget",
+                "running", "queued"]
+        return dict(zip(keys, (int(x) for x in out)))
+
+    def close(self):
+        if self.h:
+            self.lib.mp_server_drain(self.h)
+            self.poll()
+            self.lib.mp_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -376,6 +376,13 @@ int gemm_core(int algo, int cutoff, int policy, int64_t m, int64_t l, int64_t n,
         });
         return launch_status();
     }
+    if (algo == MP_EXACT) {
+        Prof pr(MP_K_SIMPLE, (double)m * l * n, s);
+        dispatch(p, [&](auto w) {
+            launch_gemm_exact<decltype(w)::value>(A, B, C, m, l, n, p, st, s);
+        });
+        return launch_status();
+    }
     auto lv = plan(m, l, n, cutoff, policy);
     if (algo == MP_BLOCK || lv.size() <= 1) {
         Prof pr(MP_K_LEAF, (double)m * l * n, s);
@@ -403,6 +410,16 @@ BMat sub_view(BMat M, int64_t r0, int64_t c0)
 }
 
 }  // namespace
+
+static size_t lu_ws_bytes(int64_t n, int p, int panel, int algo, int cutoff, int policy)
+{
+    const int L = limbs_of(p);
+    const int64_t K = std::min<int64_t>(panel, n);
+    const int64_t nt = n - K;                              // largest trailing block
+    size_t b = mat_bytes(1, nt, nt, L) + mat_bytes(1, n, 1, L) + padded((size_t)n * 8);
+    b += gemm_ws_bytes(algo, nt, K, nt, cutoff, policy, L) + 512;
+    return b;
+}
 
 namespace mpg {
 // C := A B with the recursion's buffers carved from a caller-supplied device
@@ -439,6 +456,40 @@ bool gemm_args_ok(int64_t m, int64_t l, int64_t n, int32_t prec, int32_t algo, i
 }
 
 cudaStream_t current_stream() { return g_ts.stream; }
+
+size_t lu_scratch_bytes(int64_t n, int p, int panel, int algo, int cutoff, int policy)
+{
+    return lu_ws_bytes(n, p, panel, algo, cutoff, policy);
+}
+
+// C_b = A_b B_b for a batch of equally shaped products by the Block kernel
+// (the server's batched launches).  Stream-ordered.
+int gemm_block_batched(int p, BMat A, BMat B, BMat C, int64_t batch, int64_t m, int64_t l,
+                       int64_t n, cudaStream_t s)
+{
+    DevStatus *st = status_ptr();
+    if (!st) return MP_ERR_CUDA;
+    Prof pr(MP_K_LEAF, (double)batch * m * l * n, s);
+    dispatch(p, [&](auto w) {
+        launch_gemm_block<decltype(w)::value>(A, B, C, batch, m, l, n, p, st, s);
+    });
+    return launch_status();
+}
+
+// +0 in every element of a batch of rows x cols matrices
+int fill_zero_batched(BMat M, int64_t batch, int64_t rows, int64_t cols, int p, cudaStream_t s)
+{
+    const int L = limbs_of(p);
+    for (int64_t b = 0; b < batch; ++b) {
+        BMat v = M;
+        v.limb += b * M.bs_limb;
+        v.exp += b * M.bs_es;
+        v.sign += b * M.bs_es;
+        fill_zero_kernel<<<(unsigned)std::min<int64_t>((rows * cols + 127) / 128, 152 * 32), 128, 0,
+                           s>>>(v, rows, cols, L);
+    }
+    return launch_status();
+}
 int current_odd_policy() { return g_ts.odd_policy; }
 }  // namespace mpg
 
@@ -486,7 +537,7 @@ const char *mp_strerror(int status)
     case MP_ERR_TIMEOUT: return "device wait timed out";
     case MP_ERR_CUDA: return "CUDA runtime error";
     case MP_ERR_RANGE: return "exponent out of range";
-    case MP_ERR_UNSUPPORTED: return "unsupported";
+    case MP_ERR_UNSUPPORTED: return "unsupported (e.g. exponent spread too wide for exact accumulation)";
     case MP_ERR_SCRATCH: return "product needs more than the static scratch array holds";
     default: return "unknown status";
     }
@@ -509,6 +560,7 @@ int mp_sync_status(void)
     if (h.flags & ST_SINGULAR) return MP_ERR_SINGULAR;
     if (h.flags & ST_DIVZERO) return MP_ERR_ARG;
     if (h.flags & ST_RANGE) return MP_ERR_RANGE;
+    if (h.flags & ST_WIDE) return MP_ERR_UNSUPPORTED;
     return MP_OK;
 }
 
@@ -597,7 +649,7 @@ int mpgemm(int64_t m, int64_t l, int64_t n, int32_t prec, int32_t algo, int32_t 
            const mpmat_t *A, const mpmat_t *B, mpmat_t *C)
 {
     if (!valid_prec(prec) || m < 0 || l < 0 || n < 0) return MP_ERR_ARG;
-    if (algo < MP_SIMPLE || algo > MP_WINOGRAD) return MP_ERR_ARG;
+    if (algo < MP_SIMPLE || algo > MP_EXACT) return MP_ERR_ARG;
     if ((algo == MP_STRASSEN || algo == MP_WINOGRAD) && cutoff < 1) return MP_ERR_ARG;
     if (!valid_mat(A, m, l, prec) || !valid_mat(B, l, n, prec) || !valid_mat(C, m, n, prec))
         return MP_ERR_ARG;
@@ -613,15 +665,6 @@ int mpgemm(int64_t m, int64_t l, int64_t n, int32_t prec, int32_t algo, int32_t 
                      st, s);
 }
 
-static size_t lu_ws_bytes(int64_t n, int p, int panel, int algo, int cutoff, int policy)
-{
-    const int L = limbs_of(p);
-    const int64_t K = std::min<int64_t>(panel, n);
-    const int64_t nt = n - K;                              // largest trailing block
-    size_t b = mat_bytes(1, nt, nt, L) + mat_bytes(1, n, 1, L) + padded((size_t)n * 8);
-    b += gemm_ws_bytes(algo, nt, K, nt, cutoff, policy, L) + 512;
-    return b;
-}
 
 size_t mplu_workspace_size(int64_t n, int32_t prec)
 {

@@ -22,6 +22,7 @@ enum : unsigned {
     ST_DIVZERO = 2u,
     ST_SINGULAR = 4u,
     ST_TIMEOUT = 8u,
+    ST_WIDE = 16u,         // exact accumulation: exponent spread beyond the accumulator
 };
 
 struct DevStatus {
@@ -69,6 +70,11 @@ template <int W>
 void launch_border(BMat A, BMat B, BMat C, int64_t nodes, int64_t m, int64_t l, int64_t n,
                    int64_t mr, bool last_row, bool last_col, int p, DevStatus *st,
                    cudaStream_t s);
+
+// C = RN_p(exact A B): every dot product exact, rounded once
+template <int W>
+void launch_gemm_exact(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p,
+                       DevStatus *st, cudaStream_t s);
 
 // LU (Sec. 4): pivot search + row exchange of column k; l_ik = a_ik / a_kk;
 // one elimination step a_ij -= a_ik a_kj on [r0, r1) x [c0, c1); solves

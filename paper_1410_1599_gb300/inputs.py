@@ -169,15 +169,23 @@ def _normalize(X: np.ndarray, over: np.ndarray):
     lead = np.where(first < L, lead, np.uint64(1))
     z = first * 64 + _clz64(lead)
     z = np.where(first < L, z, 0)
-    zw = z // 64
-    zb = (z % 64).astype(np.uint64)
-    Xp = np.concatenate([X, np.zeros((N, L + 1), np.uint64)], axis=1)
-    out = np.zeros_like(X)
-    for t in range(L):
-        hi = Xp[np.arange(N), t + zw]
-        lo = Xp[np.arange(N), t + zw + 1]
-        sh = np.where(zb == 0, hi, (hi << zb) | (lo >> (np.uint64(64) - np.where(zb == 0, 1, zb).astype(np.uint64))))
-        out[:, t] = sh
+    out = np.empty_like(X)
+    # common case: the leading one is in limb 0, an in-limb shift by zb < 64
+    fast = first == 0
+    zb = z[fast].astype(np.uint64)[:, None]
+    Xf = X[fast]
+    nxt = np.concatenate([Xf[:, 1:], np.zeros((Xf.shape[0], 1), np.uint64)], axis=1)
+    sh = np.where(zb == 0, Xf, (Xf << zb) | (nxt >> (np.uint64(64) - np.where(zb == 0, 1, zb).astype(np.uint64))))
+    out[fast] = sh
+    # rare case: whole limbs of leading zeros (or zero), element by element
+    for r in np.nonzero(~fast)[0]:
+        zw_r, zb_r = int(z[r]) // 64, int(z[r]) % 64
+        v = 0
+        for t in range(L):
+            v = (v << 64) | int(X[r, t])
+        v = (v << (64 * zw_r + zb_r)) & ((1 << (64 * L)) - 1)
+        for t in range(L):
+            out[r, t] = (v >> (64 * (L - 1 - t))) & 0xFFFFFFFFFFFFFFFF
     exp = -z
     # the value exactly 1.0 (X wrapped to 0 with the carry in `over`)
     one = (over == 1)

@@ -1,0 +1,117 @@
+"""Serving loop (continuous batching): every request's result is the same
+alone and in a concurrent mix (bit for bit), small Block GEMMs of one
+precision and bucket are batched, the memory budget holds, and malformed,
+oversized and cancelled requests are reported."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as orc
+from paper_1410_1599_gb300 import binding as mp
+from paper_1410_1599_gb300 import inputs as gen
+from tests.gpu_util import assert_bits_equal
+
+pytestmark = pytest.mark.gpu
+
+PRECS = [128, 256, 512, 1024, 2048]
+
+
+def _requests(count, seed):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(count):
+        p = int(rng.choice(PRECS))
+        if rng.random() < 0.7:
+            m, l, n = (int(x) for x in rng.integers(16, 160, 3))
+            algo = mp.WINOGRAD if min(m, l, n) > 100 else mp.BLOCK
+            A = gen.uniform_pm1(m, l, p, 1000 + i, -16, 16)
+            B = gen.uniform_pm1(l, n, p, 2000 + i, -16, 16)
+            reqs.append(("gemm", i, A, B, algo))
+        else:
+            n = int(rng.integers(16, 90))
+            A = gen.well_conditioned(n, p, 3000 + i)
+            b = gen.uniform_pm1(n, 1, p, 4000 + i)
+            reqs.append(("lu", i, A, b, mp.WINOGRAD if n > 64 else mp.SIMPLE))
+    return reqs
+
+
+def _submit(srv, r):
+    kind, rid, A, B, algo = r
+    if kind == "gemm":
+        return srv.submit_gemm(rid, A, B, algo=algo, cutoff=32)
+    return srv.submit_lu(rid, A, B, algo=algo, cutoff=16, panel=32)
+
+
+def test_alone_equals_mixed():
+    reqs = _requests(40, 5)
+    # alone: one slot, one request at a time
+    alone = {}
+    srv = mp.Server(budget_bytes=8 << 30, slots=1)
+    for r in reqs:
+        assert _submit(srv, r) == 0
+        srv.drain()
+        st, ms, out = srv.results[r[1]]
+        assert st == mp.REQ_DONE
+        alone[r[1]] = out
+    srv.close()
+    # mixed: everything at once, eight slots
+    srv = mp.Server(budget_bytes=8 << 30, slots=8)
+    for r in reqs:
+        assert _submit(srv, r) == 0
+    srv.drain()
+    stats = srv.stats()
+    assert stats["completed"] == len(reqs)
+    assert stats["batches"] >= 1 and stats["batched_requests"] >= 2
+    for r in reqs:
+        st, ms, out = srv.results[r[1]]
+        assert st == mp.REQ_DONE
+        assert_bits_equal(out, alone[r[1]], "request %d" % r[1])
+    srv.close()
+    # and the results are the algorithms' own (oracle) results
+    for r in reqs[:6]:
+        kind, rid, A, B, algo = r
+        if kind == "gemm":
+            want = orc.gemm(algo, A, B, cutoff=32)
+        else:
+            F, piv, rc = orc.lu(A, panel=32, algo=algo, cutoff=16)
+            want = orc.lu_solve(F, piv, B)
+        assert_bits_equal(alone[rid], want, "oracle %d" % rid)
+
+
+def test_budget_is_respected_and_oversized_rejected():
+    p = 512
+    A = gen.uniform_pm1(200, 200, p, 1)
+    B = gen.uniform_pm1(200, 200, p, 2)
+    per = mp.Server(budget_bytes=1 << 40, slots=1)
+    per.close()
+    budget = 3 * 200 * 200 * 73 * 2          # about two requests' operands
+    srv = mp.Server(budget_bytes=budget, slots=8)
+    for i in range(6):
+        assert srv.submit_gemm(i, A, B, algo=mp.SIMPLE) == 0
+    big = gen.uniform_pm1(600, 600, p, 3)
+    assert srv.submit_gemm(99, big, big, algo=mp.SIMPLE) == -2     # never fits
+    srv.drain()
+    st = srv.stats()
+    assert st["completed"] == 6 and st["peak_bytes"] <= budget
+    outs = [srv.results[i][2] for i in range(6)]
+    for o in outs[1:]:
+        assert_bits_equal(o, outs[0], "same request")
+    srv.close()
+
+
+def test_malformed_and_cancelled():
+    srv = mp.Server(budget_bytes=1 << 30, slots=1)
+    A = gen.uniform_pm1(4, 4, 128, 1)
+    bad = mp.HostMP(A.limb, A.exp, A.sign, 5000)          # precision out of range
+    assert srv.submit_gemm(1, bad, bad) == -1
+    # a long head request keeps the single slot busy; cancel a queued one
+    H = gen.uniform_pm1(300, 300, 1024, 2)
+    assert srv.submit_gemm(10, H, H, algo=mp.SIMPLE) == 0
+    for i in range(11, 15):
+        assert srv.submit_gemm(i, A, A, algo=mp.WINOGRAD, cutoff=2) == 0
+    assert srv.cancel(13) == 0
+    assert srv.cancel(13) == -1
+    srv.drain()
+    assert srv.results[13][0] == mp.REQ_CANCELLED
+    assert all(srv.results[i][0] == mp.REQ_DONE for i in (10, 11, 12, 14))
+    srv.close()
