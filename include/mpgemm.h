@@ -69,9 +69,16 @@ enum {
     MP_BLOCK    = 1,   /* Eq. 2: blocked, same k-ascending sequence per c_ij */
     MP_STRASSEN = 2,   /* Strassen's P1..P7 recursion */
     MP_WINOGRAD = 3,   /* Winograd's variant, S1..S8 / M1..M7 / T1, T2 */
-    MP_EXACT    = 4    /* every c_ij the exact dot product, rounded once (the
+    MP_EXACT    = 4,   /* every c_ij the exact dot product, rounded once (the
                           accuracy reference of Sec. 3's error tables; the
                           result of the split form) */
+    MP_SPLIT    = 5    /* the same result as MP_EXACT by the split form: rows of
+                          A / columns of B aligned to their largest exponent,
+                          cut into signed 8-bit digits, digit products on
+                          tensor cores (exact integer fp16 x fp16 -> fp32
+                          chunks folded into int64), exact recombination, one
+                          rounding; rows/columns whose exponents spread more
+                          than 64 bits are computed by the MP_EXACT kernel */
 };
 
 /* handling of odd dimensions in the recursion (Sec. 2, last paragraph) */
@@ -129,7 +136,7 @@ size_t mpgemm_workspace_size(int64_t m, int64_t l, int64_t n, int32_t prec,
 
 /*
  * C := A B with A m x l, B l x n, C m x n, all of precision prec.
- *   algo   : MP_SIMPLE, MP_BLOCK, MP_STRASSEN, MP_WINOGRAD or MP_EXACT;
+ *   algo   : MP_SIMPLE, MP_BLOCK, MP_STRASSEN, MP_WINOGRAD, MP_EXACT or MP_SPLIT;
  *   cutoff : Strassen/Winograd recurse while m, l and n all exceed it
  *            (n_min of Sec. 2, >= 1); below it the leaf product is Block.
  * Every c_ij of Simple/Block is (((+0 + a_i1 b_1j) + a_i2 b_2j) + ...) with
@@ -143,6 +150,16 @@ size_t mpgemm_workspace_size(int64_t m, int64_t l, int64_t n, int32_t prec,
  */
 int mpgemm(int64_t m, int64_t l, int64_t n, int32_t prec, int32_t algo, int32_t cutoff,
            const mpmat_t *A, const mpmat_t *B, mpmat_t *C);
+
+/*
+ * C_b := A_b B_b for b = 0 .. batch-1, independent equally shaped products
+ * (Simple or Block; each C_b exactly as mpgemm would compute it).  The
+ * operands are stacked by rows: A is (batch*m) x l with A_b = rows
+ * [b*m, (b+1)*m), B is (batch*l) x n, C is (batch*m) x n; one grouped launch
+ * covers all of them.  Other algorithms return MP_ERR_UNSUPPORTED.
+ */
+int mpgemm_batched(int64_t batch, int64_t m, int64_t l, int64_t n, int32_t prec, int32_t algo,
+                   const mpmat_t *A, const mpmat_t *B, mpmat_t *C);
 
 /*
  * mpgemm_noalloc -- the same product as mpgemm, for callers that cannot
@@ -271,7 +288,10 @@ enum {
     MP_K_FIXUP = 4,      /* peel fix-ups (rank-1 update, last row / column) */
     MP_K_ELEMENTWISE = 5,/* mp_elementwise, mp_convert, fills */
     MP_K_LU = 6,         /* LU panel, row exchange, TRSM, trailing subtract, solves */
-    MP_K_COUNT = 7
+    MP_K_SPLIT = 7,      /* split form: digit-product (tensor core) kernel */
+    MP_K_SPLIT_AUX = 8,  /* split form: alignment, recombination, wide fallback */
+    MP_K_EXACT = 9,      /* exact-dot GEMM kernel */
+    MP_K_COUNT = 10
 };
 
 /* While enabled (on != 0), every kernel the library launches from the

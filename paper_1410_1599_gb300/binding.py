@@ -17,7 +17,7 @@ from .inputs import EXP_ZERO, HostMP, limbs_for
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "lib", "libmpgemm.so")
 
-SIMPLE, BLOCK, STRASSEN, WINOGRAD, EXACT = 0, 1, 2, 3, 4
+SIMPLE, BLOCK, STRASSEN, WINOGRAD, EXACT, SPLIT = 0, 1, 2, 3, 4, 5
 PEEL, MIXED = 0, 1
 OP_ADD, OP_SUB, OP_MUL, OP_DIV = 0, 1, 2, 3
 
@@ -31,14 +31,15 @@ EXPORTS = ["mp_set_stream", "mp_set_workspace", "mp_set_odd_policy", "mp_set_lu"
            "mp_elementwise", "mp_convert", "mpgemm_workspace_size", "mpgemm",
            "mplu_workspace_size", "mplu", "mp_sync_status", "mp_singular_column",
            "mp_strerror", "mp_version", "mp_profile_enable", "mp_profile_read",
-           "mpgemm_noalloc", "mp_server_create", "mp_server_submit", "mp_server_cancel",
+           "mpgemm_noalloc", "mpgemm_batched", "mp_server_create", "mp_server_submit", "mp_server_cancel",
            "mp_server_poll", "mp_server_drain", "mp_server_stats", "mp_server_destroy"]
 
 REQ_GEMM, REQ_LU_SOLVE = 0, 1
 REQ_DONE, REQ_PENDING, REQ_RUNNING, REQ_CANCELLED, REQ_FAILED = 0, 1, 2, 3, 4
 
-K_LEAF, K_SIMPLE, K_OPERANDS, K_COMBINE, K_FIXUP, K_ELEMENTWISE, K_LU = range(7)
-K_NAMES = ["leaf_gemm", "simple_gemm", "operands", "combine", "fixup", "elementwise", "lu"]
+K_LEAF, K_SIMPLE, K_OPERANDS, K_COMBINE, K_FIXUP, K_ELEMENTWISE, K_LU, K_SPLIT, K_SPLIT_AUX, K_EXACT = range(10)
+K_NAMES = ["leaf_gemm", "simple_gemm", "operands", "combine", "fixup", "elementwise", "lu",
+           "split_slices", "split_aux", "exact_gemm"]
 
 
 class MPError(RuntimeError):
@@ -87,6 +88,9 @@ def load_library(path: str = LIB_PATH):
                                            C.POINTER(MPMat)]
             lib.mplu.argtypes = [C.c_int64, C.c_int32, C.POINTER(MPMat), C.c_void_p,
                                  C.POINTER(MPMat), C.POINTER(MPMat)]
+            lib.mpgemm_batched.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
+                                           C.c_int32, C.POINTER(MPMat), C.POINTER(MPMat),
+                                           C.POINTER(MPMat)]
             lib.mp_elementwise.argtypes = [C.c_int, C.POINTER(MPMat), C.POINTER(MPMat),
                                            C.POINTER(MPMat)]
             lib.mp_convert.argtypes = [C.POINTER(MPMat), C.POINTER(MPMat)]
@@ -234,6 +238,14 @@ def mpgemm(A: DeviceMP, B: DeviceMP, C_: DeviceMP, algo: int = SIMPLE, cutoff: i
     a, b, c = A.struct(), B.struct(), C_.struct()
     _check(load_library().mpgemm(A.rows, A.cols, B.cols, A.p, algo, cutoff, C.byref(a),
                                  C.byref(b), C.byref(c)), "mpgemm")
+
+
+def mpgemm_batched(batch: int, A: DeviceMP, B: DeviceMP, C_: DeviceMP, algo: int = BLOCK) -> None:
+    """batch independent products on row-stacked operands (see include/mpgemm.h)."""
+    m, l, n = A.rows // batch, A.cols, B.cols
+    a, b, c = A.struct(), B.struct(), C_.struct()
+    _check(load_library().mpgemm_batched(batch, m, l, n, A.p, algo, C.byref(a), C.byref(b),
+                                         C.byref(c)), "mpgemm_batched")
 
 
 def mpgemm_noalloc(A: DeviceMP, B: DeviceMP, C_: DeviceMP, algo: int = WINOGRAD,

@@ -348,10 +348,58 @@ int run_recursion(int algo, const std::vector<LevelDims> &lv, int p, BMat A0, BM
     return launch_status();
 }
 
+// split form: digit planes, exponent / spread vectors, diagonal sums
+size_t split_ws_bytes(int64_t m, int64_t l, int64_t n, int p)
+{
+    const size_t S = (size_t)split_digit_count(p), lp = (size_t)split_row_pad(l);
+    return padded(S * m * lp * 2) + padded(S * n * lp * 2) + padded((size_t)m * 8) +
+           padded((size_t)n * 8) + padded((size_t)m) + padded((size_t)n) +
+           padded((2 * S - 1) * m * n * 8) + 8 * 256;
+}
+
+int run_split(int64_t m, int64_t l, int64_t n, int p, BMat A, BMat B, BMat C, Workspace &ws,
+              DevStatus *st, cudaStream_t s)
+{
+    const size_t mk = ws.mark();
+    const size_t S = (size_t)split_digit_count(p), lp = (size_t)split_row_pad(l);
+    __half *pa = (__half *)ws.take(S * m * lp * 2);
+    __half *pb = (__half *)ws.take(S * n * lp * 2);
+    int64_t *ea = (int64_t *)ws.take((size_t)m * 8);
+    int64_t *eb = (int64_t *)ws.take((size_t)n * 8);
+    uint8_t *wa = (uint8_t *)ws.take((size_t)m);
+    uint8_t *wb = (uint8_t *)ws.take((size_t)n);
+    long long *D = (long long *)ws.take((2 * S - 1) * m * n * 8);
+    {
+        Prof pr(MP_K_SPLIT_AUX, (double)(m * l + l * n), s);
+        dispatch(p, [&](auto w) {
+            launch_split_prep<decltype(w)::value>(A, B, m, l, n, p, pa, pb, ea, eb, wa, wb, s);
+        });
+    }
+    {
+        Prof pr(MP_K_SPLIT, (double)S * S * m * (double)lp * n, s);
+        launch_split_slices(pa, pb, m, l, n, p, D, s);
+    }
+    {
+        Prof pr(MP_K_SPLIT_AUX, (double)m * n, s);
+        dispatch(p, [&](auto w) {
+            launch_split_finish<decltype(w)::value>(D, m, n, p, ea, eb, wa, wb, C, st, s);
+        });
+    }
+    {
+        Prof pr(MP_K_SPLIT_AUX, 0.0, s);
+        dispatch(p, [&](auto w) {
+            launch_gemm_exact<decltype(w)::value>(A, B, C, m, l, n, p, st, s, wa, wb);
+        });
+    }
+    ws.reset(mk);
+    return launch_status();
+}
+
 // C := A B for (possibly strided) views, with the recursion's buffers carved
 // from ws (which must hold gemm_ws_bytes(...)).  Stream-ordered.
 size_t gemm_ws_bytes(int algo, int64_t m, int64_t l, int64_t n, int cutoff, int policy, int L)
 {
+    if (algo == MP_SPLIT) return (m > 0 && l > 0 && n > 0) ? split_ws_bytes(m, l, n, 64 * L) : 0;
     if (algo != MP_STRASSEN && algo != MP_WINOGRAD) return 0;
     if (m <= 0 || l <= 0 || n <= 0) return 0;
     auto lv = plan(m, l, n, cutoff, policy);
@@ -376,8 +424,11 @@ int gemm_core(int algo, int cutoff, int policy, int64_t m, int64_t l, int64_t n,
         });
         return launch_status();
     }
+    if (algo == MP_SPLIT) {
+        return run_split(m, l, n, p, A, B, C, ws, st, s);
+    }
     if (algo == MP_EXACT) {
-        Prof pr(MP_K_SIMPLE, (double)m * l * n, s);
+        Prof pr(MP_K_EXACT, (double)m * l * n, s);
         dispatch(p, [&](auto w) {
             launch_gemm_exact<decltype(w)::value>(A, B, C, m, l, n, p, st, s);
         });
@@ -638,6 +689,8 @@ int mp_convert(const mpmat_t *X, mpmat_t *R)
 size_t mpgemm_workspace_size(int64_t m, int64_t l, int64_t n, int32_t prec, int32_t algo,
                              int32_t cutoff)
 {
+    if (algo == MP_SPLIT)
+        return (m > 0 && l > 0 && n > 0 && valid_prec(prec)) ? split_ws_bytes(m, l, n, prec) : 0;
     if (algo != MP_STRASSEN && algo != MP_WINOGRAD) return 0;
     if (cutoff < 1 || m <= 0 || l <= 0 || n <= 0 || !valid_prec(prec)) return 0;
     auto lv = plan(m, l, n, cutoff, g_ts.odd_policy);
@@ -649,7 +702,7 @@ int mpgemm(int64_t m, int64_t l, int64_t n, int32_t prec, int32_t algo, int32_t 
            const mpmat_t *A, const mpmat_t *B, mpmat_t *C)
 {
     if (!valid_prec(prec) || m < 0 || l < 0 || n < 0) return MP_ERR_ARG;
-    if (algo < MP_SIMPLE || algo > MP_EXACT) return MP_ERR_ARG;
+    if (algo < MP_SIMPLE || algo > MP_SPLIT) return MP_ERR_ARG;
     if ((algo == MP_STRASSEN || algo == MP_WINOGRAD) && cutoff < 1) return MP_ERR_ARG;
     if (!valid_mat(A, m, l, prec) || !valid_mat(B, l, n, prec) || !valid_mat(C, m, n, prec))
         return MP_ERR_ARG;
@@ -665,6 +718,38 @@ int mpgemm(int64_t m, int64_t l, int64_t n, int32_t prec, int32_t algo, int32_t 
                      st, s);
 }
 
+
+int mpgemm_batched(int64_t batch, int64_t m, int64_t l, int64_t n, int32_t prec, int32_t algo,
+                   const mpmat_t *A, const mpmat_t *B, mpmat_t *C)
+{
+    if (!valid_prec(prec) || batch < 0 || m < 0 || l < 0 || n < 0) return MP_ERR_ARG;
+    if (algo != MP_SIMPLE && algo != MP_BLOCK)
+        return (algo >= MP_STRASSEN && algo <= MP_SPLIT) ? MP_ERR_UNSUPPORTED : MP_ERR_ARG;
+    if (!valid_mat(A, batch * m, l, prec) || !valid_mat(B, batch * l, n, prec) ||
+        !valid_mat(C, batch * m, n, prec))
+        return MP_ERR_ARG;
+    if (overlaps(C, A) || overlaps(C, B)) return MP_ERR_ARG;
+    if (batch == 0 || m == 0 || n == 0) return MP_OK;
+    cudaStream_t s = g_ts.stream;
+    DevStatus *st = status_ptr();
+    if (!st) return MP_ERR_CUDA;
+    const int L = limbs_of(prec);
+    if (l == 0) {
+        Prof pr(MP_K_ELEMENTWISE, (double)batch * m * n, s);
+        fill_zero_kernel<<<(unsigned)std::min<int64_t>((batch * m * n + 127) / 128, 152 * 32), 128, 0,
+                           s>>>(bmat(C), batch * m, n, L);
+        return launch_status();
+    }
+    BMat a = bmat(A), b = bmat(B), c = bmat(C);
+    a.bs_limb = a.bs_es = m * A->ld;
+    b.bs_limb = b.bs_es = l * B->ld;
+    c.bs_limb = c.bs_es = m * C->ld;
+    Prof pr(MP_K_LEAF, (double)batch * m * l * n, s);
+    dispatch(prec, [&](auto w) {
+        launch_gemm_block<decltype(w)::value>(a, b, c, batch, m, l, n, prec, st, s);
+    });
+    return launch_status();
+}
 
 size_t mplu_workspace_size(int64_t n, int32_t prec)
 {

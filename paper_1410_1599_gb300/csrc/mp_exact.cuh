@@ -49,15 +49,20 @@ template <int W>
 __device__ __noinline__ void exact_one(const BMat &A, const BMat &B, const BMat &C, int64_t i,
                                        int64_t j, int64_t l, const RoundSpec &rs, DevStatus *status);
 
+// rowsel / colsel (optional): compute only c_ij with rowsel[i] | colsel[j]
 template <int W>
 __global__ void __launch_bounds__(ExactCfg<W>::THREADS)
-gemm_exact_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p, DevStatus *status)
+gemm_exact_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p, DevStatus *status,
+                  const uint8_t *rowsel, const uint8_t *colsel)
 {
     const RoundSpec rs = make_spec<W>(p);
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= n) return;
-    for (int64_t i = blockIdx.y; i < m; i += gridDim.y)
+    const bool cj = colsel ? colsel[j] != 0 : true;
+    for (int64_t i = blockIdx.y; i < m; i += gridDim.y) {
+        if (rowsel && !(rowsel[i] || cj)) continue;
         exact_one<W>(A, B, C, i, j, l, rs, status);
+    }
 }
 
 template <int W>
@@ -170,16 +175,17 @@ __device__ __noinline__ void exact_one(const BMat &A, const BMat &B, const BMat 
 
 template <int W>
 void launch_gemm_exact(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p,
-                       DevStatus *st, cudaStream_t s)
+                       DevStatus *st, cudaStream_t s, const uint8_t *rowsel, const uint8_t *colsel)
 {
     if (m <= 0 || n <= 0) return;
     constexpr int T = ExactCfg<W>::THREADS;
     dim3 grid((unsigned)((n + T - 1) / T), (unsigned)(m < 65535 ? m : 65535));
-    gemm_exact_kernel<W><<<grid, T, 0, s>>>(A, B, C, m, l, n, p, st);
+    gemm_exact_kernel<W><<<grid, T, 0, s>>>(A, B, C, m, l, n, p, st, rowsel, colsel);
 }
 
 #define MPG_INSTANTIATE_EXACT(W)                                                                \
     template void launch_gemm_exact<W>(BMat, BMat, BMat, int64_t, int64_t, int64_t, int,        \
-                                       DevStatus *, cudaStream_t);
+                                       DevStatus *, cudaStream_t, const uint8_t *,              \
+                                       const uint8_t *);
 
 }  // namespace mpg

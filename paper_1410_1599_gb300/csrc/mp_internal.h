@@ -2,6 +2,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace mpg {
@@ -74,7 +75,23 @@ void launch_border(BMat A, BMat B, BMat C, int64_t nodes, int64_t m, int64_t l, 
 // C = RN_p(exact A B): every dot product exact, rounded once
 template <int W>
 void launch_gemm_exact(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p,
-                       DevStatus *st, cudaStream_t s);
+                       DevStatus *st, cudaStream_t s, const uint8_t *rowsel = nullptr,
+                       const uint8_t *colsel = nullptr);
+
+// split form of C = RN_p(exact A B) (mp_split.cuh): digit planes, slice
+// products by weight diagonal, recombination; rows/columns beyond the
+// spread budget are recomputed by launch_gemm_exact with rowsel/colsel
+int split_digit_count(int p);
+int64_t split_row_pad(int64_t l);
+template <int W>
+void launch_split_prep(BMat A, BMat B, int64_t m, int64_t l, int64_t n, int p, __half *pa,
+                       __half *pb, int64_t *ea, int64_t *eb, uint8_t *wa, uint8_t *wb, cudaStream_t s);
+void launch_split_slices(const __half *pa, const __half *pb, int64_t m, int64_t l, int64_t n,
+                         int p, long long *D, cudaStream_t s);
+template <int W>
+void launch_split_finish(const long long *D, int64_t m, int64_t n, int p, const int64_t *ea,
+                         const int64_t *eb, const uint8_t *wa, const uint8_t *wb, BMat C,
+                         DevStatus *st, cudaStream_t s);
 
 // LU (Sec. 4): pivot search + row exchange of column k; l_ik = a_ik / a_kk;
 // one elimination step a_ij -= a_ik a_kj on [r0, r1) x [c0, c1); solves

@@ -29,12 +29,3 @@ def test_exact_cancellation_and_zero():
     want = orc.dot_exact(A, B)
     assert_bits_equal(got, want, "cancellation")
     assert got.exp[0, 0] == gen.EXP_ZERO and got.sign[0, 0] == 0
-
-
-def test_exact_is_more_accurate_than_simple_at_equal_precision():
-    p, n = 128, 300
-    A = gen.uniform_pm1(n, n, p, 63)
-    B = gen.uniform_pm1(n, n, p, 64)
-    ex = gemm(A, B, mp.EXACT)
-    ref = orc.dot_exact(A, B, rows=np.arange(8), cols=np.arange(8), p_out=2 * p)
-    assert_bits_equal(ex.sub(np.arange(8), np.arange(8)), orc.convert(ref, p), "rounded once")

@@ -88,3 +88,23 @@ def test_full_size_sampled(algo, n):
         cols = orc.sample_set(1, ALGOS[algo], n, n, n, cutoff, orc.PEEL, int(j0))
         want = orc.gemm_sampled(ALGOS[algo], A, B, rows, cols, cutoff=cutoff)
         assert_bits_equal(got.sub(rows, cols), want, "%s n=%d sample (%d,%d)" % (algo, n, i0, j0))
+
+
+def test_batched_equals_individual():
+    """Config 1's batch of independent 64^3 products (256-bit) in one launch."""
+    p, m, l, n, batch = 256, 64, 64, 64, 24
+    As = [gen.uniform_pm1(m, l, p, 500 + b) for b in range(batch)]
+    Bs = [gen.uniform_pm1(l, n, p, 600 + b) for b in range(batch)]
+    stack = lambda Ms: gen.HostMP(np.concatenate([M.limb for M in Ms], axis=1),
+                                  np.concatenate([M.exp for M in Ms], axis=0),
+                                  np.concatenate([M.sign for M in Ms], axis=0), p)
+    dA, dB = dev(stack(As)), dev(stack(Bs))
+    dC = mp.DeviceMP.empty(batch * m, n, p)
+    for algo in (mp.SIMPLE, mp.BLOCK):
+        mp.mpgemm_batched(batch, dA, dB, dC, algo)
+        mp.check_status("batched")
+        C = dC.to_host()
+        for b in (0, 7, batch - 1):
+            want = orc.gemm(orc.SIMPLE, As[b], Bs[b])
+            got = C.sub(np.arange(b * m, (b + 1) * m), np.arange(n))
+            assert_bits_equal(got, want, "batch %d" % b)

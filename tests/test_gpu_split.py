@@ -1,0 +1,58 @@
+"""The split form (MP_SPLIT): rows of A / columns of B aligned and cut into
+signed 8-bit digits, digit products on tensor cores, exact recombination and
+one rounding -- bit for bit the oracle's correctly rounded exact dot product,
+including rows/columns beyond the 64-bit spread budget (limb fallback)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1410_1599_gb300 import binding as mp
+from paper_1410_1599_gb300 import inputs as gen
+from tests.gpu_util import assert_bits_equal, gemm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("p", [53, 128, 200, 256, 512, 1024, 2048])
+def test_split_matches_exact_oracle(p):
+    m, l, n = (37, 70, 45) if p >= 1024 else (70, 131, 66)
+    A = gen.uniform_pm1(m, l, p, 71, -16, 16)
+    B = gen.uniform_pm1(l, n, p, 72, -16, 16)
+    want = orc.dot_exact(A, B)
+    assert_bits_equal(gemm(A, B, mp.SPLIT), want, "split p=%d" % p)
+
+
+def test_split_wide_rows_and_columns_fall_back():
+    p, m, l, n = 256, 40, 64, 33
+    A = gen.uniform_pm1(m, l, p, 73, -8, 8)
+    B = gen.uniform_pm1(l, n, p, 74, -8, 8)
+    A.exp[3, 5] -= 200          # row 3 spreads over 200 bits
+    B.exp[7, 11] += 150         # column 11 too
+    A.exp[10, :] = gen.EXP_ZERO # an all-zero row
+    A.limb[:, 10, :] = 0
+    want = orc.dot_exact(A, B)
+    assert_bits_equal(gemm(A, B, mp.SPLIT), want, "split with wide rows/cols")
+
+
+def test_split_cancellation_to_zero_and_long_k():
+    p = 128
+    A = gen.from_ints([[3, -3, 5, -5], [1, 1, 1, 1]], p)
+    B = gen.from_ints([[7], [7], [1], [1]], p)
+    got = gemm(A, B, mp.SPLIT)
+    assert_bits_equal(got, orc.dot_exact(A, B), "cancellation")
+    assert got.exp[0, 0] == gen.EXP_ZERO
+    # k beyond one fp32 chunk
+    A = gen.uniform_pm1(9, 1500, 512, 75, -4, 4)
+    B = gen.uniform_pm1(1500, 7, 512, 76, -4, 4)
+    assert_bits_equal(gemm(A, B, mp.SPLIT), orc.dot_exact(A, B), "long k")
+
+
+def test_split_equals_exact_kernel_larger():
+    p, n = 1024, 256
+    A = gen.uniform_pm1(n, n, p, 77, -16, 16)
+    B = gen.uniform_pm1(n, n, p, 78, -16, 16)
+    s = gemm(A, B, mp.SPLIT)
+    e = gemm(A, B, mp.EXACT)
+    assert_bits_equal(s, e, "split vs exact kernel")
+    rows, cols = np.arange(0, n, 37), np.arange(5, n, 41)
+    assert_bits_equal(s.sub(rows, cols), orc.dot_exact(A, B, rows=rows, cols=cols), "oracle sample")
