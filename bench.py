@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--lu-n", type=int, default=1024)
     ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--serve", action="store_true", help="only the serving run (its own JSON line)")
+    ap.add_argument("--split", action="store_true",
+                    help="only the split-form comparison (4096^3 at 1024 bits by default)")
     return ap.parse_args()
 
 
@@ -432,6 +434,60 @@ def serve_run(n_req, seed=11, slots=8, budget=150 << 30):
             "peak_gb": round(max(st1["peak_bytes"], st2["peak_bytes"]) / 2 ** 30, 3)}
 
 
+def split_run(n=4096, p=1024, with_simple=True):
+    """Split form vs the exact limb path (same correctly rounded result) on
+    n^3 at p bits, entries U[-1,1)*2^e, e ~ U{-16..16}."""
+    import numpy as np
+    import torch
+
+    from oracle import oracle as orc
+    from paper_1410_1599_gb300 import binding as mp
+    from paper_1410_1599_gb300 import inputs as gen
+
+    A = gen.uniform_pm1(n, n, p, 13, -16, 16)
+    B = gen.uniform_pm1(n, n, p, 14, -16, 16)
+    dA, dB = mp.DeviceMP.from_host(A), mp.DeviceMP.from_host(B)
+    out = {}
+    res = {}
+    for name, algo in (("split", mp.SPLIT), ("exact_limb", mp.EXACT)) + ((("simple_limb", mp.SIMPLE),) if with_simple else ()):
+        C = mp.DeviceMP.empty(n, n, p)
+        torch.cuda.synchronize()
+        mp.profile_enable(True)
+        t0 = time.perf_counter()
+        mp.mpgemm(dA, dB, C, algo, 64)
+        rc = mp.sync_status()
+        t = time.perf_counter() - t0
+        prof = mp.profile_read()
+        mp.profile_enable(False)
+        out[name] = {"seconds": round(t, 3), "eff_gflops": round(2.0 * n ** 3 / t / 1e9, 3), "status": rc,
+                     "kernels_ms": {k: round(v[1], 2) for k, v in prof.items() if v[0]}}
+        if name == "split":
+            S = (p + 64 + 7) // 8 + 1
+            macs = prof["split_slices"][2]
+            out[name]["digits"] = S
+            out[name]["tensor_macs"] = macs
+            out[name]["slice_tmac_per_s"] = round(macs / (prof["split_slices"][1] * 1e-3) / 1e12, 2)
+        res[name] = C
+    same = bool(torch.equal(res["split"].limb, res["exact_limb"].limb) and
+                torch.equal(res["split"].exp, res["exact_limb"].exp) and
+                torch.equal(res["split"].sign, res["exact_limb"].sign))
+    rows = np.array([0, 1, n // 2, n - 1])
+    cols = np.array([0, n // 3, n - 1])
+    want = orc.dot_exact(A, B, rows=rows, cols=cols)
+    got = res["split"].to_host().sub(rows, cols)
+    oracle_ok = bool(np.array_equal(got.limb, want.limb) and np.array_equal(got.exp, want.exp)
+                     and np.array_equal(got.sign, want.sign))
+    exps = A.exp.astype(np.float64)
+    wide_rows = int(sum(1 for i in range(n) if (A.exp[i][A.exp[i] != gen.EXP_ZERO]).min()
+                        < (A.exp[i][A.exp[i] != gen.EXP_ZERO]).max() - 64))
+    wide_cols = int(sum(1 for j in range(n) if (B.exp[:, j][B.exp[:, j] != gen.EXP_ZERO]).min()
+                        < (B.exp[:, j][B.exp[:, j] != gen.EXP_ZERO]).max() - 64))
+    return {"n": n, "prec": p, "split_equals_exact_limb_all_outputs": same,
+            "split_equals_oracle_samples": oracle_ok, "wide_rows": wide_rows, "wide_cols": wide_cols,
+            "speedup_split_vs_exact_limb": round(out["exact_limb"]["seconds"] / out["split"]["seconds"], 3),
+            "peak_mma_sync_f16_tmac_measured": 300.8, **out}
+
+
 def cpu_baseline(A, B, seconds):
     """The oracle (plain C, all host threads) computing a sample of outputs of
     the same product by Simple dot products: eff GFLOP/s = 2 l outputs / t.
@@ -506,6 +562,13 @@ def run_reference(a, rank, world):
 def main():
     a = parse()
     rank, world, local = dist_env()
+    if a.split:
+        import torch
+        from paper_1410_1599_gb300 import build as libbuild
+        libbuild.build()
+        torch.cuda.set_device(local)
+        print(json.dumps({"split_form": split_run(a.n if a.n != 2048 else 4096, a.prec if a.prec != 512 else 1024)}), flush=True)
+        return
     if a.serve:
         import torch
         from paper_1410_1599_gb300 import build as libbuild
