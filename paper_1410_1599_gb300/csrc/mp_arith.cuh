@@ -208,6 +208,31 @@ MP_DEV void mul_full(uint32_t (&P)[2 * W], const uint32_t (&a)[W], const uint32_
     }
 }
 
+// Truncated product: the partial products a_i b_j with i + j >= W - 2 only.
+// The result T satisfies T <= a b < T + (W - 1) 2^(32(W-1)): the omitted
+// columns 0 .. W-3 sum to less than (W - 2) 2^(32(W-1)) and their carries
+// into word W-1 are at most W - 2.  Words W-1 .. 2W-1 of T are returned in
+// P[W-1 .. 2W-1] (lower words are scratch).
+template <int W>
+MP_DEV void mul_trunc(uint32_t (&P)[2 * W], const uint32_t (&a)[W], const uint32_t (&b)[W])
+{
+#pragma unroll
+    for (int i = 0; i < 2 * W; ++i) P[i] = 0u;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        const uint32_t bj = b[j];
+        const int i0 = (W - 2 - j > 0) ? W - 2 - j : 0;
+        P[j + i0] = mad_lo_cc(a[i0], bj, P[j + i0]);
+#pragma unroll
+        for (int i = i0 + 1; i < W; ++i) P[j + i] = madc_lo_cc(a[i], bj, P[j + i]);
+        P[j + W] = addc(P[j + W], 0u);
+        P[j + i0 + 1] = mad_hi_cc(a[i0], bj, P[j + i0 + 1]);
+#pragma unroll
+        for (int i = i0 + 1; i < W - 1; ++i) P[j + 1 + i] = madc_hi_cc(a[i], bj, P[j + 1 + i]);
+        P[j + W] = madc_hi(a[W - 1], bj, P[j + W]);
+    }
+}
+
 // Top half of a * b by a sliding window over the product, for large W where
 // a fully unrolled 2W-word product is too much code: rows of b are taken four
 // at a time (outer loop not unrolled); after each group the four lowest
@@ -267,6 +292,45 @@ MP_DEV void mul_impl(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, const RoundSpec &
     int64_t e = a.e + b.e;
     if constexpr (W <= 16) {
         uint32_t P[2 * W];
+        if (rs.r == 0) {
+            // p = 32W: round from the truncated product when its error bound
+            // cannot change the decision.  With w = word W-1 of T and the round
+            // bit at bit rpos of that word (31, or 30 when the product needs the
+            // one-bit normalisation), the exact word lies in [w, w + W - 1]
+            // (no carry into word W when w + W - 1 < 2^32).  If that interval
+            // stays inside one block of 2^rpos, the round bit is known; when it
+            // is 1 the bits under it are certainly nonzero unless w sits exactly
+            // on the block start.  Otherwise the full product decides.
+            mul_trunc<W>(P, a.m, b.m);
+            const uint32_t w = P[W - 1];
+            const uint32_t top = P[2 * W - 1] >> 31;
+            const int rpos = top ? 31 : 30;
+            const uint32_t wend = w + (uint32_t)(W - 1);
+            const uint32_t rb = (w >> rpos) & 1u;
+            const bool safe = (wend >= w) && ((w >> rpos) == (wend >> rpos)) &&
+                              !(rb && (w & ((1u << rpos) - 1u)) == 0u);
+            if (safe) {
+                if (!top) {
+#pragma unroll
+                    for (int i = 2 * W - 1; i > W; --i) P[i] = __funnelshift_l(P[i - 1], P[i], 1);
+                    P[W] = __funnelshift_l(w, P[W], 1);
+                    e -= 1;
+                }
+                P[W] = add_cc(P[W], rb);
+#pragma unroll
+                for (int i = W + 1; i < 2 * W; ++i) P[i] = addc_cc(P[i], 0u);
+                const uint32_t c = addc(0u, 0u);
+#pragma unroll
+                for (int i = 0; i < W; ++i) r.m[i] = P[W + i];
+                if (c) {
+                    r.m[W - 1] = 0x80000000u;
+                    e += 1;
+                }
+                r.e = e;
+                r.s = s;
+                return;
+            }
+        }
         mul_full<W>(P, a.m, b.m);
         uint32_t low = 0u;
 #pragma unroll

@@ -131,3 +131,41 @@ def test_range_overflow_is_reported():
     assert mp.sync_status() == -6
     want, _ = orc.scalar("mul", X, X)
     assert orc.range_error() == 1
+
+
+def _words_number(words_le, p, e, sign=0):
+    """Interchange entry from little-endian 32-bit words (mantissa of 32*len bits)."""
+    N = 0
+    for i, w in enumerate(words_le):
+        N |= (w & 0xFFFFFFFF) << (32 * i)
+    bl = N.bit_length()
+    return (sign, N, bl - e)     # value N * 2^(e - bl): fraction N/2^bl times 2^e
+
+
+@pytest.mark.parametrize("p", [128, 256, 512])
+def test_mul_truncation_boundaries(p):
+    """Products whose truncated partial sum cannot decide the rounding: the
+    word under the mantissa sits just below the round bit, exactly on a tie,
+    or just above it, with and without a nonzero tail.  a and b have only
+    their top and bottom 32-bit words set, so the omitted partial product is
+    a0*b0 alone."""
+    W = p // 32
+    cases = []
+    for s_top, a0, b0 in [(0xFFFFFFFF, 0x40000000, 0x40000001),   # w = 0x7fffffff, tail != 0
+                          (0xFFFFFFFF, 0x80000000, 0x00000000),   # w = 0x80000000, no tail: tie
+                          (0xFFFFFFFF, 0x7FFFFFFF, 0x00000001),   # w = 0x80000000 after carry
+                          (0xFFFFFFFF, 0x00000003, 0x7FFFFFF0),
+                          (0x80000000, 0x80000000, 0x00000000),   # product < 1/2: shifted case
+                          (0x80000001, 0x3FFFFFFF, 0x40000001)]:
+        a = [a0] + [0] * (W - 2) + [s_top]
+        b = [b0] + [0] * (W - 2) + [s_top]
+        cases.append((a, b))
+    xs = [_words_number(a, p, 1) for a, b in cases]
+    ys = [_words_number(b, p, -3, 1) for a, b in cases]
+    X = gen.from_exact_ints(xs, p, (1, len(xs)))
+    Y = gen.from_exact_ints(ys, p, (1, len(ys)))
+    want, rc = orc.scalar("mul", X, Y)
+    dR = mp.DeviceMP.empty(1, len(xs), p)
+    mp.elementwise(mp.OP_MUL, dev(X), dev(Y), dR)
+    mp.check_status("mul boundaries")
+    assert_bits_equal(dR.to_host(), want, "mul boundaries p=%d" % p)
