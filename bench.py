@@ -196,6 +196,17 @@ def run_ours(a, rank, world, local):
     kernels = {k: {"launches_per_step": v[0] / a.steps, "ms_per_step": v[1] / a.steps,
                    "share": v[1] / max(sum(x[1] for x in prof.values()), 1e-9)}
                for k, v in prof.items() if v[0]}
+    # HBM roofline of the recursion's elementwise kernels: algorithmic bytes
+    # operand sums read 4 quadrants and write 7 child operands (11 per 7 written),
+    # combinations read 7 child products and write 4 (11 per 4 written)
+    be = 8 * ((p + 63) // 64) + 9
+    hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6768.4
+    for k, per in (("operands", 11.0 / 7.0), ("combine", 11.0 / 4.0)):
+        if k in kernels and prof[k][1] > 0:
+            gbs = prof[k][2] * per * be / (prof[k][1] * 1e-3) / 1e9
+            kernels[k]["achieved_gbs"] = round(gbs, 1)
+            kernels[k]["hbm_frac"] = round(gbs / hbm, 3)
 
     # end to end through the public API with host buffers (pinned), copies timed
     hA = [t.cpu().pin_memory() for t in (dA.limb, dA.exp, dA.sign)]
@@ -219,7 +230,7 @@ def run_ours(a, rank, world, local):
     e2e_ms = allmax(e0.elapsed_time(e1) / e2e_steps)
     mp.check_status("e2e")
 
-    extras, extras_lu, serving = {}, None, None
+    extras, extras_lu, serving, by_prec, split_small = {}, None, None, {}, None
     if not a.no_extras and rank == 0:
         for name in ("simple", "block", "strassen", "winograd"):
             if name == a.algo:
@@ -237,7 +248,35 @@ def run_ours(a, rank, world, local):
             torch.cuda.synchronize()
             extras[name] = round(flops / (e0.elapsed_time(e1) * 1e-3) / 1e9, 3)
         mp.check_status("extras")
-        extras_lu = [lu_run(a.lu_n, 256, mp.WINOGRAD), lu_run(a.lu_n, 256, mp.SIMPLE)]
+        del dA, dB, dC
+        mp.set_workspace(None)
+        del ws
+        torch.cuda.empty_cache()
+        # the metric's precisions: Winograd vs Simple at 256 and 1024 bits, same n
+        for pp in (256, 1024):
+            Ap = mp.DeviceMP.from_host(gen.uniform_pm1(n, n, pp, 33, -16, 16))
+            Bp = mp.DeviceMP.from_host(gen.uniform_pm1(n, n, pp, 34, -16, 16))
+            Cp = mp.DeviceMP.empty(n, n, pp)
+            res = {}
+            for name in ("simple", "winograd"):
+                mp.mpgemm(Ap, Bp, Cp, ALGO_NAMES[name], cutoff)       # warm (module load)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                mp.mpgemm(Ap, Bp, Cp, ALGO_NAMES[name], cutoff)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                res[name] = round(flops / (e0.elapsed_time(e1) * 1e-3) / 1e9, 3)
+            res["speedup_winograd_vs_simple"] = round(res["winograd"] / res["simple"], 3)
+            by_prec["p%d" % pp] = res
+            mp.check_status("by precision")
+            del Ap, Bp, Cp
+            torch.cuda.empty_cache()
+        extras_lu = [lu_run(a.lu_n, 256, mp.WINOGRAD), lu_run(a.lu_n, 256, mp.SIMPLE),
+                     lu_run(a.lu_n, 1024, mp.WINOGRAD),
+                     lu_run(a.lu_n, 256, mp.WINOGRAD, kind="lotkin"),
+                     lu_run(a.lu_n, 1024, mp.WINOGRAD, kind="lotkin")]
+        mp.set_stream(stream)
+        split_small = split_run(1024, 1024, with_simple=False)
         mp.set_stream(stream)
         serving = serve_run(a.serve_requests)
         mp.set_stream(stream)
@@ -270,8 +309,12 @@ def run_ours(a, rank, world, local):
             line["speedup_vs_simple"] = round(extras.get(a.algo, value) / extras["simple"], 3)
         if cpu:
             line["cpu_baseline"] = cpu
+        if by_prec:
+            line["by_precision_n%d" % n] = by_prec
         if extras_lu:
             line["lu"] = extras_lu
+        if split_small:
+            line["split_form_n1024_p1024"] = split_small
         if serving:
             line["serving"] = serving
         print(json.dumps(line), flush=True)
@@ -299,10 +342,13 @@ def lu_run(n, p, algo, panel=128, cutoff=64, kind="well"):
     piv = torch.zeros(n, dtype=torch.int64, device="cuda")
     mp.set_lu(panel, algo, cutoff)
     torch.cuda.synchronize()
+    mp.profile_enable(True)
     t0 = time.perf_counter()
     mp.mplu(dA, piv, db, dx)
     rc = mp.sync_status()
     t = time.perf_counter() - t0
+    prof = mp.profile_read()
+    mp.profile_enable(False)
     mp.set_lu(128, mp.SIMPLE, 64)
     # residual r = b - A x at 2p (exact widening, Simple product, one subtraction)
     q = 2 * p
@@ -333,6 +379,8 @@ def lu_run(n, p, algo, panel=128, cutoff=64, kind="well"):
     fwd = float(np.abs(dbl(fe)).max())
     return {"n": n, "prec": p, "algo": {0: "simple", 1: "block", 2: "strassen", 3: "winograd"}[algo],
             "panel": panel, "matrix": kind, "seconds": round(t, 4), "status": rc,
+            "kernel_ms": {k: round(v[1], 2) for k, v in prof.items() if v[0]},
+            "launches": int(sum(v[0] for v in prof.values())),
             "eff_gflops": round((2.0 / 3.0) * n ** 3 / t / 1e9, 4),
             "backward_error": back, "forward_error": fwd}
 

@@ -277,19 +277,18 @@ def rn_reciprocal(d: int, p: int):
 
 
 def lotkin(n: int, p: int) -> HostMP:
-    """First row all ones; a_ij = 1/(i+j-1) (1-based) rounded to p bits."""
-    cache = {}
-    vals = []
-    for i in range(n):
-        for j in range(n):
-            if i == 0:
-                vals.append((0, 1, 0))
-            else:
-                d = i + j + 1
-                if d not in cache:
-                    cache[d] = rn_reciprocal(d, p)
-                vals.append(cache[d])
-    return from_exact_ints(vals, p, (n, n))
+    """First row all ones; a_ij = 1/(i+j-1) (1-based) rounded to p bits.
+    Only 2n distinct values occur: they are built once and gathered."""
+    table = from_exact_ints([rn_reciprocal(d, p) if d > 0 else (0, 1, 0) for d in range(2 * n + 1)],
+                            p, (1, 2 * n + 1))
+    one = from_exact_ints([(0, 1, 0)], p, (1, 1))
+    d = np.arange(n)[:, None] + np.arange(n)[None, :] + 1          # 0-based i + j + 1
+    M = HostMP(np.ascontiguousarray(table.limb[:, 0, :][:, d]), table.exp[0, d].copy(),
+               table.sign[0, d].copy(), p)
+    M.limb[:, 0, :] = one.limb[:, 0, :1]
+    M.exp[0, :] = one.exp[0, 0]
+    M.sign[0, :] = 0
+    return M
 
 
 def ones(rows: int, cols: int, p: int) -> HostMP:
