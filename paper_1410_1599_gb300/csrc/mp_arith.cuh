@@ -290,7 +290,7 @@ MP_DEV void mul_impl(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, const RoundSpec &
         return;
     }
     int64_t e = a.e + b.e;
-    if constexpr (W <= 16) {
+    if constexpr (W <= 32) {
         uint32_t P[2 * W];
         if (rs.r == 0) {
             // p = 32W: round from the truncated product when its error bound
@@ -539,48 +539,83 @@ template <int W>
 MP_DEV void div_impl(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, const RoundSpec &rs)
 {
     const uint32_t s = a.s ^ b.s;
-    if (a.e == EXP_ZERO) { set_zero<W>(r, s); return; }
-    // remainder R (W+1 words) starts as a's mantissa; divisor D = b's mantissa
-    uint32_t R[W + 1], D[W + 1], Q[W + 1];
+    if (a.e == EXP_ZERO || b.e == EXP_ZERO) { set_zero<W>(r, s); return; }   // callers reject b = 0
+    // Schoolbook long division in radix 2^32 (Knuth, TAOCP vol. 2, Sec. 4.3.1,
+    // Algorithm D) of the integers A = a.m and D = b.m, both with the top bit
+    // set (so D needs no normalisation): Q = floor(A 2^(32(W+1)) / D) with
+    // remainder R.  Since A / D lies in (1/2, 2), Q has 32(W+1) or 32(W+1) + 1
+    // significant bits -- at least p + 32 -- and R != 0 is the sticky bit.
+    uint32_t R[W + 1], Q[W + 2];
+    // leading digit (weight 2^(32(W+1))): 1 iff A >= D; R = A - digit * D
+    uint32_t T[W];
+    T[0] = sub_cc(a.m[0], b.m[0]);
 #pragma unroll
-    for (int i = 0; i < W; ++i) { R[i] = a.m[i]; D[i] = b.m[i]; Q[i] = 0u; }
-    R[W] = 0u; D[W] = 0u; Q[W] = 0u;
-    // quotient bits q_0 (weight 1), q_1 (1/2), ..., q_{p+1}; Q holds them as an
-    // integer of p + 2 bits, most significant first
-    const int nq = rs.p + 2;
-    for (int t = 0; t < nq; ++t) {
-        // trial subtraction R - D
-        uint32_t T[W + 1];
-        T[0] = sub_cc(R[0], D[0]);
+    for (int i = 1; i < W; ++i) T[i] = subc_cc(a.m[i], b.m[i]);
+    const uint32_t q0 = subc(0u, 0u) ? 0u : 1u;
 #pragma unroll
-        for (int i = 1; i <= W; ++i) T[i] = subc_cc(R[i], D[i]);
-        const uint32_t br = subc(0u, 0u);
-        const uint32_t bit = br ? 0u : 1u;
-        if (bit) {
+    for (int i = 0; i < W; ++i) R[i] = q0 ? T[i] : a.m[i];
+    R[W] = 0u;
 #pragma unroll
-            for (int i = 0; i <= W; ++i) R[i] = T[i];
+    for (int i = 0; i < W + 2; ++i) Q[i] = 0u;
+    Q[0] = q0;
+    const uint32_t d1 = b.m[W - 1], d2 = b.m[W - 2];
+#pragma unroll 1
+    for (int t = 0; t <= W; ++t) {
+        // R < D: bring down a zero digit, R <- R 2^32 (W + 1 words)
+#pragma unroll
+        for (int i = W; i > 0; --i) R[i] = R[i - 1];
+        R[0] = 0u;
+        // estimate the digit from the top two words of R and the top word of
+        // D, then refine with the second word of D (at most two decrements)
+        const uint64_t num = ((uint64_t)R[W] << 32) | R[W - 1];
+        uint64_t qh = num / d1, rh = num - qh * d1;
+        if (qh > 0xffffffffull) {
+            qh = 0xffffffffull;
+            rh = num - qh * d1;
         }
-        // Q = 2Q + bit
+#pragma unroll 1
+        for (int c = 0; c < 2 && rh <= 0xffffffffull && qh * d2 > ((rh << 32) | R[W - 2]); ++c) {
+            --qh;
+            rh += d1;
+        }
+        const uint32_t q = (uint32_t)qh;
+        // R -= q D, one pass: product words and the borrow chain together
+        uint64_t cy = 0;
+        uint32_t br = 0u;
 #pragma unroll
-        for (int i = W; i > 0; --i) Q[i] = (Q[i] << 1) | (Q[i - 1] >> 31);
-        Q[0] = (Q[0] << 1) | bit;
-        // R = 2R
+        for (int i = 0; i < W; ++i) {
+            const uint64_t pr = (uint64_t)b.m[i] * q + cy;
+            cy = pr >> 32;
+            const uint64_t df = (uint64_t)R[i] - (uint32_t)pr - br;
+            R[i] = (uint32_t)df;
+            br = (uint32_t)(df >> 63);
+        }
+        const uint64_t dt = (uint64_t)R[W] - cy - br;
+        R[W] = (uint32_t)dt;
+        const uint32_t neg = (uint32_t)(dt >> 63);
+        uint32_t qd = q;
+        if (neg) {                              // estimate one too large: add D back
+            R[0] = add_cc(R[0], b.m[0]);
 #pragma unroll
-        for (int i = W; i > 0; --i) R[i] = (R[i] << 1) | (R[i - 1] >> 31);
-        R[0] <<= 1;
+            for (int i = 1; i < W; ++i) R[i] = addc_cc(R[i], b.m[i]);
+            R[W] = addc(R[W], 0u);
+            qd -= 1u;
+        }
+#pragma unroll
+        for (int i = W + 1; i > 0; --i) Q[i] = Q[i - 1];
+        Q[0] = qd;
     }
     bool rem = false;
 #pragma unroll
-    for (int i = 0; i <= W; ++i) rem |= R[i] != 0u;
-    // value = Q * 2^-(p+1) * 2^(ea - eb); normalise Q (p+2 or p+1 significant
-    // bits) to the top of a (W+1)-word buffer and round
-    int64_t e = a.e - b.e + 1;
-    const int lz = clz_words<W + 1>(Q);
-    shl<W + 1>(Q, lz);
-    e -= lz - (32 * (W + 1) - nq);
+    for (int i = 0; i < W; ++i) rem |= R[i] != 0u;
+    // value = Q 2^(-32(W+1)) 2^(ea - eb); the leading one is bit 0 of Q[W+1]
+    // (A >= D) or bit 31 of Q[W]
+    const int lz = q0 ? 31 : 32;
+    shl<W + 2>(Q, lz);
+    int64_t e = a.e - b.e + 32 - lz;
 #pragma unroll
-    for (int i = 0; i < W; ++i) r.m[i] = Q[i + 1];
-    round_mant<W>(r.m, e, Q[0], rem, rs);
+    for (int i = 0; i < W; ++i) r.m[i] = Q[i + 2];
+    round_mant<W>(r.m, e, Q[1], rem || Q[0] != 0u, rs);
     r.e = e;
     r.s = s;
 }
@@ -605,16 +640,18 @@ __device__ __noinline__ void div_call(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, 
     div_impl<W>(r, a, b, rs);
 }
 
-template <int W>
+// INL: inline the operation even for W = 32 (used by the GEMM inner loops,
+// where the call overhead through local memory would dominate)
+template <int W, bool INL = false>
 MP_DEV void add(Mp<W> &r, const Mp<W> &x, const Mp<W> &y, uint32_t neg_y, const RoundSpec &rs)
 {
-    if constexpr (W >= 32) add_call<W>(r, x, y, neg_y, rs);
+    if constexpr (W >= 64 || (W >= 32 && !INL)) add_call<W>(r, x, y, neg_y, rs);
     else add_impl<W>(r, x, y, neg_y, rs);
 }
-template <int W>
+template <int W, bool INL = false>
 MP_DEV void mul(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, const RoundSpec &rs)
 {
-    if constexpr (W >= 32) mul_call<W>(r, a, b, rs);
+    if constexpr (W >= 64 || (W >= 32 && !INL)) mul_call<W>(r, a, b, rs);
     else mul_impl<W>(r, a, b, rs);
 }
 template <int W>

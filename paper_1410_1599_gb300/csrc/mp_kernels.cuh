@@ -136,8 +136,8 @@ gemm_simple_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int 
     for (int64_t k = 0; k < l; ++k) {
         ld<W>(a, A, 0, i, k, rs.L);
         ld<W>(b, B, 0, k, j, rs.L);
-        mul<W>(t, a, b, rs);
-        add<W>(c, c, t, 0u, rs);
+        mul<W, true>(t, a, b, rs);
+        add<W, true>(c, c, t, 0u, rs);
     }
     if (st<W>(c, C, 0, i, j, rs.L)) flag(status, ST_RANGE);
 }
@@ -233,8 +233,8 @@ gemm_block_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p
                 a.s = (uint32_t)(sAs[ty * BK + kk] & 1);
                 bb.e = sBe[kk * BN + tx];
                 bb.s = (uint32_t)(sBs[kk * BN + tx] & 1);
-                mul<W>(t, a, bb, rs);
-                add<W>(c, c, t, 0u, rs);
+                mul<W, true>(t, a, bb, rs);
+                add<W, true>(c, c, t, 0u, rs);
             }
         }
         __syncthreads();

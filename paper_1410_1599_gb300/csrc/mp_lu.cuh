@@ -6,6 +6,12 @@
 
 namespace mpg {
 
+// threads of the single-CTA pivot kernel: fewer for wide numbers,
+// so each thread keeps its operands in registers
+template <int W> struct LuCfg {
+    static constexpr int PIVOT = (W <= 16) ? 1024 : 256;
+};
+
 // |x| > |y| on loaded numbers (zero is the smallest magnitude)
 template <int W>
 MP_DEV bool absgreater(const Mp<W> &x, const Mp<W> &y)
@@ -17,7 +23,7 @@ MP_DEV bool absgreater(const Mp<W> &x, const Mp<W> &y)
 // exchange rows k and pivot over all n columns.  A zero pivot column is
 // recorded (smallest such column wins) and nothing is exchanged.
 template <int W>
-__global__ void __launch_bounds__(1024) lu_pivot_kernel(BMat A, int64_t n, int64_t k, int64_t *piv,
+__global__ void __launch_bounds__(LuCfg<W>::PIVOT) lu_pivot_kernel(BMat A, int64_t n, int64_t k, int64_t *piv,
                                                         int p, DevStatus *status)
 {
     const RoundSpec rs = make_spec<W>(p);
@@ -132,16 +138,24 @@ __global__ void lu_rank1_kernel(BMat A, int64_t k, int64_t r0, int64_t r1, int64
     if (bad) flag(status, ST_RANGE);
 }
 
-// One CTA: x = U^-1 L^-1 P b, both substitutions column by column.  y is an
-// n x 1 work vector; x receives the solution.
+// ------------------------------------------------------- triangular solves
+// x = U^-1 L^-1 P b, both substitutions column-oriented: row i of the
+// forward pass takes y_i <- RN(y_i - RN(l_ij y_j)) for j = 0, 1, .., i-1 in
+// that order; the backward pass sets x_j = RN(y_j / u_jj) for j = n-1 down to
+// 0 and then y_i <- RN(y_i - RN(u_ij x_j)) for every i < j.  The rows are cut
+// into blocks of SB: a one-CTA kernel finishes the diagonal block (its
+// columns in order), then a grid kernel applies those columns to every row
+// beyond the block, each row taking them in the same order as above.  Every
+// y_i therefore sees exactly the update sequence of the plain column loop.
+constexpr int SB = 64;
+
+// perm = the row exchanges applied in order; y = P b
 template <int W>
-__global__ void __launch_bounds__(1024) lu_solve_kernel(BMat LU, int64_t n, const int64_t *piv,
-                                                        BMat b, BMat y, BMat x, int64_t *perm,
-                                                        int p, DevStatus *status)
+__global__ void __launch_bounds__(1024) lu_permute_kernel(int64_t n, const int64_t *piv, BMat b,
+                                                          BMat y, int64_t *perm, int p)
 {
     const RoundSpec rs = make_spec<W>(p);
     const int tid = threadIdx.x, nt = blockDim.x;
-    // permutation of the row exchanges, applied in order
     for (int64_t i = tid; i < n; i += nt) perm[i] = i;
     __syncthreads();
     if (tid == 0) {
@@ -153,54 +167,107 @@ __global__ void __launch_bounds__(1024) lu_solve_kernel(BMat LU, int64_t n, cons
         }
     }
     __syncthreads();
-    Mp<W> v, l, u, z;
     for (int64_t i = tid; i < n; i += nt) {
-        ld_rw<W>(v, b, 0, perm[i], 0, rs.L);
-        st<W>(v, y, 0, i, 0, rs.L);
+        const int64_t src = perm[i];
+        for (int q = 0; q < rs.L; ++q) y.limb[(int64_t)q * y.plane + i * y.ld] = b.limb[(int64_t)q * b.plane + src * b.ld];
+        y.exp[i * y.ld] = b.exp[src * b.ld];
+        y.sign[i * y.ld] = b.sign[src * b.ld];
     }
-    __syncthreads();
-    // forward: unit lower
-    for (int64_t j = 0; j < n; ++j) {
-        Mp<W> yj;
-        ld_rw<W>(yj, y, 0, j, 0, rs.L);
-        for (int64_t i = j + 1 + tid; i < n; i += nt) {
+}
+
+// forward, diagonal block [c0, c1): one thread per row
+template <int W>
+__global__ void __launch_bounds__(SB) lu_fwd_diag_kernel(BMat LU, BMat y, int64_t c0, int64_t c1, int p,
+                                                         DevStatus *status)
+{
+    const RoundSpec rs = make_spec<W>(p);
+    const int64_t i = c0 + threadIdx.x;
+    Mp<W> yi, yj, l, z;
+    bool bad = false;
+    if (i < c1) ld_rw<W>(yi, y, 0, i, 0, rs.L);
+    for (int64_t j = c0; j + 1 < c1; ++j) {
+        __syncthreads();                     // y_j is final
+        if (i > j && i < c1) {
+            ld_rw<W>(yj, y, 0, j, 0, rs.L);
             ld_rw<W>(l, LU, 0, i, j, rs.L);
-            ld_rw<W>(v, y, 0, i, 0, rs.L);
             mul<W>(z, l, yj, rs);
-            add<W>(v, v, z, 1u, rs);
-            st<W>(v, y, 0, i, 0, rs.L);
+            add<W>(yi, yi, z, 1u, rs);
+            if (i == j + 1) bad |= st<W>(yi, y, 0, i, 0, rs.L);    // y_i final next step
         }
-        __syncthreads();
     }
-    // backward: x_j = y_j / u_jj, then eliminate x_j from rows i < j
-    __shared__ int s_zero;
-    if (tid == 0) s_zero = 0;
-    __syncthreads();
-    for (int64_t j = n - 1; j >= 0; --j) {
-        if (tid == 0) {
-            ld_rw<W>(v, y, 0, j, 0, rs.L);
+    if (bad) flag(status, ST_RANGE);
+}
+
+// forward, rows [c1, n) take columns [c0, c1)
+template <int W>
+__global__ void lu_fwd_update_kernel(BMat LU, BMat y, int64_t n, int64_t c0, int64_t c1, int p,
+                                     DevStatus *status)
+{
+    const RoundSpec rs = make_spec<W>(p);
+    const int64_t i = c1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Mp<W> yi, yj, l, z;
+    ld_rw<W>(yi, y, 0, i, 0, rs.L);
+    for (int64_t j = c0; j < c1; ++j) {
+        ld_rw<W>(yj, y, 0, j, 0, rs.L);
+        ld_rw<W>(l, LU, 0, i, j, rs.L);
+        mul<W>(z, l, yj, rs);
+        add<W>(yi, yi, z, 1u, rs);
+    }
+    if (st<W>(yi, y, 0, i, 0, rs.L)) flag(status, ST_RANGE);
+}
+
+// backward, diagonal block [c0, c1): x_j for j = c1-1 down to c0; a zero
+// u_jj gives x_j = +0 and reports the matrix singular
+template <int W>
+__global__ void __launch_bounds__(SB) lu_bwd_diag_kernel(BMat LU, BMat y, BMat x, int64_t c0, int64_t c1,
+                                                         int p, DevStatus *status)
+{
+    const RoundSpec rs = make_spec<W>(p);
+    const int64_t i = c0 + threadIdx.x;
+    Mp<W> yi, xj, u, z;
+    bool bad = false, zero = false;
+    if (i < c1) ld_rw<W>(yi, y, 0, i, 0, rs.L);
+    for (int64_t j = c1 - 1; j >= c0; --j) {
+        if (i == j) {                        // y_j is final: x_j = y_j / u_jj
             ld_rw<W>(u, LU, 0, j, j, rs.L);
             if (u.e == EXP_ZERO) {
-                s_zero = 1;
+                zero = true;
                 set_zero<W>(z, 0u);
             } else {
-                div<W>(z, v, u, rs);
+                div<W>(z, yi, u, rs);
             }
-            st<W>(z, x, 0, j, 0, rs.L);
+            bad |= st<W>(z, x, 0, j, 0, rs.L);
         }
         __syncthreads();
-        Mp<W> xj;
-        ld_rw<W>(xj, x, 0, j, 0, rs.L);
-        for (int64_t i = tid; i < j; i += nt) {
+        if (i >= c0 && i < j) {
+            ld_rw<W>(xj, x, 0, j, 0, rs.L);
             ld_rw<W>(u, LU, 0, i, j, rs.L);
-            ld_rw<W>(v, y, 0, i, 0, rs.L);
             mul<W>(z, u, xj, rs);
-            add<W>(v, v, z, 1u, rs);
-            st<W>(v, y, 0, i, 0, rs.L);
+            add<W>(yi, yi, z, 1u, rs);
         }
-        __syncthreads();
     }
-    if (tid == 0 && s_zero) atomicOr(&status->flags, ST_SINGULAR);
+    if (zero) atomicOr(&status->flags, ST_SINGULAR);
+    if (bad) flag(status, ST_RANGE);
+}
+
+// backward, rows [0, c0) take columns c1-1 down to c0
+template <int W>
+__global__ void lu_bwd_update_kernel(BMat LU, BMat y, BMat x, int64_t c0, int64_t c1, int p,
+                                     DevStatus *status)
+{
+    const RoundSpec rs = make_spec<W>(p);
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= c0) return;
+    Mp<W> yi, xj, u, z;
+    ld_rw<W>(yi, y, 0, i, 0, rs.L);
+    for (int64_t j = c1 - 1; j >= c0; --j) {
+        ld_rw<W>(xj, x, 0, j, 0, rs.L);
+        ld_rw<W>(u, LU, 0, i, j, rs.L);
+        mul<W>(z, u, xj, rs);
+        add<W>(yi, yi, z, 1u, rs);
+    }
+    if (st<W>(yi, y, 0, i, 0, rs.L)) flag(status, ST_RANGE);
 }
 
 // ================================================================ launchers
@@ -208,7 +275,7 @@ template <int W>
 void launch_lu_pivot(BMat A, int64_t n, int64_t k, int64_t *piv, int p, DevStatus *st,
                      cudaStream_t s)
 {
-    lu_pivot_kernel<W><<<1, (W <= 16) ? 1024 : 256, 0, s>>>(A, n, k, piv, p, st);
+    lu_pivot_kernel<W><<<1, LuCfg<W>::PIVOT, 0, s>>>(A, n, k, piv, p, st);
 }
 
 template <int W>
@@ -232,8 +299,18 @@ template <int W>
 void launch_lu_solve(BMat LU, int64_t n, const int64_t *piv, BMat b, BMat y, BMat x,
                      int64_t *perm, int p, DevStatus *st, cudaStream_t s)
 {
-    const int threads = (W <= 16) ? 1024 : (W == 32 ? 512 : 256);
-    lu_solve_kernel<W><<<1, threads, 0, s>>>(LU, n, piv, b, y, x, perm, p, st);
+    constexpr int T = 64;
+    lu_permute_kernel<W><<<1, 1024, 0, s>>>(n, piv, b, y, perm, p);
+    for (int64_t c0 = 0; c0 < n; c0 += SB) {
+        const int64_t c1 = c0 + SB < n ? c0 + SB : n;
+        lu_fwd_diag_kernel<W><<<1, SB, 0, s>>>(LU, y, c0, c1, p, st);
+        if (c1 < n) lu_fwd_update_kernel<W><<<grid_for(n - c1, T), T, 0, s>>>(LU, y, n, c0, c1, p, st);
+    }
+    for (int64_t c0 = ((n - 1) / SB) * SB; c0 >= 0; c0 -= SB) {
+        const int64_t c1 = c0 + SB < n ? c0 + SB : n;
+        lu_bwd_diag_kernel<W><<<1, SB, 0, s>>>(LU, y, x, c0, c1, p, st);
+        if (c0 > 0) lu_bwd_update_kernel<W><<<grid_for(c0, T), T, 0, s>>>(LU, y, x, c0, c1, p, st);
+    }
 }
 
 #define MPG_INSTANTIATE_LU(W)                                                                   \
