@@ -55,6 +55,53 @@ def dist_env():
     return rank, world, local
 
 
+class Replicas:
+    """N independent replicas of the workload, one per rank (the product does
+    not shard: each rank multiplies its own matrices).  Nothing crosses ranks
+    on the data path; the only collectives are the timing barrier and the max
+    of the per-rank step time, and the reported value is the whole job's:
+    world x (work per rank) / (slowest rank's time)."""
+
+    def __init__(self, rank, world, backend="nccl", device="cuda"):
+        self.rank, self.world, self.backend, self.device = rank, world, backend, device
+
+    def init(self, local=0):
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            if self.backend == "nccl":
+                dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+            else:
+                dist.init_process_group(self.backend)
+
+    def seeds(self):
+        """Input seeds of this rank's A and B: every replica has its own data."""
+        return 3 + 1000 * self.rank, 4 + 1000 * self.rank
+
+    def barrier(self):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def allmax(self, x):
+        if self.world == 1:
+            return x
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def whole_job(self, work_per_rank, seconds):
+        """Aggregate rate over all ranks, from the slowest rank's time."""
+        return self.world * work_per_rank / seconds
+
+    def close(self):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
 def workload_config(a):
     return {"workload": "mp_gemm_%s_n%d_p%d_cutoff%d" % (a.algo, a.n, a.prec, a.cutoff),
             "m": a.n, "l": a.n, "n": a.n, "prec_bits": a.prec, "algo": a.algo,
@@ -125,27 +172,15 @@ def run_ours(a, rank, world, local):
 
     libbuild.build()
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
-    def allmax(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    rep = Replicas(rank, world)
+    rep.init(local)
+    barrier, allmax = rep.barrier, rep.allmax
 
     n, p, cutoff, algo = a.n, a.prec, a.cutoff, ALGO_NAMES[a.algo]
     flops = 2.0 * n * n * n
-    A = gen.uniform_pm1(n, n, p, 3 + 1000 * rank, -16, 16)
-    B = gen.uniform_pm1(n, n, p, 4 + 1000 * rank, -16, 16)
+    seed_a, seed_b = rep.seeds()
+    A = gen.uniform_pm1(n, n, p, seed_a, -16, 16)
+    B = gen.uniform_pm1(n, n, p, seed_b, -16, 16)
     dA, dB = mp.DeviceMP.from_host(A), mp.DeviceMP.from_host(B)
     dC = mp.DeviceMP.empty(n, n, p)
     stream = torch.cuda.Stream()
@@ -176,7 +211,7 @@ def run_ours(a, rank, world, local):
     mp.check_status("timed")
     barrier()
     ms = allmax(ms)
-    value = world * flops / (ms * 1e-3) / 1e9
+    value = rep.whole_job(flops, ms * 1e-3) / 1e9
 
     # kernel-level timing of the same steps (CUDA events around every launch)
     mp.profile_enable(True)
@@ -300,7 +335,7 @@ def run_ours(a, rank, world, local):
                          "work_per_madd_imad": imad_per_madd, "traffic": None},
             "kernels": kernels,
             "gpu_launches": int(round(launches_per_step * a.steps)),
-            "e2e": {"value": round(world * flops / (e2e_ms * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
+            "e2e": {"value": round(rep.whole_job(flops, e2e_ms * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "clocks": clk,
             "algos_gflops": extras,
@@ -318,9 +353,7 @@ def run_ours(a, rank, world, local):
         if serving:
             line["serving"] = serving
         print(json.dumps(line), flush=True)
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    rep.close()
 
 
 def lu_run(n, p, algo, panel=128, cutoff=64, kind="well"):
@@ -581,7 +614,7 @@ def run_reference(a, rank, world):
 
     from oracle import oracle as orc
     threads = orc.max_threads()
-    per_step = max(threads, int(256 * 512 / p))
+    per_step = min(n, max(threads, int(256 * 512 / p)))
     rng = np.random.default_rng(1)
     subs = []
     for s in range(a.warmup + a.steps):
