@@ -532,9 +532,9 @@ MP_DEV int cmpabs(const Mp<W> &a, const Mp<W> &b)
 }
 
 // --------------------------------------------------------------- division
-// r = RN_p(a / b), b != 0.  Binary restoring division of the mantissas
-// producing p + 2 quotient bits (the quotient of two fractions in [1/2, 1)
-// lies in (1/2, 2)), then one rounding with the remainder as sticky.
+// r = RN_p(a / b), b != 0: exact long division of the mantissas (the
+// quotient of two fractions in [1/2, 1) lies in (1/2, 2)), then one rounding
+// with the remainder as sticky.
 template <int W>
 MP_DEV void div_impl(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, const RoundSpec &rs)
 {
@@ -559,6 +559,10 @@ MP_DEV void div_impl(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, const RoundSpec &
     for (int i = 0; i < W + 2; ++i) Q[i] = 0u;
     Q[0] = q0;
     const uint32_t d1 = b.m[W - 1], d2 = b.m[W - 2];
+    // reciprocal of the top divisor word for the two-by-one digit division
+    // (Moller and Granlund, "Improved division by invariant integers", 2011,
+    // Alg. 4): v = floor((2^64 - 1) / d1) - 2^32
+    const uint32_t v = (uint32_t)(0xffffffffffffffffull / d1 - 0x100000000ull);
 #pragma unroll 1
     for (int t = 0; t <= W; ++t) {
         // R < D: bring down a zero digit, R <- R 2^32 (W + 1 words)
@@ -567,11 +571,20 @@ MP_DEV void div_impl(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, const RoundSpec &
         R[0] = 0u;
         // estimate the digit from the top two words of R and the top word of
         // D, then refine with the second word of D (at most two decrements)
-        const uint64_t num = ((uint64_t)R[W] << 32) | R[W - 1];
-        uint64_t qh = num / d1, rh = num - qh * d1;
-        if (qh > 0xffffffffull) {
+        const uint32_t u1 = R[W], u0 = R[W - 1];
+        uint64_t qh, rh;
+        if (u1 >= d1) {                         // u1 == d1: the digit estimate saturates
             qh = 0xffffffffull;
-            rh = num - qh * d1;
+            rh = (((uint64_t)u1 << 32) | u0) - qh * d1;
+        } else {
+            const uint64_t t = (uint64_t)v * u1 + (((uint64_t)u1 << 32) | u0);   // mod 2^64
+            uint32_t q1 = (uint32_t)(t >> 32) + 1u;
+            const uint32_t q0 = (uint32_t)t;
+            uint32_t rr = u0 - q1 * d1;
+            if (rr > q0) { q1 -= 1u; rr += d1; }
+            if (rr >= d1) { q1 += 1u; rr -= d1; }
+            qh = q1;
+            rh = rr;
         }
 #pragma unroll 1
         for (int c = 0; c < 2 && rh <= 0xffffffffull && qh * d2 > ((rh << 32) | R[W - 2]); ++c) {

@@ -2,14 +2,14 @@
 // and the triangular solves (arXiv 1410.1599 Sec. 4), one instantiation per
 // word-capacity class W (lu_w*.cu).
 #pragma once
-#include "mp_kernels.cuh"
+#include "mp_warp.cuh"
 
 namespace mpg {
 
 // threads of the single-CTA pivot kernel: fewer for wide numbers,
 // so each thread keeps its operands in registers
 template <int W> struct LuCfg {
-    static constexpr int PIVOT = (W <= 16) ? 1024 : 256;
+    static constexpr int PIVOT = (W <= 8) ? 512 : 256;
 };
 
 // |x| > |y| on loaded numbers (zero is the smallest magnitude)
@@ -22,48 +22,68 @@ MP_DEV bool absgreater(const Mp<W> &x, const Mp<W> &y)
 // One CTA: pivot = first row i in [k, n) of largest |a_ik|; record it, then
 // exchange rows k and pivot over all n columns.  A zero pivot column is
 // recorded (smallest such column wins) and nothing is exchanged.
+//
+// Each thread finds the first largest of its rows by full comparison.  The
+// block then reduces the key (exponent, top 64 mantissa bits), which orders
+// magnitudes except between numbers that agree in the key; the threads whose
+// candidate carries the largest key list it, and one thread settles the list
+// (usually one entry) by full comparison, lower row first among equals.
 template <int W>
 __global__ void __launch_bounds__(LuCfg<W>::PIVOT) lu_pivot_kernel(BMat A, int64_t n, int64_t k, int64_t *piv,
                                                         int p, DevStatus *status)
 {
+    constexpr int NT = LuCfg<W>::PIVOT, NW = NT / 32;
     const RoundSpec rs = make_spec<W>(p);
-    __shared__ int64_t s_row[1024];
+    __shared__ int64_t s_row[NT];
+    __shared__ int64_t s_we[NW];
+    __shared__ uint64_t s_wm[NW];
+    __shared__ int s_nc;
     __shared__ int64_t s_best;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    // per thread: best candidate by (exponent, then limbs, then lowest row)
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     int64_t best = -1;
     Mp<W> bx, x;
     set_zero<W>(bx, 0u);
-    for (int64_t i = k + tid; i < n; i += nt) {
+    for (int64_t i = k + tid; i < n; i += NT) {
         ld_rw<W>(x, A, 0, i, k, rs.L);
         if (best < 0 || absgreater<W>(x, bx)) {
             best = i;
             bx = x;
         }
     }
-    s_row[tid] = best;
+    if (tid == 0) s_nc = 0;
+    // key of this thread's candidate (no candidate or zero: smallest key)
+    const int64_t ke = (best < 0) ? EXP_ZERO : bx.e;
+    const uint64_t km = (best < 0 || bx.e == EXP_ZERO)
+                            ? 0ull : (((uint64_t)bx.m[W - 1] << 32) | bx.m[W - 2]);
+    int64_t me = ke;
+    uint64_t mm = km;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const int64_t oe = __shfl_xor_sync(0xffffffffu, me, o);
+        const uint64_t om = __shfl_xor_sync(0xffffffffu, mm, o);
+        if (oe > me || (oe == me && om > mm)) { me = oe; mm = om; }
+    }
+    if (lane == 0) { s_we[wid] = me; s_wm[wid] = mm; }
     __syncthreads();
-    // tree reduction: compare through global memory reloads (rows are few)
-    for (int stride = nt / 2; stride > 0; stride >>= 1) {
-        if (tid < stride) {
-            const int64_t ra = s_row[tid], rb = s_row[tid + stride];
-            if (rb >= 0) {
-                bool take = false;
-                if (ra < 0) take = true;
-                else {
-                    Mp<W> xa, xb;
-                    ld_rw<W>(xa, A, 0, ra, k, rs.L);
-                    ld_rw<W>(xb, A, 0, rb, k, rs.L);
-                    const int c = cmpabs<W>(xb, xa);
-                    take = c > 0 || (c == 0 && rb < ra);
-                }
-                if (take) s_row[tid] = rb;
+    me = s_we[0];
+    mm = s_wm[0];
+    for (int w = 1; w < NW; ++w)
+        if (s_we[w] > me || (s_we[w] == me && s_wm[w] > mm)) { me = s_we[w]; mm = s_wm[w]; }
+    if (best >= 0 && ke == me && km == mm) s_row[atomicAdd(&s_nc, 1)] = best;
+    __syncthreads();
+    if (tid == 0) {
+        int64_t pr = k;
+        if (s_nc > 0) {
+            pr = s_row[0];
+            Mp<W> xa, xb;
+            ld_rw<W>(xa, A, 0, pr, k, rs.L);
+            for (int c = 1; c < s_nc; ++c) {
+                const int64_t rb = s_row[c];
+                ld_rw<W>(xb, A, 0, rb, k, rs.L);
+                const int cmp = cmpabs<W>(xb, xa);
+                if (cmp > 0 || (cmp == 0 && rb < pr)) { pr = rb; xa = xb; }
             }
         }
-        __syncthreads();
-    }
-    if (tid == 0) {
-        const int64_t pr = s_row[0] < 0 ? k : s_row[0];
         Mp<W> v;
         ld_rw<W>(v, A, 0, pr, k, rs.L);
         piv[k] = pr;
@@ -79,7 +99,7 @@ __global__ void __launch_bounds__(LuCfg<W>::PIVOT) lu_pivot_kernel(BMat A, int64
     const int64_t pr = s_best;
     if (pr == k) return;
     const int L = rs.L;
-    for (int64_t c = tid; c < n; c += nt) {
+    for (int64_t c = tid; c < n; c += NT) {
         for (int q = 0; q < L; ++q) {
             uint64_t *a = A.limb + (int64_t)q * A.plane + k * A.ld + c;
             uint64_t *b = A.limb + (int64_t)q * A.plane + pr * A.ld + c;
@@ -99,19 +119,37 @@ __global__ void __launch_bounds__(LuCfg<W>::PIVOT) lu_pivot_kernel(BMat A, int64
 }
 
 // l_ik = RN(a_ik / a_kk) for i in (k, n); a zero a_kk (already reported by
-// the pivot step) leaves the column untouched
+// the pivot step) leaves the column untouched.  Up to 1024 bits one warp
+// forms each quotient (the division's latency is on the critical path of
+// the factorisation); wider numbers take one thread per row.
 template <int W>
 __global__ void lu_divide_kernel(BMat A, int64_t n, int64_t k, int p)
 {
     const RoundSpec rs = make_spec<W>(p);
-    Mp<W> d, x, q;
-    ld_rw<W>(d, A, 0, k, k, rs.L);
-    if (d.e == EXP_ZERO) return;
-    for (int64_t i = k + 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        ld_rw<W>(x, A, 0, i, k, rs.L);
-        div<W>(q, x, d, rs);
-        st<W>(q, A, 0, i, k, rs.L);
+    if constexpr (W <= 32) {
+        const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;
+        int64_t de;
+        uint32_t ds;
+        const uint32_t dm = wld<W>(A, 0, k, k, rs.L, de, ds);
+        if (de == EXP_ZERO) return;
+        for (int64_t i = k + 1 + (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; i < n;
+             i += nwarps) {
+            int64_t xe, qe;
+            uint32_t xs, qs;
+            const uint32_t xm = wld<W>(A, 0, i, k, rs.L, xe, xs);
+            const uint32_t qm = warp_div<W>(xm, xe, xs, dm, de, ds, qe, qs, rs);
+            wst<W>(qm, qe, qs, A, 0, i, k, rs.L);
+        }
+    } else {
+        Mp<W> d, x, q;
+        ld_rw<W>(d, A, 0, k, k, rs.L);
+        if (d.e == EXP_ZERO) return;
+        for (int64_t i = k + 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            ld_rw<W>(x, A, 0, i, k, rs.L);
+            div<W>(q, x, d, rs);
+            st<W>(q, A, 0, i, k, rs.L);
+        }
     }
 }
 
@@ -131,8 +169,8 @@ __global__ void lu_rank1_kernel(BMat A, int64_t k, int64_t r0, int64_t r1, int64
         ld_rw<W>(l, A, 0, i, k, rs.L);
         ld_rw<W>(u, A, 0, k, j, rs.L);
         ld_rw<W>(y, A, 0, i, j, rs.L);
-        mul<W>(z, l, u, rs);
-        add<W>(y, y, z, 1u, rs);
+        mul<W, true>(z, l, u, rs);
+        add<W, true>(y, y, z, 1u, rs);
         bad |= st<W>(y, A, 0, i, j, rs.L);
     }
     if (bad) flag(status, ST_RANGE);
@@ -190,8 +228,8 @@ __global__ void __launch_bounds__(SB) lu_fwd_diag_kernel(BMat LU, BMat y, int64_
         if (i > j && i < c1) {
             ld_rw<W>(yj, y, 0, j, 0, rs.L);
             ld_rw<W>(l, LU, 0, i, j, rs.L);
-            mul<W>(z, l, yj, rs);
-            add<W>(yi, yi, z, 1u, rs);
+            mul<W, true>(z, l, yj, rs);
+            add<W, true>(yi, yi, z, 1u, rs);
             if (i == j + 1) bad |= st<W>(yi, y, 0, i, 0, rs.L);    // y_i final next step
         }
     }
@@ -211,14 +249,15 @@ __global__ void lu_fwd_update_kernel(BMat LU, BMat y, int64_t n, int64_t c0, int
     for (int64_t j = c0; j < c1; ++j) {
         ld_rw<W>(yj, y, 0, j, 0, rs.L);
         ld_rw<W>(l, LU, 0, i, j, rs.L);
-        mul<W>(z, l, yj, rs);
-        add<W>(yi, yi, z, 1u, rs);
+        mul<W, true>(z, l, yj, rs);
+        add<W, true>(yi, yi, z, 1u, rs);
     }
     if (st<W>(yi, y, 0, i, 0, rs.L)) flag(status, ST_RANGE);
 }
 
 // backward, diagonal block [c0, c1): x_j for j = c1-1 down to c0; a zero
-// u_jj gives x_j = +0 and reports the matrix singular
+// u_jj gives x_j = +0 and reports the matrix singular.  Up to 1024 bits the
+// first warp forms each x_j together.
 template <int W>
 __global__ void __launch_bounds__(SB) lu_bwd_diag_kernel(BMat LU, BMat y, BMat x, int64_t c0, int64_t c1,
                                                          int p, DevStatus *status)
@@ -229,22 +268,42 @@ __global__ void __launch_bounds__(SB) lu_bwd_diag_kernel(BMat LU, BMat y, BMat x
     bool bad = false, zero = false;
     if (i < c1) ld_rw<W>(yi, y, 0, i, 0, rs.L);
     for (int64_t j = c1 - 1; j >= c0; --j) {
-        if (i == j) {                        // y_j is final: x_j = y_j / u_jj
-            ld_rw<W>(u, LU, 0, j, j, rs.L);
-            if (u.e == EXP_ZERO) {
-                zero = true;
-                set_zero<W>(z, 0u);
-            } else {
-                div<W>(z, yi, u, rs);
+        if constexpr (W <= 32) {
+            if (i == j) st<W>(yi, y, 0, j, 0, rs.L);          // y_j is final
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                int64_t ye, ue, qe;
+                uint32_t ys, us, qs;
+                const uint32_t um = wld<W>(LU, 0, j, j, rs.L, ue, us);
+                const uint32_t ym = wld<W>(y, 0, j, 0, rs.L, ye, ys);
+                uint32_t qm = 0u;
+                if (ue == EXP_ZERO) {
+                    zero = true;
+                    qe = EXP_ZERO;
+                    qs = 0u;
+                } else {
+                    qm = warp_div<W>(ym, ye, ys, um, ue, us, qe, qs, rs);
+                }
+                bad |= wst<W>(qm, qe, qs, x, 0, j, 0, rs.L);
             }
-            bad |= st<W>(z, x, 0, j, 0, rs.L);
+        } else {
+            if (i == j) {                        // y_j is final: x_j = y_j / u_jj
+                ld_rw<W>(u, LU, 0, j, j, rs.L);
+                if (u.e == EXP_ZERO) {
+                    zero = true;
+                    set_zero<W>(z, 0u);
+                } else {
+                    div<W>(z, yi, u, rs);
+                }
+                bad |= st<W>(z, x, 0, j, 0, rs.L);
+            }
         }
         __syncthreads();
         if (i >= c0 && i < j) {
             ld_rw<W>(xj, x, 0, j, 0, rs.L);
             ld_rw<W>(u, LU, 0, i, j, rs.L);
-            mul<W>(z, u, xj, rs);
-            add<W>(yi, yi, z, 1u, rs);
+            mul<W, true>(z, u, xj, rs);
+            add<W, true>(yi, yi, z, 1u, rs);
         }
     }
     if (zero) atomicOr(&status->flags, ST_SINGULAR);
@@ -264,8 +323,8 @@ __global__ void lu_bwd_update_kernel(BMat LU, BMat y, BMat x, int64_t c0, int64_
     for (int64_t j = c1 - 1; j >= c0; --j) {
         ld_rw<W>(xj, x, 0, j, 0, rs.L);
         ld_rw<W>(u, LU, 0, i, j, rs.L);
-        mul<W>(z, u, xj, rs);
-        add<W>(yi, yi, z, 1u, rs);
+        mul<W, true>(z, u, xj, rs);
+        add<W, true>(yi, yi, z, 1u, rs);
     }
     if (st<W>(yi, y, 0, i, 0, rs.L)) flag(status, ST_RANGE);
 }
@@ -283,7 +342,10 @@ void launch_lu_divide(BMat A, int64_t n, int64_t k, int p, cudaStream_t s)
 {
     const int64_t rows = n - k - 1;
     if (rows <= 0) return;
-    lu_divide_kernel<W><<<grid_for(rows, 64), 64, 0, s>>>(A, n, k, p);
+    if constexpr (W <= 32)
+        lu_divide_kernel<W><<<grid_for(rows * 32, 128), 128, 0, s>>>(A, n, k, p);
+    else
+        lu_divide_kernel<W><<<grid_for(rows, 64), 64, 0, s>>>(A, n, k, p);
 }
 
 template <int W>
