@@ -375,28 +375,50 @@ MP_DEV int warp_max(int v)
 // x (N words) >>= sh bits, 0 <= sh <= 32N; returns the OR of the bits
 // shifted out.  A select network over the word shift; stages no lane of the
 // warp needs are skipped (warp-uniform branch).
+// one stage of the word-shift select network per bit J of the word count;
+// the stages are expanded at compile time so every index is a constant
+template <int N, int J>
+MP_DEV void shr_words_stage(uint32_t (&x)[N], int q, int qmax, uint32_t &st)
+{
+    if constexpr ((1 << J) <= N) {
+        constexpr int d = 1 << J;
+        if (qmax >= d) {
+            const bool on = (q >> J) & 1;
+#pragma unroll
+            for (int i = 0; i < d && i < N; ++i) st |= on ? x[i] : 0u;
+#pragma unroll
+            for (int i = 0; i < N; ++i) x[i] = on ? ((i + d < N) ? x[i + d] : 0u) : x[i];
+        }
+        shr_words_stage<N, J + 1>(x, q, qmax, st);
+    }
+}
+
 template <int N>
 MP_DEV uint32_t shr_sticky(uint32_t (&x)[N], int sh)
 {
     const int q = sh >> 5, b = sh & 31;
     const int qmax = warp_max(q);
     uint32_t st = 0u;
-#pragma unroll
-    for (int j = 0; (1 << j) <= N; ++j) {
-        const int d = 1 << j;
-        if (qmax >= d) {
-            const bool on = (q >> j) & 1;
-#pragma unroll
-            for (int i = 0; i < d && i < N; ++i) st |= on ? x[i] : 0u;
-#pragma unroll
-            for (int i = 0; i < N; ++i) x[i] = on ? ((i + d < N) ? x[i + d] : 0u) : x[i];
-        }
-    }
+    shr_words_stage<N, 0>(x, q, qmax, st);
     st |= x[0] & ((1u << b) - 1u);
 #pragma unroll
     for (int i = 0; i < N - 1; ++i) x[i] = __funnelshift_r(x[i], x[i + 1], b);
     x[N - 1] >>= b;
     return st;
+}
+
+template <int N, int J>
+MP_DEV void shl_words_stage(uint32_t (&x)[N], int q, int qmax)
+{
+    if constexpr ((1 << J) < N) {
+        constexpr int d = 1 << J;
+        if (qmax >= d) {
+            const bool on = (q >> J) & 1;
+#pragma unroll
+            for (int i = N - 1; i >= 0; --i) x[i] = on ? ((i - d >= 0) ? x[i - d] : 0u) : x[i];
+        }
+        shl_words_stage<N, J + 1>(x, q, qmax);
+    }
 }
 
 // x (N words) <<= sh bits, 0 <= sh < 32N
@@ -405,15 +427,7 @@ MP_DEV void shl(uint32_t (&x)[N], int sh)
 {
     const int q = sh >> 5, b = sh & 31;
     const int qmax = warp_max(q);
-#pragma unroll
-    for (int j = 0; (1 << j) < N; ++j) {
-        const int d = 1 << j;
-        if (qmax >= d) {
-            const bool on = (q >> j) & 1;
-#pragma unroll
-            for (int i = N - 1; i >= 0; --i) x[i] = on ? ((i - d >= 0) ? x[i - d] : 0u) : x[i];
-        }
-    }
+    shl_words_stage<N, 0>(x, q, qmax);
 #pragma unroll
     for (int i = N - 1; i > 0; --i) x[i] = __funnelshift_l(x[i - 1], x[i], b);
     x[0] <<= b;
@@ -489,7 +503,7 @@ MP_DEV void add_impl(Mp<W> &r, const Mp<W> &x, const Mp<W> &y, uint32_t neg_y, c
     // S = X + (Y ^ mask) + cin; the first add only loads cin into the carry flag
     const uint32_t mask = 0u - eff_sub;
     const uint32_t cin = eff_sub & (st == 0u ? 1u : 0u);
-    uint32_t S[W + 1];
+    uint32_t (&S)[W + 1] = X;                    // the sum replaces X
     (void)add_cc(cin, 0xffffffffu);
 #pragma unroll
     for (int i = 0; i <= W; ++i) S[i] = addc_cc(X[i], Y[i] ^ mask);

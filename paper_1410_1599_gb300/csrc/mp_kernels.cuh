@@ -242,6 +242,199 @@ gemm_block_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p
     if (valid && st<W>(c, C, b, i, j, L)) flag(status, ST_RANGE);
 }
 
+// ------------------------------------------ Block leaf for 2048-bit numbers
+// At W = 64 three register-resident operands do not fit in a thread's 255
+// registers.  Here each thread keeps c and a_ik in registers and reads b_kj
+// word by word from shared memory (four words per 16-byte load) while it
+// forms the product, so nothing goes through local memory.  The slab of B
+// is stored one element per BW-word record (mantissa words little-endian,
+// padded from 64 to 68 words: a warp's 16-byte loads then hit every bank
+// once).  Values and summation order are those of gemm_block_kernel.
+constexpr int BW64 = 68;
+
+// top words of the truncated product a * b, b read from shared memory:
+// acc[q] = word W-2+q of sum_{i+j >= W-2} a_i b_j 2^(32(i+j))
+template <int W>
+MP_DEV void mul_trunc_sm(uint32_t (&acc)[W + 2], const uint32_t (&a)[W], const uint32_t *b)
+{
+#pragma unroll
+    for (int q = 0; q < W + 2; ++q) acc[q] = 0u;
+#pragma unroll
+    for (int j0 = 0; j0 < W; j0 += 4) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(b + j0);
+        const uint32_t bv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = j0 + u;
+            const uint32_t bj = bv[u];
+            const int i0 = (W - 2 - j > 0) ? W - 2 - j : 0;
+            // position i + j lives in acc[i + j - (W - 2)]
+            acc[j + i0 - (W - 2)] = mad_lo_cc(a[i0], bj, acc[j + i0 - (W - 2)]);
+#pragma unroll
+            for (int i = i0 + 1; i < W; ++i) acc[j + i - (W - 2)] = madc_lo_cc(a[i], bj, acc[j + i - (W - 2)]);
+            acc[j + 2] = addc(acc[j + 2], 0u);
+            acc[j + i0 + 1 - (W - 2)] = mad_hi_cc(a[i0], bj, acc[j + i0 + 1 - (W - 2)]);
+#pragma unroll
+            for (int i = i0 + 1; i < W - 1; ++i)
+                acc[j + 1 + i - (W - 2)] = madc_hi_cc(a[i], bj, acc[j + 1 + i - (W - 2)]);
+            acc[j + 2] = madc_hi(a[W - 1], bj, acc[j + 2]);
+        }
+    }
+}
+
+// t = RN_p(a * b) with b's mantissa in shared memory (p = 32W or below)
+template <int W>
+MP_DEV void mul_sm(Mp<W> &t, const uint32_t (&am)[W], int64_t ae, uint32_t as, const uint32_t *bm,
+                   int64_t be, uint32_t bs, const RoundSpec &rs)
+{
+    t.s = as ^ bs;
+    if (ae == EXP_ZERO || be == EXP_ZERO) {
+        set_zero<W>(t, t.s);
+        return;
+    }
+    int64_t e = ae + be;
+    if (rs.r == 0) {
+        // the truncation test of mul_impl: decide from the truncated product
+        // unless its error bound reaches the rounding boundary
+        uint32_t acc[W + 2];
+        mul_trunc_sm<W>(acc, am, bm);
+        const uint32_t w = acc[1];
+        const uint32_t top = acc[W + 1] >> 31;
+        const int rpos = top ? 31 : 30;
+        const uint32_t wend = w + (uint32_t)(W - 1);
+        const uint32_t rb = (w >> rpos) & 1u;
+        const bool safe = (wend >= w) && ((w >> rpos) == (wend >> rpos)) &&
+                          !(rb && (w & ((1u << rpos) - 1u)) == 0u);
+        if (safe) {
+            if (!top) {
+#pragma unroll
+                for (int i = W + 1; i > 2; --i) acc[i] = __funnelshift_l(acc[i - 1], acc[i], 1);
+                acc[2] = __funnelshift_l(w, acc[2], 1);
+                e -= 1;
+            }
+            acc[2] = add_cc(acc[2], rb);
+#pragma unroll
+            for (int i = 3; i < W + 2; ++i) acc[i] = addc_cc(acc[i], 0u);
+            const uint32_t c = addc(0u, 0u);
+#pragma unroll
+            for (int i = 0; i < W; ++i) t.m[i] = acc[i + 2];
+            if (c) {
+                t.m[W - 1] = 0x80000000u;
+                e += 1;
+            }
+            t.e = e;
+            return;
+        }
+    }
+    // exact top half with sticky (rare for p = 32W)
+    uint32_t pw1, pw2;
+    bool low_nz;
+    mul_top<W>(t.m, pw1, pw2, low_nz, am, bm);
+    if (!(t.m[W - 1] >> 31)) {
+#pragma unroll
+        for (int i = W - 1; i > 0; --i) t.m[i] = (t.m[i] << 1) | (t.m[i - 1] >> 31);
+        t.m[0] = (t.m[0] << 1) | (pw1 >> 31);
+        pw1 = (pw1 << 1) | (pw2 >> 31);
+        pw2 <<= 1;
+        e -= 1;
+    }
+    round_mant<W>(t.m, e, pw1, low_nz || pw2 != 0u, rs);
+    t.e = e;
+}
+
+struct Block64Cfg {
+    static constexpr int W = 64, BN = 32, BM = 4, BK = 4, THREADS = BM * BN;
+    static constexpr size_t smem()
+    {
+        return (size_t)BK * BN * BW64 * 4 + (size_t)BM * BK * W * 4 + (size_t)(BM * BK + BK * BN) * 9;
+    }
+};
+
+template <int W>
+__global__ void __launch_bounds__(Block64Cfg::THREADS)
+gemm_block64_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p,
+                    int64_t tiles_m, int64_t tiles_n, DevStatus *status)
+{
+    using Cfg = Block64Cfg;
+    static_assert(W == Cfg::W, "2048-bit leaf");
+    constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const RoundSpec rs = make_spec<W>(p);
+    const int L = rs.L;
+    // [BK][BN] records of BW64 words, [BM][BK] records of W words, exps, signs
+    uint32_t *sB = reinterpret_cast<uint32_t *>(smem_raw);
+    uint32_t *sA = sB + BK * BN * BW64;
+    int64_t *sAe = reinterpret_cast<int64_t *>(sA + BM * BK * W);
+    int64_t *sBe = sAe + BM * BK;
+    int8_t *sAs = reinterpret_cast<int8_t *>(sBe + BK * BN);
+    int8_t *sBs = sAs + BM * BK;
+
+    const int64_t tile = blockIdx.x;
+    const int64_t b = tile / (tiles_m * tiles_n);
+    const int64_t tm = (tile / tiles_n) % tiles_m, tn = tile % tiles_n;
+    const int tx = threadIdx.x % BN, ty = threadIdx.x / BN;
+    const int64_t i = tm * BM + ty, j = tn * BN + tx;
+    const bool valid = (i < m) && (j < n);
+
+    Mp<W> c, t;
+    set_zero<W>(c, 0u);
+    for (int64_t k0 = 0; k0 < l; k0 += BK) {
+        const int kc = (int)((l - k0) < BK ? (l - k0) : BK);
+        // limb q of a record goes to words W-2-2q (low half) and W-1-2q
+        for (int e = threadIdx.x; e < W / 2 * BK * BN; e += blockDim.x) {
+            const int cc = e % BN, kk = (e / BN) % BK, q = e / (BN * BK);
+            const int64_t gj = tn * BN + cc, gk = k0 + kk;
+            const uint64_t v = (q < L && gj < n && kk < kc)
+                                   ? __ldg(B.limb + b * B.bs_limb + (int64_t)q * B.plane + gk * B.ld + gj)
+                                   : 0ull;
+            *reinterpret_cast<uint64_t *>(sB + (kk * BN + cc) * BW64 + (W - 2 - 2 * q)) = v;
+        }
+        for (int e = threadIdx.x; e < W / 2 * BM * BK; e += blockDim.x) {
+            const int kk = e % BK, rr = (e / BK) % BM, q = e / (BK * BM);
+            const int64_t gi = tm * BM + rr, gk = k0 + kk;
+            const uint64_t v = (q < L && gi < m && kk < kc)
+                                   ? __ldg(A.limb + b * A.bs_limb + (int64_t)q * A.plane + gi * A.ld + gk)
+                                   : 0ull;
+            *reinterpret_cast<uint64_t *>(sA + (rr * BK + kk) * W + (W - 2 - 2 * q)) = v;
+        }
+        for (int e = threadIdx.x; e < BM * BK; e += blockDim.x) {
+            const int kk = e % BK, rr = e / BK;
+            const int64_t gi = tm * BM + rr, gk = k0 + kk;
+            const bool ok = gi < m && kk < kc;
+            sAe[e] = ok ? __ldg(A.exp + b * A.bs_es + gi * A.ld + gk) : EXP_ZERO;
+            sAs[e] = ok ? __ldg(A.sign + b * A.bs_es + gi * A.ld + gk) : (int8_t)0;
+        }
+        for (int e = threadIdx.x; e < BK * BN; e += blockDim.x) {
+            const int cc = e % BN, kk = e / BN;
+            const int64_t gj = tn * BN + cc, gk = k0 + kk;
+            const bool ok = gj < n && kk < kc;
+            sBe[e] = ok ? __ldg(B.exp + b * B.bs_es + gk * B.ld + gj) : EXP_ZERO;
+            sBs[e] = ok ? __ldg(B.sign + b * B.bs_es + gk * B.ld + gj) : (int8_t)0;
+        }
+        __syncthreads();
+        if (valid) {
+            for (int kk = 0; kk < kc; ++kk) {
+                uint32_t am[W];
+                const uint32_t *ap = sA + (ty * BK + kk) * W;
+#pragma unroll
+                for (int q = 0; q < W; q += 4) {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(ap + q);
+                    am[q] = v.x;
+                    am[q + 1] = v.y;
+                    am[q + 2] = v.z;
+                    am[q + 3] = v.w;
+                }
+                mul_sm<W>(t, am, sAe[ty * BK + kk], (uint32_t)(sAs[ty * BK + kk] & 1),
+                          sB + (kk * BN + tx) * BW64, sBe[kk * BN + tx],
+                          (uint32_t)(sBs[kk * BN + tx] & 1), rs);
+                add_impl<W>(c, c, t, 0u, rs);
+            }
+        }
+        __syncthreads();
+    }
+    if (valid && st<W>(c, C, b, i, j, L)) flag(status, ST_RANGE);
+}
+
 // ------------------------------------------- recursion: operand sums (Sec. 2)
 // Thread per (node, r < h, c < k).  Quadrant reads outside the parent's real
 // m x l are zero (padding); the even part never reaches a peeled last row
@@ -504,17 +697,30 @@ void launch_gemm_block(BMat A, BMat B, BMat C, int64_t batch, int64_t m, int64_t
 {
     using Cfg = BlockCfg<W>;
     if (batch <= 0 || m <= 0 || n <= 0) return;
-    const int L = (p + 63) >> 6;
-    const int64_t tm = (m + Cfg::BM - 1) / Cfg::BM, tn = (n + Cfg::BN - 1) / Cfg::BN;
-    const size_t sm = Cfg::smem(L);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(gemm_block_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Cfg::smem(W / 2));
-        attr_set = true;
+    if constexpr (W == 64) {
+        using C64 = Block64Cfg;
+        const int64_t tm = (m + C64::BM - 1) / C64::BM, tn = (n + C64::BN - 1) / C64::BN;
+        static bool attr64 = false;
+        if (!attr64) {
+            cudaFuncSetAttribute(gemm_block64_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)C64::smem());
+            attr64 = true;
+        }
+        gemm_block64_kernel<64><<<(unsigned)(batch * tm * tn), C64::THREADS, C64::smem(), s>>>(
+            A, B, C, m, l, n, p, tm, tn, st);
+    } else {
+        const int L = (p + 63) >> 6;
+        const int64_t tm = (m + Cfg::BM - 1) / Cfg::BM, tn = (n + Cfg::BN - 1) / Cfg::BN;
+        const size_t sm = Cfg::smem(L);
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaFuncSetAttribute(gemm_block_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Cfg::smem(W / 2));
+            attr_set = true;
+        }
+        gemm_block_kernel<W><<<(unsigned)(batch * tm * tn), Cfg::THREADS, sm, s>>>(
+            A, B, C, m, l, n, p, tm, tn, st);
     }
-    gemm_block_kernel<W><<<(unsigned)(batch * tm * tn), Cfg::THREADS, sm, s>>>(
-        A, B, C, m, l, n, p, tm, tn, st);
 }
 
 template <int W>
