@@ -24,6 +24,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 ALGO_NAMES = {"simple": 0, "block": 1, "strassen": 2, "winograd": 3}
+# DRAM bytes (read + write) of one leaf launch of the 512-bit Winograd product
+# with cutoff 64, per 64^3 leaf: one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of the current leaf kernel at n = 1024 (2401 leaves,
+# 2.136 GB), scaled by the leaves of a launch.  Reset to None whenever the
+# leaf kernel changes.
+LEAF_TRAFFIC_PER_LEAF_P512_C64 = 2.136e9 / 2401
 PEAK_IMAD_PER_CLK_PER_SM = 64      # 32-bit integer multiply-add lanes per SM per clock
 SM_COUNT_GB300 = 152
 
@@ -100,6 +106,19 @@ class Replicas:
         if self.world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()
+
+
+def leaf_traffic(a):
+    """DRAM bytes of one leaf launch for the captured configuration, else None."""
+    if a.prec != 512 or a.cutoff != 64 or a.algo not in ("strassen", "winograd"):
+        return None
+    n, leaves = a.n, 1
+    while n > a.cutoff and n % 2 == 0:
+        n //= 2
+        leaves *= 7
+    if n != 64:
+        return None
+    return round(leaves * LEAF_TRAFFIC_PER_LEAF_P512_C64)
 
 
 def workload_config(a):
@@ -332,7 +351,8 @@ def run_ours(a, rank, world, local):
                          "peak": round(peak, 3), "unit": "T IMAD/s",
                          "frac": round(achieved / peak, 4),
                          "peak_note": "derived: 152 SMs x 64 IMAD/clk x 2070 MHz",
-                         "work_per_madd_imad": imad_per_madd, "traffic": None},
+                         "work_per_madd_imad": imad_per_madd, "traffic": leaf_traffic(a),
+                         "traffic_unit": "bytes per launch (ncu capture, scaled by leaves)"},
             "kernels": kernels,
             "gpu_launches": int(round(launches_per_step * a.steps)),
             "e2e": {"value": round(rep.whole_job(flops, e2e_ms * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
