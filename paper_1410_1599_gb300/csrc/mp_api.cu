@@ -468,6 +468,7 @@ static size_t lu_ws_bytes(int64_t n, int p, int panel, int algo, int cutoff, int
     const int64_t K = std::min<int64_t>(panel, n);
     const int64_t nt = n - K;                              // largest trailing block
     size_t b = mat_bytes(1, nt, nt, L) + mat_bytes(1, n, 1, L) + padded((size_t)n * 8);
+    b += padded((size_t)mpg::LU_COL_MAX_CTAS * 8) + padded(sizeof(unsigned));
     b += gemm_ws_bytes(algo, nt, K, nt, cutoff, policy, L) + 512;
     return b;
 }
@@ -779,24 +780,37 @@ int mplu(int64_t n, int32_t prec, mpmat_t *A, int64_t *piv, const mpmat_t *b, mp
     BMat T = carve(ws, 1, nt0, nt0, L);                    // trailing product, ld = nt0
     BMat y = carve(ws, 1, n, 1, L);
     int64_t *perm = (int64_t *)ws.take((size_t)n * 8);
+    int64_t *cand = (int64_t *)ws.take((size_t)mpg::LU_COL_MAX_CTAS * 8);
+    unsigned *ticket = (unsigned *)ws.take(sizeof(unsigned));
+    if (cudaMemsetAsync(ticket, 0, sizeof(unsigned), s) != cudaSuccess) return MP_ERR_CUDA;
     const BMat A0 = bmat(A);
     dispatch(prec, [&](auto w) {
         constexpr int WW = decltype(w)::value;
+        const bool fused = lu_fused_ok<WW>(K);
         for (int64_t j0 = 0; j0 < n && rc == MP_OK; j0 += K) {
             const int64_t je = std::min<int64_t>(j0 + K, n);
             {
                 Prof pr(MP_K_LU, (double)(je - j0) * (n - j0), s);
-                for (int64_t k = j0; k < je; ++k) {
-                    launch_lu_pivot<WW>(A0, n, k, piv, prec, st, s);
-                    launch_lu_divide<WW>(A0, n, k, prec, s);
-                    launch_lu_rank1<WW>(A0, k, k + 1, n, k + 1, je, prec, st, s);
+                if (fused) {
+                    launch_lu_pivot<WW>(A0, n, j0, piv, prec, st, s);
+                    for (int64_t k = j0; k < je; ++k)
+                        launch_lu_column<WW>(A0, n, k, je, piv, prec, st, cand, ticket, s);
+                } else {
+                    for (int64_t k = j0; k < je; ++k) {
+                        launch_lu_pivot<WW>(A0, n, k, piv, prec, st, s);
+                        launch_lu_divide<WW>(A0, n, k, prec, s);
+                        launch_lu_rank1<WW>(A0, k, k + 1, n, k + 1, je, prec, st, s);
+                    }
                 }
             }
             if (je >= n) break;
             {
                 Prof pr(MP_K_LU, (double)(je - j0) * (je - j0) * (n - je) / 2, s);
-                for (int64_t r = j0; r + 1 < je; ++r)          // U12 = L11^-1 A12
-                    launch_lu_rank1<WW>(A0, r, r + 1, je, je, n, prec, st, s);
+                if (fused)                                     // U12 = L11^-1 A12
+                    launch_lu_u12<WW>(A0, n, j0, je, prec, st, s);
+                else
+                    for (int64_t r = j0; r + 1 < je; ++r)
+                        launch_lu_rank1<WW>(A0, r, r + 1, je, je, n, prec, st, s);
             }
             const int64_t nt = n - je;
             BMat Tv = T;

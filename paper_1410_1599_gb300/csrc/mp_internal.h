@@ -106,5 +106,17 @@ void launch_lu_rank1(BMat A, int64_t k, int64_t r0, int64_t r1, int64_t c0, int6
 template <int W>
 void launch_lu_solve(BMat LU, int64_t n, const int64_t *piv, BMat b, BMat y, BMat x,
                      int64_t *perm, int p, DevStatus *st, cudaStream_t s);
+// Fused panel column step (l_ik, the panel row updates and the next pivot in
+// one launch) and the one-launch U12 solve; up to 1024 bits, panels <= 128.
+// cand holds LU_COL_MAX_CTAS row slots; *ticket starts at 0 and is returned
+// to 0 by every launch.
+constexpr int64_t LU_COL_MAX_CTAS = 152 * 8;
+template <int W>
+bool lu_fused_ok(int64_t panel);
+template <int W>
+void launch_lu_column(BMat A, int64_t n, int64_t k, int64_t je, int64_t *piv, int p, DevStatus *st,
+                      int64_t *cand, unsigned *ticket, cudaStream_t s);
+template <int W>
+void launch_lu_u12(BMat A, int64_t n, int64_t j0, int64_t je, int p, DevStatus *st, cudaStream_t s);
 
 }  // namespace mpg

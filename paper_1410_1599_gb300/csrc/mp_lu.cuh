@@ -176,6 +176,239 @@ __global__ void lu_rank1_kernel(BMat A, int64_t k, int64_t r0, int64_t r1, int64
     if (bad) flag(status, ST_RANGE);
 }
 
+// ---------------------------------------------- fused column step (W <= 32)
+// One launch per panel column k does what the pivot / divide / rank-1 kernels
+// do in three: a warp per row i > k forms l_ik = RN(a_ik / a_kk) together,
+// then its lanes update the row's panel columns k+1 .. je-1
+// (a_ij = RN(a_ij - RN(l_ik a_kj))), lane 0 tracking the first largest
+// |a_i,k+1| of the warp's rows.  Each CTA posts its candidate; the last CTA to
+// finish (ticket counter, no waiting) picks the pivot of column k+1 among
+// the posted rows and exchanges the two full rows, so the next launch starts
+// on a pivoted column.  The operations and their order per element are the
+// same as in the separate kernels.
+constexpr int LU_COL_WARPS = 4;
+
+// First row of largest |a_{r,col}| among the rows rows[0 .. cnt), ties to the
+// lower row, by the NT threads of a CTA (key reduction as in lu_pivot_kernel,
+// full comparison only among key ties).  Returns -1 when cnt == 0 or every
+// listed row is negative.
+// load through L2 only: the rows were written by other CTAs of this launch
+template <int W>
+MP_DEV void ld_cg(Mp<W> &x, const BMat &M, int64_t r, int64_t c, int L)
+{
+    const int64_t lo = lim_off(M, 0, r, c), eo = es_off(M, 0, r, c);
+#pragma unroll
+    for (int k = 0; k < W / 2; ++k) {
+        const uint64_t v = (k < L) ? __ldcg(M.limb + lo + (int64_t)k * M.plane) : 0ull;
+        x.m[W - 1 - 2 * k] = (uint32_t)(v >> 32);
+        x.m[W - 2 - 2 * k] = (uint32_t)v;
+    }
+    x.e = __ldcg(M.exp + eo);
+    x.s = (uint32_t)(__ldcg(M.sign + eo) & 1);
+}
+
+template <int W, int NT, class RowOf>
+__device__ int64_t cta_pick_row(const BMat &A, int64_t col, int cnt, RowOf row_of, const RoundSpec &rs,
+                                int64_t *s_list, int *s_nc, int64_t *s_we, uint64_t *s_wm)
+{
+    constexpr int NW = NT / 32;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    int64_t best = -1;
+    Mp<W> bx, x;
+    set_zero<W>(bx, 0u);
+    for (int c = tid; c < cnt; c += NT) {
+        const int64_t r = row_of(c);
+        if (r < 0) continue;
+        ld_cg<W>(x, A, r, col, rs.L);
+        const int cmp = best < 0 ? 1 : cmpabs<W>(x, bx);
+        if (cmp > 0 || (cmp == 0 && r < best)) {
+            best = r;
+            bx = x;
+        }
+    }
+    if (tid == 0) *s_nc = 0;
+    const int64_t ke = (best < 0) ? EXP_ZERO : bx.e;
+    const uint64_t km = (best < 0 || bx.e == EXP_ZERO) ? 0ull : (((uint64_t)bx.m[W - 1] << 32) | bx.m[W - 2]);
+    int64_t me = ke;
+    uint64_t mm = km;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const int64_t oe = __shfl_xor_sync(0xffffffffu, me, o);
+        const uint64_t om = __shfl_xor_sync(0xffffffffu, mm, o);
+        if (oe > me || (oe == me && om > mm)) { me = oe; mm = om; }
+    }
+    if (lane == 0) { s_we[wid] = me; s_wm[wid] = mm; }
+    __syncthreads();
+    me = s_we[0];
+    mm = s_wm[0];
+    for (int w = 1; w < NW; ++w)
+        if (s_we[w] > me || (s_we[w] == me && s_wm[w] > mm)) { me = s_we[w]; mm = s_wm[w]; }
+    if (best >= 0 && ke == me && km == mm) s_list[atomicAdd(s_nc, 1)] = best;
+    __syncthreads();
+    int64_t pr = -1;
+    if (tid == 0 && *s_nc > 0) {
+        pr = s_list[0];
+        Mp<W> xa, xb;
+        ld_cg<W>(xa, A, pr, col, rs.L);
+        for (int c = 1; c < *s_nc; ++c) {
+            const int64_t rb = s_list[c];
+            ld_cg<W>(xb, A, rb, col, rs.L);
+            const int cmp = cmpabs<W>(xb, xa);
+            if (cmp > 0 || (cmp == 0 && rb < pr)) { pr = rb; xa = xb; }
+        }
+    }
+    return pr;    // meaningful in thread 0
+}
+
+// exchange rows r1 and r2 of A over all n columns (the threads of one CTA)
+template <int W>
+__device__ void cta_swap_rows(const BMat &A, int64_t n, int64_t r1, int64_t r2, int L)
+{
+    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+        for (int q = 0; q < L; ++q) {
+            uint64_t *a = A.limb + (int64_t)q * A.plane + r1 * A.ld + c;
+            uint64_t *b = A.limb + (int64_t)q * A.plane + r2 * A.ld + c;
+            const uint64_t t = *a;
+            *a = *b;
+            *b = t;
+        }
+        int64_t *ea = A.exp + r1 * A.ld + c, *eb = A.exp + r2 * A.ld + c;
+        const int64_t te = *ea;
+        *ea = *eb;
+        *eb = te;
+        int8_t *sa = A.sign + r1 * A.ld + c, *sb = A.sign + r2 * A.ld + c;
+        const int8_t ts = *sa;
+        *sa = *sb;
+        *sb = ts;
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(LU_COL_WARPS * 32)
+lu_column_kernel(BMat A, int64_t n, int64_t k, int64_t je, int64_t *piv, int p, DevStatus *status,
+                 int64_t *cand, unsigned *ticket)
+{
+    static_assert(W <= 32, "warp-per-row column step");
+    constexpr int NT = LU_COL_WARPS * 32;
+    const RoundSpec rs = make_spec<W>(p);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t nw = (int64_t)gridDim.x * LU_COL_WARPS;
+    const bool next = k + 1 < je;
+    __shared__ int64_t s_list[NT];
+    __shared__ int64_t s_we[LU_COL_WARPS];
+    __shared__ uint64_t s_wm[LU_COL_WARPS];
+    __shared__ int s_nc;
+    __shared__ int s_last;
+    int64_t de;
+    uint32_t ds;
+    const uint32_t dm = wld<W>(A, 0, k, k, rs.L, de, ds);
+    int64_t best = -1;                      // lane 0: the warp's first largest |a_i,k+1|
+    Mp<W> bx;
+    set_zero<W>(bx, 0u);
+    bool bad = false;
+    for (int64_t i = k + 1 + (int64_t)blockIdx.x * LU_COL_WARPS + wid; i < n; i += nw) {
+        int64_t qe;
+        uint32_t qs;
+        uint32_t qm = wld<W>(A, 0, i, k, rs.L, qe, qs);
+        if (de != EXP_ZERO) {               // a zero pivot leaves the column as it is
+            int64_t xe = qe;
+            uint32_t xs = qs;
+            qm = warp_div<W>(qm, xe, xs, dm, de, ds, qe, qs, rs);
+            wst<W>(qm, qe, qs, A, 0, i, k, rs.L);
+        }
+        Mp<W> l;
+#pragma unroll
+        for (int w = 0; w < W; ++w) l.m[w] = __shfl_sync(0xffffffffu, qm, w);
+        l.e = qe;
+        l.s = qs;
+        for (int64_t j = k + 1 + lane; j < je; j += 32) {
+            Mp<W> u, y, z;
+            ld_rw<W>(u, A, 0, k, j, rs.L);
+            ld_rw<W>(y, A, 0, i, j, rs.L);
+            mul<W, true>(z, l, u, rs);
+            add<W, true>(y, y, z, 1u, rs);
+            bad |= st<W>(y, A, 0, i, j, rs.L);
+            if (j == k + 1 && (best < 0 || absgreater<W>(y, bx))) {
+                best = i;
+                bx = y;
+            }
+        }
+        __syncwarp();
+    }
+    if (bad) flag(status, ST_RANGE);
+    if (!next) return;
+    // this CTA's candidate for the pivot of column k+1
+    __shared__ int64_t s_wrow[LU_COL_WARPS];
+    if (lane == 0) s_wrow[wid] = best;
+    __syncthreads();
+    const int64_t cb = cta_pick_row<W, NT>(A, k + 1, LU_COL_WARPS, [&](int c) { return s_wrow[c]; }, rs,
+                                           s_list, &s_nc, s_we, s_wm);
+    if (threadIdx.x == 0) cand[blockIdx.x] = cb;
+    // publish, then the last CTA to arrive picks among all candidates
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1) ? 1 : 0;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int cnt = (int)gridDim.x;
+    const int64_t pr0 = cta_pick_row<W, NT>(A, k + 1, cnt, [&](int c) { return ((volatile int64_t *)cand)[c]; },
+                                            rs, s_list, &s_nc, s_we, s_wm);
+    __shared__ int64_t s_pr;
+    if (threadIdx.x == 0) {
+        const int64_t pr = pr0 < 0 ? k + 1 : pr0;
+        Mp<W> v;
+        ld_cg<W>(v, A, pr, k + 1, rs.L);
+        piv[k + 1] = pr;
+        if (v.e == EXP_ZERO) {
+            atomicOr(&status->flags, ST_SINGULAR);
+            atomicMin(&status->singular_col, (long long)(k + 1));
+            s_pr = k + 1;
+        } else {
+            s_pr = pr;
+        }
+        *ticket = 0u;                       // ready for the next launch
+    }
+    __syncthreads();
+    if (s_pr != k + 1) cta_swap_rows<W>(A, n, k + 1, s_pr, rs.L);
+}
+
+// ------------------------------------------- U12 = L11^-1 A12, one launch
+// One CTA per column j of A12 (grid-stride), thread t <-> panel row j0 + t
+// (panels of at most 128 columns).  Row r is final after the steps s < r;
+// it is then shared, and every row below takes a_ij = RN(a_ij - RN(l_ir a_rj))
+// -- per element the steps s = j0 .. i-1 in ascending order, as the
+// row-step launches do.
+template <int W>
+__global__ void __launch_bounds__(128) lu_u12_kernel(BMat A, int64_t n, int64_t j0, int64_t je, int p,
+                                                     DevStatus *status)
+{
+    const RoundSpec rs = make_spec<W>(p);
+    __shared__ Mp<W> s_x;
+    const int64_t i = j0 + threadIdx.x;
+    const bool mine = i < je;
+    bool bad = false;
+    for (int64_t j = je + blockIdx.x; j < n; j += gridDim.x) {
+        Mp<W> y, l, x, z;
+        if (mine) ld_rw<W>(y, A, 0, i, j, rs.L);
+        if (threadIdx.x == 0) s_x = y;
+        for (int64_t r = j0; r + 1 < je; ++r) {
+            __syncthreads();                 // s_x = a_rj, final
+            if (mine && i > r) {
+                x = s_x;
+                ld_rw<W>(l, A, 0, i, r, rs.L);
+                mul<W, true>(z, l, x, rs);
+                add<W, true>(y, y, z, 1u, rs);
+            }
+            __syncthreads();
+            if (i == r + 1) s_x = y;
+        }
+        if (mine && i > j0) bad |= st<W>(y, A, 0, i, j, rs.L);
+        __syncthreads();
+    }
+    if (bad) flag(status, ST_RANGE);
+}
+
 // ------------------------------------------------------- triangular solves
 // x = U^-1 L^-1 P b, both substitutions column-oriented: row i of the
 // forward pass takes y_i <- RN(y_i - RN(l_ij y_j)) for j = 0, 1, .., i-1 in
@@ -375,6 +608,37 @@ void launch_lu_solve(BMat LU, int64_t n, const int64_t *piv, BMat b, BMat y, BMa
     }
 }
 
+// true when the fused column step and the one-launch U12 solve apply
+template <int W>
+bool lu_fused_ok(int64_t panel)
+{
+    return W <= 32 && panel <= 128;
+}
+
+template <int W>
+void launch_lu_column(BMat A, int64_t n, int64_t k, int64_t je, int64_t *piv, int p, DevStatus *st,
+                      int64_t *cand, unsigned *ticket, cudaStream_t s)
+{
+    if constexpr (W <= 32) {
+        const int64_t rows = n - k - 1;
+        if (rows <= 0) return;
+        int64_t g = (rows + LU_COL_WARPS - 1) / LU_COL_WARPS;
+        if (g > LU_COL_MAX_CTAS) g = LU_COL_MAX_CTAS;
+        lu_column_kernel<W><<<(unsigned)g, LU_COL_WARPS * 32, 0, s>>>(A, n, k, je, piv, p, st, cand, ticket);
+    }
+}
+
+template <int W>
+void launch_lu_u12(BMat A, int64_t n, int64_t j0, int64_t je, int p, DevStatus *st, cudaStream_t s)
+{
+    if constexpr (W <= 32) {
+        const int64_t cols = n - je;
+        if (cols <= 0) return;
+        const int64_t g = cols < 152 * 8 ? cols : 152 * 8;
+        lu_u12_kernel<W><<<(unsigned)g, 128, 0, s>>>(A, n, j0, je, p, st);
+    }
+}
+
 #define MPG_INSTANTIATE_LU(W)                                                                   \
     template void launch_lu_pivot<W>(BMat, int64_t, int64_t, int64_t *, int, DevStatus *,       \
                                      cudaStream_t);                                             \
@@ -382,6 +646,10 @@ void launch_lu_solve(BMat LU, int64_t n, const int64_t *piv, BMat b, BMat y, BMa
     template void launch_lu_rank1<W>(BMat, int64_t, int64_t, int64_t, int64_t, int64_t, int,    \
                                      DevStatus *, cudaStream_t);                                \
     template void launch_lu_solve<W>(BMat, int64_t, const int64_t *, BMat, BMat, BMat,          \
-                                     int64_t *, int, DevStatus *, cudaStream_t);
+                                     int64_t *, int, DevStatus *, cudaStream_t);                \
+    template bool lu_fused_ok<W>(int64_t);                                                      \
+    template void launch_lu_column<W>(BMat, int64_t, int64_t, int64_t, int64_t *, int,          \
+                                      DevStatus *, int64_t *, unsigned *, cudaStream_t);        \
+    template void launch_lu_u12<W>(BMat, int64_t, int64_t, int64_t, int, DevStatus *, cudaStream_t);
 
 }  // namespace mpg
