@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--lu-n", type=int, default=1024)
     ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--serve", action="store_true", help="only the serving run (its own JSON line)")
+    ap.add_argument("--lu", action="store_true",
+                    help="only the LU runs: n = --lu-n at 256 and 1024 bits, well-conditioned and Lotkin")
     ap.add_argument("--split", action="store_true",
                     help="only the split-form comparison (4096^3 at 1024 bits by default)")
     return ap.parse_args()
@@ -676,6 +678,15 @@ def main():
         libbuild.build()
         torch.cuda.set_device(local)
         print(json.dumps({"serving": serve_run(a.serve_requests)}), flush=True)
+        return
+    if a.lu:
+        import torch
+        from paper_1410_1599_gb300 import binding as mp
+        from paper_1410_1599_gb300 import build as libbuild
+        libbuild.build()
+        torch.cuda.set_device(local)
+        runs = [lu_run(a.lu_n, p, mp.WINOGRAD, kind=kind) for kind in ("well", "lotkin") for p in (256, 1024)]
+        print(json.dumps({"lu": runs}), flush=True)
         return
     if a.impl == "reference":
         run_reference(a, rank, world)
