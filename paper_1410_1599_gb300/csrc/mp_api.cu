@@ -377,7 +377,11 @@ int run_split(int64_t m, int64_t l, int64_t n, int p, BMat A, BMat B, BMat C, Wo
     }
     {
         Prof pr(MP_K_SPLIT, (double)S * S * m * (double)lp * n, s);
-        launch_split_slices(pa, pb, m, l, n, p, D, s);
+        const int rs = launch_split_slices(pa, pb, m, l, n, p, D, st, s);
+        if (rs != MP_OK) {
+            ws.reset(mk);
+            return rs;
+        }
     }
     {
         Prof pr(MP_K_SPLIT_AUX, (double)m * n, s);

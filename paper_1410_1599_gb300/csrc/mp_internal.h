@@ -86,8 +86,8 @@ int64_t split_row_pad(int64_t l);
 template <int W>
 void launch_split_prep(BMat A, BMat B, int64_t m, int64_t l, int64_t n, int p, __half *pa,
                        __half *pb, int64_t *ea, int64_t *eb, uint8_t *wa, uint8_t *wb, cudaStream_t s);
-void launch_split_slices(const __half *pa, const __half *pb, int64_t m, int64_t l, int64_t n,
-                         int p, long long *D, cudaStream_t s);
+int launch_split_slices(const __half *pa, const __half *pb, int64_t m, int64_t l, int64_t n, int p,
+                        long long *D, DevStatus *st, cudaStream_t s);
 template <int W>
 void launch_split_finish(const long long *D, int64_t m, int64_t n, int p, const int64_t *ea,
                          const int64_t *eb, const uint8_t *wa, const uint8_t *wb, BMat C,

@@ -1,17 +1,31 @@
 // split_core.cu -- the slice-product kernel of the split form (see
 // mp_split.cuh): D_s(i, j) = sum_{u+v=s} sum_k A_u(i,k) B_v(j,k) exactly, for
-// every weight diagonal s, on tensor cores.
+// every weight diagonal s, on the fifth-generation tensor cores.
 //
-// CTA tile 128 x 128 outputs, 8 warps of 64 x 32 (4 x 4 mma.m16n8k16 tiles).
-// The (pair, k-block) steps of a diagonal form one stream fed by a 4-stage
-// cp.async pipeline (k-blocks of 32 halves, operands staged in shared memory,
-// fragments loaded with ldmatrix).  Exactness: digit products are integers of
-// magnitude <= 2^14; an fp32 accumulator takes at most SPLIT_CHUNK = 512 of
-// them (< 2^24: every partial sum is an exact fp32 integer) and is then
-// folded into an int32 accumulator; one digit pair contributes at most
-// lp * 2^14, so the int32 holds max_pairs = floor((2^31 - 1) / (lp 2^14))
-// pairs before it is added into the int64 D_s in global memory.
+// One CTA owns a 128 x 256 output tile and a strided set of diagonals.
+//   warp 0     TMA producer: 128 x 64 A and 256 x 64 B fp16 tiles (128-byte
+//              swizzle) into a 4-stage shared-memory ring;
+//   warp 1     allocates the tensor memory and issues tcgen05.mma
+//              (kind::f16, M = 128, N = 256, K = 16, fp32 accumulation) from
+//              one thread; two 256-column accumulators alternate;
+//   warps 2-9  drain an accumulator every CHUNK = 512 k-terms: tcgen05.ld,
+//              conversion of the exact fp32 integers to int32 and accumulation
+//              in registers (each thread one tile row, 128 columns); after at
+//              most 255 chunks, and at the end of a diagonal, the int32 sums
+//              are stored to (first time) or added into the int64 D_s.
+// Exactness: a digit product is an integer of magnitude <= 2^14; an fp32
+// accumulator takes at most 512 of them (< 2^24: every partial sum is an
+// exact fp32 integer, whatever the tensor core's summation order); an int32
+// register takes at most 255 such chunks (< 2^31).  Chunks may cross pair
+// boundaries inside a diagonal: all its products carry the same weight.
+// Every wait is bounded; a wait that runs out sets ST_TIMEOUT and the CTA
+// unwinds (tensor memory is released on every path).
+#include <cstdio>
+#include <cstdlib>
+
+#include "mpgemm.h"
 #include "mp_split.cuh"
+#include "mp_tc.cuh"
 
 namespace mpg {
 
@@ -20,186 +34,289 @@ int64_t split_row_pad(int64_t l) { return split_lpad(l); }
 
 namespace {
 
-constexpr int TM = 128, TN = 128, TK = SPLIT_TK, STAGES = 4, PADK = TK + 8;
-constexpr int THREADS = 256;
-constexpr int STAGE_HALVES = (TM + TN) * PADK;
-constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_HALVES * 2;
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int KB_PER_CHUNK = SPLIT_CHUNK / BK;                 // 8
+constexpr int CHUNKS_PER_I32 = 255;
+constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;             // 48 KB
+constexpr int EPI_WARPS = 8, THREADS = (2 + EPI_WARPS) * 32;
+constexpr int EPI_COLS = BN / (EPI_WARPS / 4);                  // columns per epilogue thread
+constexpr uint32_t TMEM_COLS = 2 * BN;                          // two accumulators
+constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024;
+constexpr long long WAIT_LIMIT = 4000000000ll;                  // ~2 s of clock
 
-__device__ __forceinline__ uint32_t smem_addr(const void *p)
+struct Sched {
+    int S, groups, nkb;
+    int64_t m, n, tiles_n;
+};
+
+// diagonal s of this CTA: pairs u in [u0, u1]; steps = pairs x k-blocks
+__device__ __forceinline__ void diag_range(int s, int S, int &u0, int &u1)
 {
-    return (uint32_t)__cvta_generic_to_shared(p);
+    u0 = s - (S - 1) > 0 ? s - (S - 1) : 0;
+    u1 = s < S - 1 ? s : S - 1;
 }
 
-__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid)
+// acc[q] += column q of the accumulator for q < EPI_COLS (16 at a time)
+template <int Q>
+__device__ __forceinline__ void drain_columns(uint32_t taddr, int32_t (&acc)[EPI_COLS])
 {
-    const int sz = valid ? 16 : 0;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src),
-                 "r"(sz));
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N)); }
-
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void *p)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_addr(p)));
+    if constexpr (Q < EPI_COLS) {
+        tc::tmem_ld16_add_i32<Q>(taddr + Q, acc);
+        drain_columns<Q + 16>(taddr, acc);
+    }
 }
 
-__device__ __forceinline__ void mma_16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
-                                          uint32_t b1)
+// row[q] (int64) = / += acc[q] for q < valid, 16 columns per block
+template <int Q>
+__device__ __forceinline__ void flush_columns(long long *row, const int32_t (&acc)[EPI_COLS], int valid, bool first)
 {
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, "
-                 "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    if constexpr (Q < EPI_COLS) {
+        tc::flush16_i64<Q>(row, acc, valid, first);
+        flush_columns<Q + 16>(row, acc, valid, first);
+    }
 }
 
 }  // namespace
 
 __global__ void __launch_bounds__(THREADS, 1)
-split_slice_kernel(const __half *__restrict__ Ap, const __half *__restrict__ Bp, int64_t m,
-                   int64_t n, int64_t lp, int S, int max_pairs, int groups, long long *__restrict__ D)
+split_slice_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                      Sched sc, long long *__restrict__ D, DevStatus *status)
 {
-    extern __shared__ __align__(16) __half sm[];
-    const int64_t tiles_n = (n + TN - 1) / TN;
-    const int64_t tile = blockIdx.x / groups;
-    const int grp = (int)(blockIdx.x % groups);      // this CTA's share of the diagonals
-    const int64_t i0 = (tile / tiles_n) * TM, j0 = (tile % tiles_n) * TN;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int wm = warp >> 2, wn = warp & 3, g = lane >> 2, tg = lane & 3;
-    const int64_t plane_a = m * lp, plane_b = n * lp;
-    const int nkb = (int)(lp / TK);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *ring = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], accf_bar[2], acce_bar[2], drain_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
 
-    for (int s = grp; s <= 2 * S - 2; s += groups) {
-        const int u0 = s - (S - 1) > 0 ? s - (S - 1) : 0, u1 = s < S - 1 ? s : S - 1;
-        const int npairs = u1 - u0 + 1;
-        const int total = npairs * nkb;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t tile = blockIdx.x / sc.groups;
+    const int grp = (int)(blockIdx.x % sc.groups);
+    const int64_t i0 = (tile / sc.tiles_n) * BM, j0 = (tile % sc.tiles_n) * BN;
+    const int S = sc.S, nkb = sc.nkb;
 
-        // issue the copies of step t into stage buffer t % STAGES
-        auto load = [&](int t) {
-            if (t < total) {
-                const int pu = t / nkb;
-                const int u = u0 + pu, kb = t - pu * nkb;
-                const __half *Au = Ap + (int64_t)u * plane_a + kb * TK;
-                const __half *Bv = Bp + (int64_t)(s - u) * plane_b + kb * TK;
-                __half *st = sm + (t % STAGES) * STAGE_HALVES;
-#pragma unroll
-                for (int q = 0; q < (TM + TN) * TK / 8 / THREADS; ++q) {
-                    const int e = tid + q * THREADS;
-                    const int r = e / (TK / 8), c8 = (e % (TK / 8)) * 8;
-                    if (r < TM) {
-                        const bool ok = i0 + r < m;
-                        cp_async16(st + r * PADK + c8, Au + (ok ? (i0 + r) : 0) * lp + c8, ok);
-                    } else {
-                        const int rb = r - TM;
-                        const bool ok = j0 + rb < n;
-                        cp_async16(st + r * PADK + c8, Bv + (ok ? (j0 + rb) : 0) * lp + c8, ok);
-                    }
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < STAGES; ++st) {
+            tc::mbar_init(&full_bar[st], 1);
+            tc::mbar_init(&empty_bar[st], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&accf_bar[b], 1);
+            tc::mbar_init(&acce_bar[b], EPI_WARPS);
+        }
+        tc::mbar_init(&drain_bar, 1);
+        tc::mbar_fence_init();
+        abort_flag = 0;
+    }
+    if (warp == 1) tc::tmem_alloc(&tmem_slot, TMEM_COLS);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+
+    auto fail = [&]() {
+        abort_flag = 1;
+        if (status) atomicOr(&status->flags, ST_TIMEOUT);
+    };
+
+    if (warp == 0) {
+        // ------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            tc::prefetch_map(&map_a);
+            tc::prefetch_map(&map_b);
+            uint32_t g = 0;
+            for (int s = grp; s <= 2 * S - 2 && !abort_flag; s += sc.groups) {
+                int u0, u1;
+                diag_range(s, S, u0, u1);
+                const int total = (u1 - u0 + 1) * nkb;
+                for (int t = 0; t < total; ++t, ++g) {
+                    const uint32_t st = g % STAGES, ph = (g / STAGES) & 1u;
+                    if (!tc::mbar_wait(&empty_bar[st], ph ^ 1u, &abort_flag, WAIT_LIMIT)) { fail(); break; }
+                    const int u = u0 + t / nkb, kb = t % nkb;
+                    uint8_t *sa = ring + st * STAGE_BYTES, *sb = sa + A_BYTES;
+                    tc::mbar_expect_tx(&full_bar[st], STAGE_BYTES);
+                    tc::tma_load_2d(sa, &map_a, kb * BK, (int32_t)(u * sc.m + i0), &full_bar[st]);
+                    tc::tma_load_2d(sb, &map_b, kb * BK, (int32_t)((s - u) * sc.n + j0), &full_bar[st]);
                 }
             }
-            cp_commit();
-        };
-
-        int acc[4][4][4];
-        float f[4][4][4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) { acc[a][b][c] = 0; f[a][b][c] = 0.f; }
-        int pairs_in_acc = 0;
-        bool first_flush = true;
-
-        auto flush = [&]() {           // acc (int32) into D_s (int64), then clear
-            long long *Ds = D + (int64_t)s * m * n;
-#pragma unroll
-            for (int mt = 0; mt < 4; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const int64_t i = i0 + wm * 64 + mt * 16 + g + (c >= 2 ? 8 : 0);
-                        const int64_t j = j0 + wn * 32 + nt * 8 + tg * 2 + (c & 1);
-                        if (i < m && j < n) {
-                            long long *d = Ds + i * n + j;
-                            *d = (first_flush ? 0ll : *d) + (long long)acc[mt][nt][c];
-                        }
-                        acc[mt][nt][c] = 0;
-                    }
-            first_flush = false;
-            pairs_in_acc = 0;
-        };
-
-#pragma unroll
-        for (int t = 0; t < STAGES - 1; ++t) load(t);
-        for (int t = 0; t < total; ++t) {
-            cp_wait<STAGES - 2>();
-            __syncthreads();
-            load(t + STAGES - 1);
-            const __half *st = sm + (t % STAGES) * STAGE_HALVES;
-            const __half *As = st, *Bs = st + TM * PADK;
-#pragma unroll
-            for (int kk = 0; kk < TK; kk += 16) {
-                uint32_t af[4][4], bf[2][4];
-#pragma unroll
-                for (int mt = 0; mt < 4; ++mt)
-                    ldsm_x4(af[mt], As + (wm * 64 + mt * 16 + (lane & 15)) * PADK + kk + (lane >> 4) * 8);
-#pragma unroll
-                for (int np = 0; np < 2; ++np)
-                    ldsm_x4(bf[np], Bs + (wn * 32 + np * 16 + (lane & 7) + ((lane >> 4) << 3)) * PADK +
-                                        kk + ((lane >> 3) & 1) * 8);
-#pragma unroll
-                for (int mt = 0; mt < 4; ++mt)
-#pragma unroll
-                    for (int nt = 0; nt < 4; ++nt)
-                        mma_16816(f[mt][nt], af[mt], bf[nt >> 1][(nt & 1) * 2], bf[nt >> 1][(nt & 1) * 2 + 1]);
-            }
-            const int kb = t % nkb;
-            const bool pair_end = kb == nkb - 1;
-            if (((kb + 1) % (SPLIT_CHUNK / TK)) == 0 || pair_end) {
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int b = 0; b < 4; ++b)
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            acc[a][b][c] += __float2int_rn(f[a][b][c]);
-                            f[a][b][c] = 0.f;
-                        }
-            }
-            if (pair_end) {
-                ++pairs_in_acc;
-                if (pairs_in_acc == max_pairs || t == total - 1) flush();
+            if (abort_flag) {
+                // unwinding: let the copies still in flight land (bounded)
+                for (uint32_t k = g > STAGES ? g - STAGES : 0; k < g; ++k)
+                    tc::mbar_wait(&full_bar[k % STAGES], (k / STAGES) & 1u, nullptr, 200000000ll);
             }
         }
-        cp_wait<0>();
-        __syncthreads();
+    } else if (warp == 1) {
+        // ------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_f16_f32(BM, BN);
+            uint32_t g = 0, c = 0;
+            for (int s = grp; s <= 2 * S - 2 && !abort_flag; s += sc.groups) {
+                int u0, u1;
+                diag_range(s, S, u0, u1);
+                const int total = (u1 - u0 + 1) * nkb;
+                bool ok = true;
+                for (int t = 0; t < total && ok; ++t, ++g) {
+                    const uint32_t buf = c & 1u;
+                    const bool first = (t % KB_PER_CHUNK) == 0;
+                    const bool last = (t % KB_PER_CHUNK) == KB_PER_CHUNK - 1 || t == total - 1;
+                    if (first) {
+                        if (!tc::mbar_wait(&acce_bar[buf], ((c >> 1) & 1u) ^ 1u, &abort_flag, WAIT_LIMIT)) {
+                            fail();
+                            ok = false;
+                            break;
+                        }
+                        tc::fence_after_sync();
+                    }
+                    const uint32_t st = g % STAGES, ph = (g / STAGES) & 1u;
+                    if (!tc::mbar_wait(&full_bar[st], ph, &abort_flag, WAIT_LIMIT)) { fail(); ok = false; break; }
+                    tc::fence_after_sync();
+                    const uint32_t sa = tc::saddr(ring + st * STAGE_BYTES), sb = sa + A_BYTES;
+                    const uint32_t d = tmem + buf * BN;
+#pragma unroll
+                    for (int k = 0; k < BK / 16; ++k)
+                        tc::mma_f16(d, tc::desc_k128(sa + 32 * k), tc::desc_k128(sb + 32 * k), idesc,
+                                    (first && k == 0) ? 0u : 1u);
+                    tc::mma_commit(&empty_bar[st]);                 // frees the stage when done
+                    if (last) {
+                        tc::mma_commit(&accf_bar[buf]);             // the chunk is complete
+                        ++c;
+                    }
+                }
+                if (!ok) break;
+            }
+            if (abort_flag) {
+                // unwinding: every MMA issued so far completes before the
+                // tensor memory is released (bounded)
+                tc::mma_commit(&drain_bar);
+                tc::mbar_wait(&drain_bar, 0u, nullptr, 200000000ll);
+            }
+        }
+    } else {
+        // --------------------------------------------------------- epilogue
+        const int ew = warp - 2;
+        const int quarter = warp & 3;                               // TMEM lanes of this warp
+        const int part = ew >> 2;                                   // column range of the tile
+        const int64_t i = i0 + quarter * 32 + lane;
+        const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+        int32_t acc[EPI_COLS];
+        uint32_t c = 0;
+        for (int s = grp; s <= 2 * S - 2 && !abort_flag; s += sc.groups) {
+            int u0, u1;
+            diag_range(s, S, u0, u1);
+            const int total = (u1 - u0 + 1) * nkb;
+            const int nch = (total + KB_PER_CHUNK - 1) / KB_PER_CHUNK;
+            long long *Ds = D + (int64_t)s * sc.m * sc.n;
+            // segments of at most 255 chunks: int32 sums, then one int64 flush
+            for (int seg = 0; seg < nch && !abort_flag; seg += CHUNKS_PER_I32) {
+                const int seg_end = seg + CHUNKS_PER_I32 < nch ? seg + CHUNKS_PER_I32 : nch;
+#pragma unroll
+                for (int q = 0; q < EPI_COLS; ++q) acc[q] = 0;
+                for (int ch = seg; ch < seg_end; ++ch, ++c) {
+                    const uint32_t buf = c & 1u;
+                    if (!tc::mbar_wait(&accf_bar[buf], (c >> 1) & 1u, &abort_flag, WAIT_LIMIT)) { fail(); break; }
+                    tc::fence_after_sync();
+                    drain_columns<0>(tmem + lane_addr + buf * BN + part * EPI_COLS, acc);
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&acce_bar[buf]);
+                }
+                if (abort_flag) break;
+                if (i < sc.m) {
+                    // first flush of the diagonal stores, later ones add (no read-back)
+                    const int64_t jb = j0 + part * EPI_COLS;
+                    const int64_t left = sc.n - jb;
+                    flush_columns<0>(Ds + i * sc.n + jb, acc, (int)(left < EPI_COLS ? left : EPI_COLS), seg == 0);
+                }
+            }
+        }
+    }
+
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        tc::fence_after_sync();
+        tc::tmem_free(tmem, TMEM_COLS);
     }
 }
 
-void launch_split_slices(const __half *pa, const __half *pb, int64_t m, int64_t l, int64_t n,
-                         int p, long long *D, cudaStream_t s)
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// rows x lp fp16 matrix (K contiguous), boxes of box_rows x 64 with the
+// 128-byte swizzle; reads past the edges return zeros
+bool make_map(CUtensorMap *map, const __half *base, int64_t rows, int64_t lp, uint32_t box_rows)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)lp, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)lp * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
+    const cuuint32_t es[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<__half *>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+int launch_split_slices(const __half *pa, const __half *pb, int64_t m, int64_t l, int64_t n, int p,
+                        long long *D, DevStatus *st, cudaStream_t s)
 {
     const int S = split_digits(p);
     const int64_t lp = split_lpad(l);
-    const int64_t per_pair = lp * 16384;                     // |one pair's sum| <= lp 2^14
-    int max_pairs = (int)((((int64_t)1 << 31) - 1) / per_pair);
-    if (max_pairs < 1) max_pairs = 1;
+    // TMA: 16-byte aligned bases and row strides (lp is a multiple of 32)
+    if (((uintptr_t)pa & 15) || ((uintptr_t)pb & 15) || (lp * 2) % 16) return MP_ERR_ARG;
+    if ((int64_t)S * m > 0x7fffffff || (int64_t)S * n > 0x7fffffff) return MP_ERR_ARG;
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, pa, (int64_t)S * m, lp, BM) || !make_map(&mb, pb, (int64_t)S * n, lp, BN)) {
+        if (std::getenv("MPGEMM_DEBUG")) std::fprintf(stderr, "split: tensor map encoding failed\n");
+        return MP_ERR_UNSUPPORTED;
+    }
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(split_slice_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)SMEM_BYTES);
+        const cudaError_t e = cudaFuncSetAttribute(split_slice_tc_kernel,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        if (e != cudaSuccess) {
+            if (std::getenv("MPGEMM_DEBUG"))
+                std::fprintf(stderr, "split: shared memory attribute: %s\n", cudaGetErrorString(e));
+            return MP_ERR_CUDA;
+        }
         attr = true;
     }
-    const int64_t tiles = ((m + TM - 1) / TM) * ((n + TN - 1) / TN);
-    // spread the diagonals of a tile over several CTAs until about four waves
+    Sched sc;
+    sc.S = S;
+    sc.nkb = (int)((lp + BK - 1) / BK);
+    sc.m = m;
+    sc.n = n;
+    sc.tiles_n = (n + BN - 1) / BN;
+    const int64_t tiles = ((m + BM - 1) / BM) * sc.tiles_n;
+    // spread the diagonals of a tile over several CTAs until about two waves
     int groups = 1;
-    while (tiles * groups < 4 * 152 && groups * 2 <= 2 * S - 1) groups *= 2;
-    split_slice_kernel<<<(unsigned)(tiles * groups), THREADS, SMEM_BYTES, s>>>(pa, pb, m, n, lp, S,
-                                                                               max_pairs, groups, D);
+    while (tiles * groups < 2 * 152 && groups * 2 <= 2 * S - 1) groups *= 2;
+    sc.groups = groups;
+    split_slice_tc_kernel<<<(unsigned)(tiles * groups), THREADS, SMEM_BYTES, s>>>(ma, mb, sc, D, st);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess && std::getenv("MPGEMM_DEBUG"))
+        std::fprintf(stderr, "split: slice kernel launch failed: %s\n", cudaGetErrorString(e));
+    return e == cudaSuccess ? MP_OK : MP_ERR_CUDA;
 }
 
 }  // namespace mpg

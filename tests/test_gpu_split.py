@@ -56,3 +56,16 @@ def test_split_equals_exact_kernel_larger():
     assert_bits_equal(s, e, "split vs exact kernel")
     rows, cols = np.arange(0, n, 37), np.arange(5, n, 41)
     assert_bits_equal(s.sub(rows, cols), orc.dot_exact(A, B, rows=rows, cols=cols), "oracle sample")
+
+
+def test_split_many_chunks_per_diagonal():
+    """l = 2048 at 1024 bits: the middle weight diagonal gathers 137 pairs x
+    2048 k-terms = 548 exact fp32 chunks of 512, more than one int32 register
+    sum can take (255 chunks), so the int64 partial sums are built in steps."""
+    p, m, l, n = 1024, 20, 2048, 24
+    A = gen.uniform_pm1(m, l, p, 79, -6, 6)
+    B = gen.uniform_pm1(l, n, p, 80, -6, 6)
+    s = gemm(A, B, mp.SPLIT)
+    assert_bits_equal(s, gemm(A, B, mp.EXACT), "split vs exact kernel, long k")
+    rows, cols = np.array([0, 7, 19]), np.array([0, 11, 23])
+    assert_bits_equal(s.sub(rows, cols), orc.dot_exact(A, B, rows=rows, cols=cols), "oracle sample, long k")
