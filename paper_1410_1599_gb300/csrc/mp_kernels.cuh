@@ -250,7 +250,6 @@ gemm_block_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p
 // is stored one element per BW-word record (mantissa words little-endian,
 // padded from 64 to 68 words: a warp's 16-byte loads then hit every bank
 // once).  Values and summation order are those of gemm_block_kernel.
-constexpr int BW64 = 68;
 
 // top words of the truncated product a * b, b read from shared memory:
 // acc[q] = word W-2+q of sum_{i+j >= W-2} a_i b_j 2^(32(i+j))
@@ -342,28 +341,29 @@ MP_DEV void mul_sm(Mp<W> &t, const uint32_t (&am)[W], int64_t ae, uint32_t as, c
     t.e = e;
 }
 
-struct Block64Cfg {
-    static constexpr int W = 64, BN = 32, BM = 4, BK = 4, THREADS = BM * BN;
+template <int W> struct BlockSmCfg {
+    static constexpr int BN = 32, BM = 4, BK = (W == 64) ? 4 : 8, THREADS = BM * BN;
+    static constexpr int RB = W + 4;                 // words per B record
     static constexpr size_t smem()
     {
-        return (size_t)BK * BN * BW64 * 4 + (size_t)BM * BK * W * 4 + (size_t)(BM * BK + BK * BN) * 9;
+        return (size_t)BK * BN * RB * 4 + (size_t)BM * BK * W * 4 + (size_t)(BM * BK + BK * BN) * 9;
     }
 };
 
 template <int W>
-__global__ void __launch_bounds__(Block64Cfg::THREADS)
-gemm_block64_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p,
-                    int64_t tiles_m, int64_t tiles_n, DevStatus *status)
+__global__ void __launch_bounds__(BlockSmCfg<W>::THREADS)
+gemm_block_sm_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p,
+                     int64_t tiles_m, int64_t tiles_n, DevStatus *status)
 {
-    using Cfg = Block64Cfg;
-    static_assert(W == Cfg::W, "2048-bit leaf");
-    constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK;
+    using Cfg = BlockSmCfg<W>;
+    static_assert(W == 32 || W == 64, "wide leaf");
+    constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK, RB = Cfg::RB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const RoundSpec rs = make_spec<W>(p);
     const int L = rs.L;
-    // [BK][BN] records of BW64 words, [BM][BK] records of W words, exps, signs
+    // [BK][BN] records of RB words, [BM][BK] records of W words, exps, signs
     uint32_t *sB = reinterpret_cast<uint32_t *>(smem_raw);
-    uint32_t *sA = sB + BK * BN * BW64;
+    uint32_t *sA = sB + BK * BN * RB;
     int64_t *sAe = reinterpret_cast<int64_t *>(sA + BM * BK * W);
     int64_t *sBe = sAe + BM * BK;
     int8_t *sAs = reinterpret_cast<int8_t *>(sBe + BK * BN);
@@ -387,7 +387,7 @@ gemm_block64_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int
             const uint64_t v = (q < L && gj < n && kk < kc)
                                    ? __ldg(B.limb + b * B.bs_limb + (int64_t)q * B.plane + gk * B.ld + gj)
                                    : 0ull;
-            *reinterpret_cast<uint64_t *>(sB + (kk * BN + cc) * BW64 + (W - 2 - 2 * q)) = v;
+            *reinterpret_cast<uint64_t *>(sB + (kk * BN + cc) * RB + (W - 2 - 2 * q)) = v;
         }
         for (int e = threadIdx.x; e < W / 2 * BM * BK; e += blockDim.x) {
             const int kk = e % BK, rr = (e / BK) % BM, q = e / (BK * BM);
@@ -425,7 +425,7 @@ gemm_block64_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int
                     am[q + 3] = v.w;
                 }
                 mul_sm<W>(t, am, sAe[ty * BK + kk], (uint32_t)(sAs[ty * BK + kk] & 1),
-                          sB + (kk * BN + tx) * BW64, sBe[kk * BN + tx],
+                          sB + (kk * BN + tx) * RB, sBe[kk * BN + tx],
                           (uint32_t)(sBs[kk * BN + tx] & 1), rs);
                 add_impl<W>(c, c, t, 0u, rs);
             }
@@ -697,16 +697,16 @@ void launch_gemm_block(BMat A, BMat B, BMat C, int64_t batch, int64_t m, int64_t
 {
     using Cfg = BlockCfg<W>;
     if (batch <= 0 || m <= 0 || n <= 0) return;
-    if constexpr (W == 64) {
-        using C64 = Block64Cfg;
+    if constexpr (W >= 32) {
+        using C64 = BlockSmCfg<W>;
         const int64_t tm = (m + C64::BM - 1) / C64::BM, tn = (n + C64::BN - 1) / C64::BN;
         static bool attr64 = false;
         if (!attr64) {
-            cudaFuncSetAttribute(gemm_block64_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaFuncSetAttribute(gemm_block_sm_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)C64::smem());
             attr64 = true;
         }
-        gemm_block64_kernel<64><<<(unsigned)(batch * tm * tn), C64::THREADS, C64::smem(), s>>>(
+        gemm_block_sm_kernel<W><<<(unsigned)(batch * tm * tn), C64::THREADS, C64::smem(), s>>>(
             A, B, C, m, l, n, p, tm, tn, st);
     } else {
         const int L = (p + 63) >> 6;
