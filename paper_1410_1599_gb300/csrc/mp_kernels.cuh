@@ -342,7 +342,7 @@ MP_DEV void mul_sm(Mp<W> &t, const uint32_t (&am)[W], int64_t ae, uint32_t as, c
 }
 
 template <int W> struct BlockSmCfg {
-    static constexpr int BN = 32, BM = 4, BK = (W == 64) ? 4 : 8, THREADS = BM * BN;
+    static constexpr int BN = 32, BM = (W == 16) ? 8 : 4, BK = (W == 64) ? 4 : 8, THREADS = BM * BN;
     static constexpr int RB = W + 4;                 // words per B record
     static constexpr size_t smem()
     {
@@ -356,7 +356,7 @@ gemm_block_sm_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, in
                      int64_t tiles_m, int64_t tiles_n, DevStatus *status)
 {
     using Cfg = BlockSmCfg<W>;
-    static_assert(W == 32 || W == 64, "wide leaf");
+    static_assert(W == 16 || W == 32 || W == 64, "wide leaf");
     constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK, RB = Cfg::RB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const RoundSpec rs = make_spec<W>(p);
@@ -697,7 +697,7 @@ void launch_gemm_block(BMat A, BMat B, BMat C, int64_t batch, int64_t m, int64_t
 {
     using Cfg = BlockCfg<W>;
     if (batch <= 0 || m <= 0 || n <= 0) return;
-    if constexpr (W >= 32) {
+    if constexpr (W >= 16) {
         using C64 = BlockSmCfg<W>;
         const int64_t tm = (m + C64::BM - 1) / C64::BM, tn = (n + C64::BN - 1) / C64::BN;
         static bool attr64 = false;
