@@ -796,12 +796,14 @@ int mplu(int64_t n, int32_t prec, mpmat_t *A, int64_t *piv, const mpmat_t *b, mp
             {
                 Prof pr(MP_K_LU, (double)(je - j0) * (n - j0), s);
                 if (fused) {
-                    launch_lu_pivot<WW>(A0, n, j0, piv, prec, st, s);
+                    // exchanges on the panel's columns now, on the rest after the panel
+                    launch_lu_pivot<WW>(A0, n, j0, piv, prec, st, s, j0, je);
                     for (int64_t k = j0; k < je; ++k)
-                        launch_lu_column<WW>(A0, n, k, je, piv, prec, st, cand, ticket, s);
+                        launch_lu_column<WW>(A0, n, j0, k, je, piv, prec, st, cand, ticket, s);
+                    launch_lu_laswp<WW>(A0, n, j0, je, piv, prec, s);
                 } else {
                     for (int64_t k = j0; k < je; ++k) {
-                        launch_lu_pivot<WW>(A0, n, k, piv, prec, st, s);
+                        launch_lu_pivot<WW>(A0, n, k, piv, prec, st, s, 0, n);
                         launch_lu_divide<WW>(A0, n, k, prec, s);
                         launch_lu_rank1<WW>(A0, k, k + 1, n, k + 1, je, prec, st, s);
                     }

@@ -97,7 +97,7 @@ void launch_split_finish(const long long *D, int64_t m, int64_t n, int p, const 
 // one elimination step a_ij -= a_ik a_kj on [r0, r1) x [c0, c1); solves
 template <int W>
 void launch_lu_pivot(BMat A, int64_t n, int64_t k, int64_t *piv, int p, DevStatus *st,
-                     cudaStream_t s);
+                     cudaStream_t s, int64_t c0, int64_t c1);
 template <int W>
 void launch_lu_divide(BMat A, int64_t n, int64_t k, int p, cudaStream_t s);
 template <int W>
@@ -114,8 +114,10 @@ constexpr int64_t LU_COL_MAX_CTAS = 152 * 8;
 template <int W>
 bool lu_fused_ok(int64_t panel);
 template <int W>
-void launch_lu_column(BMat A, int64_t n, int64_t k, int64_t je, int64_t *piv, int p, DevStatus *st,
-                      int64_t *cand, unsigned *ticket, cudaStream_t s);
+void launch_lu_column(BMat A, int64_t n, int64_t j0, int64_t k, int64_t je, int64_t *piv, int p,
+                      DevStatus *st, int64_t *cand, unsigned *ticket, cudaStream_t s);
+template <int W>
+void launch_lu_laswp(BMat A, int64_t n, int64_t j0, int64_t je, const int64_t *piv, int p, cudaStream_t s);
 template <int W>
 void launch_lu_u12(BMat A, int64_t n, int64_t j0, int64_t je, int p, DevStatus *st, cudaStream_t s);
 

@@ -20,8 +20,10 @@ MP_DEV bool absgreater(const Mp<W> &x, const Mp<W> &y)
 }
 
 // One CTA: pivot = first row i in [k, n) of largest |a_ik|; record it, then
-// exchange rows k and pivot over all n columns.  A zero pivot column is
-// recorded (smallest such column wins) and nothing is exchanged.
+// exchange rows k and pivot over the columns [c0, c1) (all n, or the panel
+// when the other columns are exchanged later by lu_laswp_kernel).  A zero
+// pivot column is recorded (smallest such column wins) and nothing is
+// exchanged.
 //
 // Each thread finds the first largest of its rows by full comparison.  The
 // block then reduces the key (exponent, top 64 mantissa bits), which orders
@@ -30,7 +32,7 @@ MP_DEV bool absgreater(const Mp<W> &x, const Mp<W> &y)
 // (usually one entry) by full comparison, lower row first among equals.
 template <int W>
 __global__ void __launch_bounds__(LuCfg<W>::PIVOT) lu_pivot_kernel(BMat A, int64_t n, int64_t k, int64_t *piv,
-                                                        int p, DevStatus *status)
+                                                        int p, DevStatus *status, int64_t c0, int64_t c1)
 {
     constexpr int NT = LuCfg<W>::PIVOT, NW = NT / 32;
     const RoundSpec rs = make_spec<W>(p);
@@ -99,7 +101,7 @@ __global__ void __launch_bounds__(LuCfg<W>::PIVOT) lu_pivot_kernel(BMat A, int64
     const int64_t pr = s_best;
     if (pr == k) return;
     const int L = rs.L;
-    for (int64_t c = tid; c < n; c += NT) {
+    for (int64_t c = c0 + tid; c < c1; c += NT) {
         for (int q = 0; q < L; ++q) {
             uint64_t *a = A.limb + (int64_t)q * A.plane + k * A.ld + c;
             uint64_t *b = A.limb + (int64_t)q * A.plane + pr * A.ld + c;
@@ -183,9 +185,11 @@ __global__ void lu_rank1_kernel(BMat A, int64_t k, int64_t r0, int64_t r1, int64
 // (a_ij = RN(a_ij - RN(l_ik a_kj))), lane 0 tracking the first largest
 // |a_i,k+1| of the warp's rows.  Each CTA posts its candidate; the last CTA to
 // finish (ticket counter, no waiting) picks the pivot of column k+1 among
-// the posted rows and exchanges the two full rows, so the next launch starts
-// on a pivoted column.  The operations and their order per element are the
-// same as in the separate kernels.
+// the posted rows and exchanges the two rows over the panel's columns, so
+// the next launch starts on a pivoted column; the other columns take the
+// panel's exchanges afterwards, in the same order (lu_laswp_kernel).  The
+// operations and their order per element are the same as in the separate
+// kernels.
 constexpr int LU_COL_WARPS = 4;
 
 // First row of largest |a_{r,col}| among the rows rows[0 .. cnt), ties to the
@@ -260,11 +264,11 @@ __device__ int64_t cta_pick_row(const BMat &A, int64_t col, int cnt, RowOf row_o
     return pr;    // meaningful in thread 0
 }
 
-// exchange rows r1 and r2 of A over all n columns (the threads of one CTA)
+// exchange rows r1 and r2 of A over the columns [c0, c1) (one CTA)
 template <int W>
-__device__ void cta_swap_rows(const BMat &A, int64_t n, int64_t r1, int64_t r2, int L)
+__device__ void cta_swap_rows(const BMat &A, int64_t c0, int64_t c1, int64_t r1, int64_t r2, int L)
 {
-    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+    for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
         for (int q = 0; q < L; ++q) {
             uint64_t *a = A.limb + (int64_t)q * A.plane + r1 * A.ld + c;
             uint64_t *b = A.limb + (int64_t)q * A.plane + r2 * A.ld + c;
@@ -285,8 +289,8 @@ __device__ void cta_swap_rows(const BMat &A, int64_t n, int64_t r1, int64_t r2, 
 
 template <int W>
 __global__ void __launch_bounds__(LU_COL_WARPS * 32)
-lu_column_kernel(BMat A, int64_t n, int64_t k, int64_t je, int64_t *piv, int p, DevStatus *status,
-                 int64_t *cand, unsigned *ticket)
+lu_column_kernel(BMat A, int64_t n, int64_t j0, int64_t k, int64_t je, int64_t *piv, int p,
+                 DevStatus *status, int64_t *cand, unsigned *ticket)
 {
     static_assert(W <= 32, "warp-per-row column step");
     constexpr int NT = LU_COL_WARPS * 32;
@@ -370,7 +374,7 @@ lu_column_kernel(BMat A, int64_t n, int64_t k, int64_t je, int64_t *piv, int p, 
         *ticket = 0u;                       // ready for the next launch
     }
     __syncthreads();
-    if (s_pr != k + 1) cta_swap_rows<W>(A, n, k + 1, s_pr, rs.L);
+    if (s_pr != k + 1) cta_swap_rows<W>(A, j0, je, k + 1, s_pr, rs.L);   // panel columns only
 }
 
 // ------------------------------------------- U12 = L11^-1 A12, one launch
@@ -562,12 +566,45 @@ __global__ void lu_bwd_update_kernel(BMat LU, BMat y, BMat x, int64_t c0, int64_
     if (st<W>(yi, y, 0, i, 0, rs.L)) flag(status, ST_RANGE);
 }
 
+// Row exchanges k = j0 .. je-1 (rows k and piv[k], in order) on the columns
+// outside the panel, [0, j0) and [je, n): one thread per column.  Exchanges
+// of whole rows commute with the panel's work, which touches only the
+// panel's columns, so the factors equal those of exchanging full rows at once.
+template <int W>
+__global__ void lu_laswp_kernel(BMat A, int64_t n, int64_t j0, int64_t je, const int64_t *piv, int L)
+{
+    const int64_t outside = n - (je - j0);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < outside;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = t < j0 ? t : t + (je - j0);
+        for (int64_t k = j0; k < je; ++k) {
+            const int64_t r = piv[k];
+            if (r == k) continue;
+            for (int q = 0; q < L; ++q) {
+                uint64_t *a = A.limb + (int64_t)q * A.plane + k * A.ld + c;
+                uint64_t *b = A.limb + (int64_t)q * A.plane + r * A.ld + c;
+                const uint64_t x = *a;
+                *a = *b;
+                *b = x;
+            }
+            int64_t *ea = A.exp + k * A.ld + c, *eb = A.exp + r * A.ld + c;
+            const int64_t te = *ea;
+            *ea = *eb;
+            *eb = te;
+            int8_t *sa = A.sign + k * A.ld + c, *sb = A.sign + r * A.ld + c;
+            const int8_t ts = *sa;
+            *sa = *sb;
+            *sb = ts;
+        }
+    }
+}
+
 // ================================================================ launchers
 template <int W>
 void launch_lu_pivot(BMat A, int64_t n, int64_t k, int64_t *piv, int p, DevStatus *st,
-                     cudaStream_t s)
+                     cudaStream_t s, int64_t c0, int64_t c1)
 {
-    lu_pivot_kernel<W><<<1, LuCfg<W>::PIVOT, 0, s>>>(A, n, k, piv, p, st);
+    lu_pivot_kernel<W><<<1, LuCfg<W>::PIVOT, 0, s>>>(A, n, k, piv, p, st, c0, c1);
 }
 
 template <int W>
@@ -616,16 +653,25 @@ bool lu_fused_ok(int64_t panel)
 }
 
 template <int W>
-void launch_lu_column(BMat A, int64_t n, int64_t k, int64_t je, int64_t *piv, int p, DevStatus *st,
-                      int64_t *cand, unsigned *ticket, cudaStream_t s)
+void launch_lu_column(BMat A, int64_t n, int64_t j0, int64_t k, int64_t je, int64_t *piv, int p,
+                      DevStatus *st, int64_t *cand, unsigned *ticket, cudaStream_t s)
 {
     if constexpr (W <= 32) {
         const int64_t rows = n - k - 1;
         if (rows <= 0) return;
         int64_t g = (rows + LU_COL_WARPS - 1) / LU_COL_WARPS;
         if (g > LU_COL_MAX_CTAS) g = LU_COL_MAX_CTAS;
-        lu_column_kernel<W><<<(unsigned)g, LU_COL_WARPS * 32, 0, s>>>(A, n, k, je, piv, p, st, cand, ticket);
+        lu_column_kernel<W><<<(unsigned)g, LU_COL_WARPS * 32, 0, s>>>(A, n, j0, k, je, piv, p, st, cand,
+                                                                     ticket);
     }
+}
+
+template <int W>
+void launch_lu_laswp(BMat A, int64_t n, int64_t j0, int64_t je, const int64_t *piv, int p, cudaStream_t s)
+{
+    const int64_t outside = n - (je - j0);
+    if (outside <= 0) return;
+    lu_laswp_kernel<W><<<grid_for(outside, 128), 128, 0, s>>>(A, n, j0, je, piv, (p + 63) >> 6);
 }
 
 template <int W>
@@ -641,15 +687,17 @@ void launch_lu_u12(BMat A, int64_t n, int64_t j0, int64_t je, int p, DevStatus *
 
 #define MPG_INSTANTIATE_LU(W)                                                                   \
     template void launch_lu_pivot<W>(BMat, int64_t, int64_t, int64_t *, int, DevStatus *,       \
-                                     cudaStream_t);                                             \
+                                     cudaStream_t, int64_t, int64_t);                           \
     template void launch_lu_divide<W>(BMat, int64_t, int64_t, int, cudaStream_t);               \
     template void launch_lu_rank1<W>(BMat, int64_t, int64_t, int64_t, int64_t, int64_t, int,    \
                                      DevStatus *, cudaStream_t);                                \
     template void launch_lu_solve<W>(BMat, int64_t, const int64_t *, BMat, BMat, BMat,          \
                                      int64_t *, int, DevStatus *, cudaStream_t);                \
     template bool lu_fused_ok<W>(int64_t);                                                      \
-    template void launch_lu_column<W>(BMat, int64_t, int64_t, int64_t, int64_t *, int,          \
+    template void launch_lu_column<W>(BMat, int64_t, int64_t, int64_t, int64_t, int64_t *, int, \
                                       DevStatus *, int64_t *, unsigned *, cudaStream_t);        \
+    template void launch_lu_laswp<W>(BMat, int64_t, int64_t, int64_t, const int64_t *, int,     \
+                                     cudaStream_t);                                             \
     template void launch_lu_u12<W>(BMat, int64_t, int64_t, int64_t, int, DevStatus *, cudaStream_t);
 
 }  // namespace mpg
