@@ -2,9 +2,12 @@
 // mp_split.cuh): D_s(i, j) = sum_{u+v=s} sum_k A_u(i,k) B_v(j,k) exactly, for
 // every weight diagonal s, on the fifth-generation tensor cores.
 //
-// One CTA owns a 128 x 256 output tile and a strided set of diagonals.
-//   warp 0     TMA producer: 128 x 64 A and 256 x 64 B fp16 tiles (128-byte
-//              swizzle) into a 4-stage shared-memory ring;
+// A cluster of two CTAs owns two 128 x 256 output tiles stacked in rows (the
+// same 256 columns of B) and a strided set of diagonals.
+//   warp 0     TMA producer: its own 128 x 64 A tile and one 128-row half of
+//              the shared 256 x 64 B tile, multicast to both CTAs (fp16,
+//              128-byte swizzle) into a 4-stage shared-memory ring; a stage
+//              is refilled once both CTAs' MMAs have consumed it;
 //   warp 1     allocates the tensor memory and issues tcgen05.mma
 //              (kind::f16, M = 128, N = 256, K = 16, fp32 accumulation) from
 //              one thread; two 256-column accumulators alternate;
@@ -90,15 +93,17 @@ split_slice_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_co
     __shared__ volatile int abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t tile = blockIdx.x / sc.groups;
-    const int grp = (int)(blockIdx.x % sc.groups);
-    const int64_t i0 = (tile / sc.tiles_n) * BM, j0 = (tile % sc.tiles_n) * BN;
+    const uint32_t rank = tc::cluster_rank();                   // 0 or 1 in the CTA pair
+    const int64_t cl = blockIdx.x >> 1;
+    const int64_t pair = cl / sc.groups;
+    const int grp = (int)(cl % sc.groups);
+    const int64_t i0 = (2 * (pair / sc.tiles_n) + rank) * BM, j0 = (pair % sc.tiles_n) * BN;
     const int S = sc.S, nkb = sc.nkb;
 
     if (threadIdx.x == 0) {
         for (int st = 0; st < STAGES; ++st) {
             tc::mbar_init(&full_bar[st], 1);
-            tc::mbar_init(&empty_bar[st], 1);
+            tc::mbar_init(&empty_bar[st], 2);          // both CTAs' MMAs consumed it
         }
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(&accf_bar[b], 1);
@@ -110,7 +115,7 @@ split_slice_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_co
     }
     if (warp == 1) tc::tmem_alloc(&tmem_slot, TMEM_COLS);
     tc::fence_before_sync();
-    __syncthreads();
+    tc::cluster_sync();                                 // barriers of both CTAs initialised
     tc::fence_after_sync();
     const uint32_t tmem = tmem_slot;
 
@@ -136,8 +141,17 @@ split_slice_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_co
                     uint8_t *sa = ring + st * STAGE_BYTES, *sb = sa + A_BYTES;
                     tc::mbar_expect_tx(&full_bar[st], STAGE_BYTES);
                     tc::tma_load_2d(sa, &map_a, kb * BK, (int32_t)(u * sc.m + i0), &full_bar[st]);
-                    tc::tma_load_2d(sb, &map_b, kb * BK, (int32_t)((s - u) * sc.n + j0), &full_bar[st]);
+                    tc::tma_load_2d_mc(sb + rank * (B_BYTES / 2), &map_b, kb * BK,
+                                       (int32_t)((s - u) * sc.n + j0 + rank * (BN / 2)), &full_bar[st], 0x3);
                 }
+            }
+            if (!abort_flag) {
+                // both CTAs' consumption of the last fills has reached this CTA
+                for (uint32_t k = g > STAGES ? g - STAGES : 0; k < g; ++k)
+                    if (!tc::mbar_wait(&empty_bar[k % STAGES], (k / STAGES) & 1u, &abort_flag, WAIT_LIMIT)) {
+                        fail();
+                        break;
+                    }
             }
             if (abort_flag) {
                 // unwinding: let the copies still in flight land (bounded)
@@ -176,7 +190,7 @@ split_slice_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_co
                     for (int k = 0; k < BK / 16; ++k)
                         tc::mma_f16(d, tc::desc_k128(sa + 32 * k), tc::desc_k128(sb + 32 * k), idesc,
                                     (first && k == 0) ? 0u : 1u);
-                    tc::mma_commit(&empty_bar[st]);                 // frees the stage when done
+                    tc::mma_commit_mc(&empty_bar[st], 0x3);         // frees the stage in both CTAs
                     if (last) {
                         tc::mma_commit(&accf_bar[buf]);             // the chunk is complete
                         ++c;
@@ -232,7 +246,7 @@ split_slice_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_co
     }
 
     tc::fence_before_sync();
-    __syncthreads();
+    tc::cluster_sync();                                 // no multicast or arrival still bound for this CTA
     if (warp == 1) {
         tc::fence_after_sync();
         tc::tmem_free(tmem, TMEM_COLS);
@@ -286,7 +300,7 @@ int launch_split_slices(const __half *pa, const __half *pb, int64_t m, int64_t l
     if (((uintptr_t)pa & 15) || ((uintptr_t)pb & 15) || (lp * 2) % 16) return MP_ERR_ARG;
     if ((int64_t)S * m > 0x7fffffff || (int64_t)S * n > 0x7fffffff) return MP_ERR_ARG;
     CUtensorMap ma, mb;
-    if (!make_map(&ma, pa, (int64_t)S * m, lp, BM) || !make_map(&mb, pb, (int64_t)S * n, lp, BN)) {
+    if (!make_map(&ma, pa, (int64_t)S * m, lp, BM) || !make_map(&mb, pb, (int64_t)S * n, lp, BN / 2)) {
         if (std::getenv("MPGEMM_DEBUG")) std::fprintf(stderr, "split: tensor map encoding failed\n");
         return MP_ERR_UNSUPPORTED;
     }
@@ -307,12 +321,24 @@ int launch_split_slices(const __half *pa, const __half *pb, int64_t m, int64_t l
     sc.m = m;
     sc.n = n;
     sc.tiles_n = (n + BN - 1) / BN;
-    const int64_t tiles = ((m + BM - 1) / BM) * sc.tiles_n;
-    // spread the diagonals of a tile over several CTAs until about two waves
+    const int64_t pairs = ((m + 2 * BM - 1) / (2 * BM)) * sc.tiles_n;   // CTA pairs over row tiles
+    // spread the diagonals of a tile pair over several clusters until about two waves
     int groups = 1;
-    while (tiles * groups < 2 * 152 && groups * 2 <= 2 * S - 1) groups *= 2;
+    while (2 * pairs * groups < 2 * 152 && groups * 2 <= 2 * S - 1) groups *= 2;
     sc.groups = groups;
-    split_slice_tc_kernel<<<(unsigned)(tiles * groups), THREADS, SMEM_BYTES, s>>>(ma, mb, sc, D, st);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(2 * pairs * groups));
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute attr_cl[1];
+    attr_cl[0].id = cudaLaunchAttributeClusterDimension;
+    attr_cl[0].val.clusterDim.x = 2;
+    attr_cl[0].val.clusterDim.y = 1;
+    attr_cl[0].val.clusterDim.z = 1;
+    cfg.attrs = attr_cl;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, split_slice_tc_kernel, ma, mb, sc, D, st);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess && std::getenv("MPGEMM_DEBUG"))
         std::fprintf(stderr, "split: slice kernel launch failed: %s\n", cudaGetErrorString(e));
