@@ -2,12 +2,14 @@
 // mp_split.cuh): D_s(i, j) = sum_{u+v=s} sum_k A_u(i,k) B_v(j,k) exactly, for
 // every weight diagonal s, on the fifth-generation tensor cores.
 //
-// A cluster of two CTAs owns two 128 x 256 output tiles stacked in rows (the
-// same 256 columns of B) and a strided set of diagonals.
-//   warp 0     TMA producer: its own 128 x 64 A tile and one 128-row half of
-//              the shared 256 x 64 B tile, multicast to both CTAs (fp16,
-//              128-byte swizzle) into a 4-stage shared-memory ring; a stage
-//              is refilled once both CTAs' MMAs have consumed it;
+// A cluster of 2 x 2 CTAs owns a 256 x 512 block of outputs (four 128 x 256
+// tiles) and a strided set of diagonals.  CTA (r, c) shares its A tile with
+// (r, 1-c) and its B tile with (1-r, c).
+//   warp 0     TMA producer: one 64-row half of its 128 x 64 A tile,
+//              multicast to its row peer, and one 128-row half of its
+//              256 x 64 B tile, multicast to its column peer (fp16, 128-byte
+//              swizzle), into a 4-stage shared-memory ring; a stage is
+//              refilled once this CTA and both peers have consumed it;
 //   warp 1     allocates the tensor memory and issues tcgen05.mma
 //              (kind::f16, M = 128, N = 256, K = 16, fp32 accumulation) from
 //              one thread; two 256-column accumulators alternate;
@@ -50,7 +52,7 @@ constexpr long long WAIT_LIMIT = 4000000000ll;                  // ~2 s of clock
 
 struct Sched {
     int S, groups, nkb;
-    int64_t m, n, tiles_n;
+    int64_t m, n, tiles_n2;     // tiles_n2: pairs of 256-column tiles
 };
 
 // diagonal s of this CTA: pairs u in [u0, u1]; steps = pairs x k-blocks
@@ -93,17 +95,20 @@ split_slice_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_co
     __shared__ volatile int abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t rank = tc::cluster_rank();                   // 0 or 1 in the CTA pair
-    const int64_t cl = blockIdx.x >> 1;
-    const int64_t pair = cl / sc.groups;
+    const uint32_t rank = tc::cluster_rank();                   // r * 2 + c
+    const uint32_t cr = rank >> 1, cc = rank & 1u;
+    const uint16_t mask_a = (uint16_t)(3u << (2 * cr));         // CTAs sharing this A tile
+    const uint16_t mask_b = (uint16_t)((1u << cc) | (4u << cc)); // CTAs sharing this B tile
+    const int64_t cl = blockIdx.x >> 2;
+    const int64_t quad = cl / sc.groups;
     const int grp = (int)(cl % sc.groups);
-    const int64_t i0 = (2 * (pair / sc.tiles_n) + rank) * BM, j0 = (pair % sc.tiles_n) * BN;
+    const int64_t i0 = (2 * (quad / sc.tiles_n2) + cr) * BM, j0 = (2 * (quad % sc.tiles_n2) + cc) * BN;
     const int S = sc.S, nkb = sc.nkb;
 
     if (threadIdx.x == 0) {
         for (int st = 0; st < STAGES; ++st) {
             tc::mbar_init(&full_bar[st], 1);
-            tc::mbar_init(&empty_bar[st], 2);          // both CTAs' MMAs consumed it
+            tc::mbar_init(&empty_bar[st], 3);          // this CTA and both peers consumed it
         }
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(&accf_bar[b], 1);
@@ -140,9 +145,10 @@ split_slice_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_co
                     const int u = u0 + t / nkb, kb = t % nkb;
                     uint8_t *sa = ring + st * STAGE_BYTES, *sb = sa + A_BYTES;
                     tc::mbar_expect_tx(&full_bar[st], STAGE_BYTES);
-                    tc::tma_load_2d(sa, &map_a, kb * BK, (int32_t)(u * sc.m + i0), &full_bar[st]);
-                    tc::tma_load_2d_mc(sb + rank * (B_BYTES / 2), &map_b, kb * BK,
-                                       (int32_t)((s - u) * sc.n + j0 + rank * (BN / 2)), &full_bar[st], 0x3);
+                    tc::tma_load_2d_mc(sa + cc * (A_BYTES / 2), &map_a, kb * BK,
+                                       (int32_t)(u * sc.m + i0 + cc * (BM / 2)), &full_bar[st], mask_a);
+                    tc::tma_load_2d_mc(sb + cr * (B_BYTES / 2), &map_b, kb * BK,
+                                       (int32_t)((s - u) * sc.n + j0 + cr * (BN / 2)), &full_bar[st], mask_b);
                 }
             }
             if (!abort_flag) {
@@ -190,7 +196,7 @@ split_slice_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_co
                     for (int k = 0; k < BK / 16; ++k)
                         tc::mma_f16(d, tc::desc_k128(sa + 32 * k), tc::desc_k128(sb + 32 * k), idesc,
                                     (first && k == 0) ? 0u : 1u);
-                    tc::mma_commit_mc(&empty_bar[st], 0x3);         // frees the stage in both CTAs
+                    tc::mma_commit_mc(&empty_bar[st], mask_a | mask_b);   // self and both peers
                     if (last) {
                         tc::mma_commit(&accf_bar[buf]);             // the chunk is complete
                         ++c;
@@ -300,7 +306,7 @@ int launch_split_slices(const __half *pa, const __half *pb, int64_t m, int64_t l
     if (((uintptr_t)pa & 15) || ((uintptr_t)pb & 15) || (lp * 2) % 16) return MP_ERR_ARG;
     if ((int64_t)S * m > 0x7fffffff || (int64_t)S * n > 0x7fffffff) return MP_ERR_ARG;
     CUtensorMap ma, mb;
-    if (!make_map(&ma, pa, (int64_t)S * m, lp, BM) || !make_map(&mb, pb, (int64_t)S * n, lp, BN / 2)) {
+    if (!make_map(&ma, pa, (int64_t)S * m, lp, BM / 2) || !make_map(&mb, pb, (int64_t)S * n, lp, BN / 2)) {
         if (std::getenv("MPGEMM_DEBUG")) std::fprintf(stderr, "split: tensor map encoding failed\n");
         return MP_ERR_UNSUPPORTED;
     }
@@ -320,20 +326,20 @@ int launch_split_slices(const __half *pa, const __half *pb, int64_t m, int64_t l
     sc.nkb = (int)((lp + BK - 1) / BK);
     sc.m = m;
     sc.n = n;
-    sc.tiles_n = (n + BN - 1) / BN;
-    const int64_t pairs = ((m + 2 * BM - 1) / (2 * BM)) * sc.tiles_n;   // CTA pairs over row tiles
-    // spread the diagonals of a tile pair over several clusters until about two waves
+    sc.tiles_n2 = (n + 2 * BN - 1) / (2 * BN);
+    const int64_t quads = ((m + 2 * BM - 1) / (2 * BM)) * sc.tiles_n2;   // 2 x 2 tile blocks
+    // spread the diagonals of a block over several clusters until about two waves
     int groups = 1;
-    while (2 * pairs * groups < 2 * 152 && groups * 2 <= 2 * S - 1) groups *= 2;
+    while (4 * quads * groups < 2 * 152 && groups * 2 <= 2 * S - 1) groups *= 2;
     sc.groups = groups;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(2 * pairs * groups));
+    cfg.gridDim = dim3((unsigned)(4 * quads * groups));
     cfg.blockDim = dim3(THREADS);
     cfg.dynamicSmemBytes = SMEM_BYTES;
     cfg.stream = s;
     cudaLaunchAttribute attr_cl[1];
     attr_cl[0].id = cudaLaunchAttributeClusterDimension;
-    attr_cl[0].val.clusterDim.x = 2;
+    attr_cl[0].val.clusterDim.x = 4;
     attr_cl[0].val.clusterDim.y = 1;
     attr_cl[0].val.clusterDim.z = 1;
     cfg.attrs = attr_cl;
