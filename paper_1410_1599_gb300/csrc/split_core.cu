@@ -53,6 +53,7 @@ constexpr long long WAIT_LIMIT = 4000000000ll;                  // ~2 s of clock
 struct Sched {
     int S, groups, nkb;
     int64_t m, n, tiles_n2;     // tiles_n2: pairs of 256-column tiles
+    int64_t nitems;             // (2 x 2 tile block, diagonal group) work items
 };
 
 // diagonal s of this CTA: pairs u in [u0, u1]; steps = pairs x k-blocks
@@ -99,10 +100,18 @@ split_slice_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_co
     const uint32_t cr = rank >> 1, cc = rank & 1u;
     const uint16_t mask_a = (uint16_t)(3u << (2 * cr));         // CTAs sharing this A tile
     const uint16_t mask_b = (uint16_t)((1u << cc) | (4u << cc)); // CTAs sharing this B tile
-    const int64_t cl = blockIdx.x >> 2;
-    const int64_t quad = cl / sc.groups;
-    const int grp = (int)(cl % sc.groups);
-    const int64_t i0 = (2 * (quad / sc.tiles_n2) + cr) * BM, j0 = (2 * (quad % sc.tiles_n2) + cc) * BN;
+    // persistent clusters: work items (2 x 2 tile block, diagonal group) are
+    // taken round-robin; every role walks the same sequence
+    const int64_t cl0 = blockIdx.x >> 2, ncl = gridDim.x >> 2;
+    // (quads vary fastest: clusters running at the same time walk the same
+    // diagonals on neighbouring blocks and share operand tiles through L2)
+    auto item = [&](int64_t it, int64_t &i0, int64_t &j0) -> int {
+        const int64_t quads = sc.nitems / sc.groups;
+        const int64_t quad = it % quads;
+        i0 = (2 * (quad / sc.tiles_n2) + cr) * BM;
+        j0 = (2 * (quad % sc.tiles_n2) + cc) * BN;
+        return (int)(it / quads);
+    };
     const int S = sc.S, nkb = sc.nkb;
 
     if (threadIdx.x == 0) {
@@ -135,6 +144,9 @@ split_slice_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_co
             tc::prefetch_map(&map_a);
             tc::prefetch_map(&map_b);
             uint32_t g = 0;
+            for (int64_t it = cl0; it < sc.nitems && !abort_flag; it += ncl) {
+            int64_t i0, j0;
+            const int grp = item(it, i0, j0);
             for (int s = grp; s <= 2 * S - 2 && !abort_flag; s += sc.groups) {
                 int u0, u1;
                 diag_range(s, S, u0, u1);
@@ -150,6 +162,7 @@ split_slice_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_co
                     tc::tma_load_2d_mc(sb + cr * (B_BYTES / 2), &map_b, kb * BK,
                                        (int32_t)((s - u) * sc.n + j0 + cr * (BN / 2)), &full_bar[st], mask_b);
                 }
+            }
             }
             if (!abort_flag) {
                 // both CTAs' consumption of the last fills has reached this CTA
@@ -170,6 +183,9 @@ split_slice_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_co
         if (lane == 0) {
             const uint32_t idesc = tc::idesc_f16_f32(BM, BN);
             uint32_t g = 0, c = 0;
+            for (int64_t it = cl0; it < sc.nitems && !abort_flag; it += ncl) {
+            int64_t i0, j0;
+            const int grp = item(it, i0, j0);
             for (int s = grp; s <= 2 * S - 2 && !abort_flag; s += sc.groups) {
                 int u0, u1;
                 diag_range(s, S, u0, u1);
@@ -204,6 +220,7 @@ split_slice_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_co
                 }
                 if (!ok) break;
             }
+            }
             if (abort_flag) {
                 // unwinding: every MMA issued so far completes before the
                 // tensor memory is released (bounded)
@@ -216,10 +233,13 @@ split_slice_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_co
         const int ew = warp - 2;
         const int quarter = warp & 3;                               // TMEM lanes of this warp
         const int part = ew >> 2;                                   // column range of the tile
-        const int64_t i = i0 + quarter * 32 + lane;
         const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
         int32_t acc[EPI_COLS];
         uint32_t c = 0;
+        for (int64_t it = cl0; it < sc.nitems && !abort_flag; it += ncl) {
+        int64_t i0, j0;
+        const int grp = item(it, i0, j0);
+        const int64_t i = i0 + quarter * 32 + lane;
         for (int s = grp; s <= 2 * S - 2 && !abort_flag; s += sc.groups) {
             int u0, u1;
             diag_range(s, S, u0, u1);
@@ -248,6 +268,7 @@ split_slice_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_co
                     flush_columns<0>(Ds + i * sc.n + jb, acc, (int)(left < EPI_COLS ? left : EPI_COLS), seg == 0);
                 }
             }
+        }
         }
     }
 
@@ -328,12 +349,11 @@ int launch_split_slices(const __half *pa, const __half *pb, int64_t m, int64_t l
     sc.n = n;
     sc.tiles_n2 = (n + 2 * BN - 1) / (2 * BN);
     const int64_t quads = ((m + 2 * BM - 1) / (2 * BM)) * sc.tiles_n2;   // 2 x 2 tile blocks
-    // spread the diagonals of a block over several clusters until about two waves
-    int groups = 1;
-    while (4 * quads * groups < 2 * 152 && groups * 2 <= 2 * S - 1) groups *= 2;
-    sc.groups = groups;
+    // One resident cluster of four per four SMs (as many as fit at once); the
+    // diagonals of a block are spread over groups until there are about
+    // eight work items per cluster, so that the round-robin leaves little
+    // imbalance at the end.
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(4 * quads * groups));
     cfg.blockDim = dim3(THREADS);
     cfg.dynamicSmemBytes = SMEM_BYTES;
     cfg.stream = s;
@@ -344,6 +364,21 @@ int launch_split_slices(const __half *pa, const __half *pb, int64_t m, int64_t l
     attr_cl[0].val.clusterDim.z = 1;
     cfg.attrs = attr_cl;
     cfg.numAttrs = 1;
+    static int resident = 0;
+    if (resident <= 0) {
+        cfg.gridDim = dim3(4 * 38);
+        if (cudaOccupancyMaxActiveClusters(&resident, split_slice_tc_kernel, &cfg) != cudaSuccess || resident <= 0) {
+            (void)cudaGetLastError();                   // clear a failed query
+            resident = 36;
+        }
+    }
+    const int64_t clusters = resident;
+    int groups = 1;
+    while (quads * groups < 8 * clusters && groups * 2 <= 2 * S - 1) groups *= 2;
+    sc.groups = groups;
+    sc.nitems = quads * groups;
+    const int64_t ncl = sc.nitems < clusters ? sc.nitems : clusters;
+    cfg.gridDim = dim3((unsigned)(4 * ncl));
     cudaLaunchKernelEx(&cfg, split_slice_tc_kernel, ma, mb, sc, D, st);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess && std::getenv("MPGEMM_DEBUG"))
