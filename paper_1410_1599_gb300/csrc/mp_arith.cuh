@@ -187,8 +187,12 @@ MP_DEV void round_mant(uint32_t (&m)[W], int64_t &e, uint32_t below, bool sticky
 }
 
 // ------------------------------------------------------------ multiplication
-// P (2W words) = a * b, schoolbook by rows of b with two carry chains per row
-// (low and high halves of the 32x32 partial products).
+// Schoolbook products by rows of b.  Each partial product a_i b_j is formed
+// with the running row carry as one 64-bit multiply-add
+// (a_i b_j + P + c <= 2^64 - 1), which needs fewer instructions than
+// separate low/high multiply-add carry chains.
+//
+// P (2W words) = a * b
 template <int W>
 MP_DEV void mul_full(uint32_t (&P)[2 * W], const uint32_t (&a)[W], const uint32_t (&b)[W])
 {
@@ -197,14 +201,14 @@ MP_DEV void mul_full(uint32_t (&P)[2 * W], const uint32_t (&a)[W], const uint32_
 #pragma unroll
     for (int j = 0; j < W; ++j) {
         const uint32_t bj = b[j];
-        P[j] = mad_lo_cc(a[0], bj, P[j]);
+        uint64_t c = 0;
 #pragma unroll
-        for (int i = 1; i < W; ++i) P[j + i] = madc_lo_cc(a[i], bj, P[j + i]);
-        P[j + W] = addc(P[j + W], 0u);
-        P[j + 1] = mad_hi_cc(a[0], bj, P[j + 1]);
-#pragma unroll
-        for (int i = 1; i < W - 1; ++i) P[j + 1 + i] = madc_hi_cc(a[i], bj, P[j + 1 + i]);
-        P[j + W] = madc_hi(a[W - 1], bj, P[j + W]);
+        for (int i = 0; i < W; ++i) {
+            const uint64_t t = (uint64_t)a[i] * bj + P[i + j] + c;
+            P[i + j] = (uint32_t)t;
+            c = t >> 32;
+        }
+        P[j + W] = (uint32_t)c;            // not yet written by any row
     }
 }
 
@@ -222,14 +226,14 @@ MP_DEV void mul_trunc(uint32_t (&P)[2 * W], const uint32_t (&a)[W], const uint32
     for (int j = 0; j < W; ++j) {
         const uint32_t bj = b[j];
         const int i0 = (W - 2 - j > 0) ? W - 2 - j : 0;
-        P[j + i0] = mad_lo_cc(a[i0], bj, P[j + i0]);
+        uint64_t c = 0;
 #pragma unroll
-        for (int i = i0 + 1; i < W; ++i) P[j + i] = madc_lo_cc(a[i], bj, P[j + i]);
-        P[j + W] = addc(P[j + W], 0u);
-        P[j + i0 + 1] = mad_hi_cc(a[i0], bj, P[j + i0 + 1]);
-#pragma unroll
-        for (int i = i0 + 1; i < W - 1; ++i) P[j + 1 + i] = madc_hi_cc(a[i], bj, P[j + 1 + i]);
-        P[j + W] = madc_hi(a[W - 1], bj, P[j + W]);
+        for (int i = i0; i < W; ++i) {
+            const uint64_t t = (uint64_t)a[i] * bj + P[i + j] + c;
+            P[i + j] = (uint32_t)t;
+            c = t >> 32;
+        }
+        P[j + W] = (uint32_t)c;
     }
 }
 
@@ -254,14 +258,14 @@ MP_DEV void mul_top(uint32_t (&hi)[W], uint32_t &pw1, uint32_t &pw2, bool &low_n
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const uint32_t bj = b[j + u];
-            acc[u] = mad_lo_cc(a[0], bj, acc[u]);
+            uint64_t c = 0;
 #pragma unroll
-            for (int i = 1; i < W; ++i) acc[u + i] = madc_lo_cc(a[i], bj, acc[u + i]);
-            acc[u + W] = addc(acc[u + W], 0u);
-            acc[u + 1] = mad_hi_cc(a[0], bj, acc[u + 1]);
-#pragma unroll
-            for (int i = 1; i < W - 1; ++i) acc[u + 1 + i] = madc_hi_cc(a[i], bj, acc[u + 1 + i]);
-            acc[u + W] = madc_hi(a[W - 1], bj, acc[u + W]);
+            for (int i = 0; i < W; ++i) {
+                const uint64_t t = (uint64_t)a[i] * bj + acc[u + i] + c;
+                acc[u + i] = (uint32_t)t;
+                c = t >> 32;
+            }
+            acc[u + W] = (uint32_t)c;      // the window's top words start at zero
         }
         if (j == W - 4) {
             st |= acc[0] | acc[1];

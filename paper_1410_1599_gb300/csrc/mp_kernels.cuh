@@ -268,15 +268,14 @@ MP_DEV void mul_trunc_sm(uint32_t (&acc)[W + 2], const uint32_t (&a)[W], const u
             const uint32_t bj = bv[u];
             const int i0 = (W - 2 - j > 0) ? W - 2 - j : 0;
             // position i + j lives in acc[i + j - (W - 2)]
-            acc[j + i0 - (W - 2)] = mad_lo_cc(a[i0], bj, acc[j + i0 - (W - 2)]);
+            uint64_t c = 0;
 #pragma unroll
-            for (int i = i0 + 1; i < W; ++i) acc[j + i - (W - 2)] = madc_lo_cc(a[i], bj, acc[j + i - (W - 2)]);
-            acc[j + 2] = addc(acc[j + 2], 0u);
-            acc[j + i0 + 1 - (W - 2)] = mad_hi_cc(a[i0], bj, acc[j + i0 + 1 - (W - 2)]);
-#pragma unroll
-            for (int i = i0 + 1; i < W - 1; ++i)
-                acc[j + 1 + i - (W - 2)] = madc_hi_cc(a[i], bj, acc[j + 1 + i - (W - 2)]);
-            acc[j + 2] = madc_hi(a[W - 1], bj, acc[j + 2]);
+            for (int i = i0; i < W; ++i) {
+                const uint64_t t = (uint64_t)a[i] * bj + acc[j + i - (W - 2)] + c;
+                acc[j + i - (W - 2)] = (uint32_t)t;
+                c = t >> 32;
+            }
+            acc[j + 2] = (uint32_t)c;                   // not yet written by any row
         }
     }
 }
@@ -344,6 +343,7 @@ MP_DEV void mul_sm(Mp<W> &t, const uint32_t (&am)[W], int64_t ae, uint32_t as, c
 template <int W> struct BlockSmCfg {
     static constexpr int BN = 32, BM = (W == 16) ? 8 : 4, BK = (W == 64) ? 4 : 8, THREADS = BM * BN;
     static constexpr int RB = W + 4;                 // words per B record
+    static constexpr int MIN_CTAS = (W <= 32) ? 3 : 1;   // resident CTAs per SM to plan registers for
     static constexpr size_t smem()
     {
         return (size_t)BK * BN * RB * 4 + (size_t)BM * BK * W * 4 + (size_t)(BM * BK + BK * BN) * 9;
@@ -351,7 +351,7 @@ template <int W> struct BlockSmCfg {
 };
 
 template <int W>
-__global__ void __launch_bounds__(BlockSmCfg<W>::THREADS)
+__global__ void __launch_bounds__(BlockSmCfg<W>::THREADS, BlockSmCfg<W>::MIN_CTAS)
 gemm_block_sm_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p,
                      int64_t tiles_m, int64_t tiles_n, DevStatus *status)
 {
