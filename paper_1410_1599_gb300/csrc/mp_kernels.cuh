@@ -340,8 +340,15 @@ MP_DEV void mul_sm(Mp<W> &t, const uint32_t (&am)[W], int64_t ae, uint32_t as, c
     t.e = e;
 }
 
+#ifndef MPG_SM16_BM
+#define MPG_SM16_BM 8
+#endif
+#ifndef MPG_SM16_BK
+#define MPG_SM16_BK 16
+#endif
 template <int W> struct BlockSmCfg {
-    static constexpr int BN = 32, BM = (W == 16) ? 8 : 4, BK = (W == 64) ? 4 : 8, THREADS = BM * BN;
+    static constexpr int BN = 32, BM = (W == 16) ? MPG_SM16_BM : 4;
+    static constexpr int BK = (W == 64) ? 4 : (W == 16 ? MPG_SM16_BK : 8), THREADS = BM * BN;
     static constexpr int RB = W + 4;                 // words per B record
     static constexpr int MIN_CTAS = (W <= 32) ? 3 : 1;   // resident CTAs per SM to plan registers for
     static constexpr size_t smem()
