@@ -123,7 +123,7 @@ __global__ void convert_kernel(BMat X, int px, BMat R, int pr, int64_t rows, int
 // One thread per c_ij; operands read straight from global memory (through
 // the read-only cache), k ascending: c = RN(c + RN(a_ik b_kj)).
 template <int W>
-__global__ void __launch_bounds__(W <= 16 ? 256 : (W == 32 ? 128 : 64), W <= 8 ? 3 : 1)
+__global__ void __launch_bounds__(W <= 16 ? 256 : (W == 32 ? 128 : 64), W <= 16 ? 3 : 1)
 gemm_simple_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p,
                    DevStatus *status)
 {
