@@ -346,11 +346,14 @@ MP_DEV void mul_sm(Mp<W> &t, const uint32_t (&am)[W], int64_t ae, uint32_t as, c
 #ifndef MPG_SM16_BK
 #define MPG_SM16_BK 16
 #endif
+#ifndef MPG_SM16_MINCTAS
+#define MPG_SM16_MINCTAS 3
+#endif
 template <int W> struct BlockSmCfg {
     static constexpr int BN = 32, BM = (W == 16) ? MPG_SM16_BM : 4;
     static constexpr int BK = (W == 64) ? 4 : (W == 16 ? MPG_SM16_BK : 8), THREADS = BM * BN;
     static constexpr int RB = W + 4;                 // words per B record
-    static constexpr int MIN_CTAS = (W <= 32) ? 3 : 1;   // resident CTAs per SM to plan registers for
+    static constexpr int MIN_CTAS = (W == 16) ? MPG_SM16_MINCTAS : ((W <= 32) ? 3 : 1);   // resident CTAs per SM to plan registers for
     static constexpr size_t smem()
     {
         return (size_t)BK * BN * RB * 4 + (size_t)BM * BK * W * 4 + (size_t)(BM * BK + BK * BN) * 9;
