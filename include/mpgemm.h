@@ -274,6 +274,22 @@ int mp_server_drain(mp_server_t *srv);
  * [5] budget, [6] currently running, [7] currently queued. */
 int mp_server_stats(mp_server_t *srv, int64_t out[8]);
 
+/* Graph cache (no counterpart in the paper; a serving facility).  A single
+ * request whose signature (kind, sizes, precision, algorithm, cutoff, LU
+ * panel) has been seen before runs from a CUDA graph captured once over
+ * buffers the server owns; its operands are copied into those buffers, the
+ * graph is launched, the result is copied out.  max_graphs entries at most
+ * (default 8; 0 turns the cache off); entries whose footprint exceeds 1/16 of
+ * the budget are not cached; cached memory counts against the budget and
+ * idle entries are evicted, least recently used first, when a request needs
+ * the room.  Results equal those of the uncached path bit for bit.
+ * Returns MP_OK or MP_ERR_ARG. */
+int mp_server_set_graphs(mp_server_t *srv, int max_graphs);
+
+/* Graph cache counters: [0] graphs captured, [1] requests run from a graph,
+ * [2] entries held now, [3] device bytes held by them. */
+int mp_server_graph_stats(mp_server_t *srv, int64_t out[4]);
+
 /* Drain, stop the scheduler thread and free the server. */
 void mp_server_destroy(mp_server_t *srv);
 

@@ -32,7 +32,8 @@ EXPORTS = ["mp_set_stream", "mp_set_workspace", "mp_set_odd_policy", "mp_set_lu"
            "mplu_workspace_size", "mplu", "mp_sync_status", "mp_singular_column",
            "mp_strerror", "mp_version", "mp_profile_enable", "mp_profile_read",
            "mpgemm_noalloc", "mpgemm_batched", "mp_server_create", "mp_server_submit", "mp_server_cancel",
-           "mp_server_poll", "mp_server_drain", "mp_server_stats", "mp_server_destroy"]
+           "mp_server_poll", "mp_server_drain", "mp_server_stats", "mp_server_set_graphs",
+           "mp_server_graph_stats", "mp_server_destroy"]
 
 REQ_GEMM, REQ_LU_SOLVE = 0, 1
 REQ_DONE, REQ_PENDING, REQ_RUNNING, REQ_CANCELLED, REQ_FAILED = 0, 1, 2, 3, 4
@@ -104,6 +105,8 @@ def load_library(path: str = LIB_PATH):
             lib.mp_server_cancel.argtypes = [C.c_void_p, C.c_int64]
             lib.mp_server_poll.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
             lib.mp_server_drain.argtypes = [C.c_void_p]
+            lib.mp_server_set_graphs.argtypes = [C.c_void_p, C.c_int]
+            lib.mp_server_graph_stats.argtypes = [C.c_void_p, C.c_void_p]
             lib.mp_server_stats.argtypes = [C.c_void_p, C.c_void_p]
             lib.mp_server_destroy.argtypes = [C.c_void_p]
             lib.mp_profile_read.argtypes = [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double),
@@ -354,6 +357,15 @@ class Server:
         keys = ["submitted", "completed", "batches", "batched_requests", "peak_bytes", "budget",
                 "running", "queued"]
         return dict(zip(keys, (int(x) for x in out)))
+
+    def set_graphs(self, max_graphs: int) -> None:
+        """Size of the server's CUDA-graph cache for repeated request shapes (0: off)."""
+        _check(self.lib.mp_server_set_graphs(self.h, max_graphs), "set_graphs")
+
+    def graph_stats(self) -> dict:
+        out = np.zeros(4, np.int64)
+        _check(self.lib.mp_server_graph_stats(self.h, out.ctypes.data_as(C.c_void_p)))
+        return dict(zip(["captured", "replays", "cached", "cached_bytes"], (int(x) for x in out)))
 
     def close(self):
         if self.h:

@@ -9,7 +9,17 @@
 // grouped Block launch; and it retires finished work by polling events.
 // Operands, results and factors stay in device memory from admission to
 // retirement; memory is taken and returned stream-ordered.
+//
+// Repeated request shapes run from captured CUDA graphs: the second time a
+// single request's signature (kind, sizes, precision, algorithm, cutoff,
+// panel) is seen, its device work is captured once into a graph over
+// buffers the cache owns; later requests with that signature copy their
+// operands into those buffers, launch the graph and copy the result out.
+// Cached buffers count against the memory budget and idle entries are
+// evicted (least recently used) when a request needs the room.
 #include <algorithm>
+#include <map>
+#include <tuple>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -52,8 +62,11 @@ struct Req {
     size_t bytes = 0;             // device footprint when run alone
 };
 
+struct GraphEntry;
+
 struct Unit {                     // admitted work on one slot
     std::vector<Req *> reqs;
+    GraphEntry *graph = nullptr;  // cached graph the unit ran from (busy until retired)
     int slot = -1;
     cudaEvent_t done = nullptr;
     size_t bytes = 0;
@@ -64,6 +77,26 @@ struct Finished {
     int64_t id;
     int32_t status;
     double ms;
+};
+
+typedef std::tuple<int32_t, int32_t, int64_t, int64_t, int64_t, int32_t, int32_t, int32_t> Sig;
+
+Sig signature(const mp_request_t &r)
+{
+    const bool lu = r.kind == MP_REQ_LU_SOLVE;
+    return Sig(r.kind, r.prec, r.m, lu ? 0 : r.l, lu ? 0 : r.n, r.algo, r.cutoff,
+               lu ? (r.lu_panel > 0 ? r.lu_panel : 128) : 0);
+}
+
+struct GraphEntry {
+    Sig sig;
+    cudaGraphExec_t exec = nullptr;
+    char *mem = nullptr;
+    size_t bytes = 0;
+    mpmat_t A{}, B{}, C{};        // GEMM: A, B, C; LU solve: A, b, x
+    int64_t *piv = nullptr;
+    bool busy = false;
+    uint64_t last = 0;
 };
 
 bool batchable(const mp_request_t &r, int64_t *bucket)
@@ -91,6 +124,13 @@ struct mp_server {
     bool stop = false;
     int64_t n_submitted = 0, n_completed = 0, n_batches = 0, n_batched_reqs = 0;
     int64_t outstanding = 0;
+    // graph cache (touched by the scheduler thread only; `used` under mu)
+    int graph_slots = 8;
+    std::vector<GraphEntry *> graphs;
+    std::map<Sig, int> seen;
+    uint64_t tick = 0;
+    int64_t n_captures = 0, n_replays = 0;
+    size_t graph_bytes = 0;
 
     // ------------------------------------------------------------- footprint
     static size_t footprint(const mp_request_t &r)
@@ -147,6 +187,143 @@ struct mp_server {
         cudaMemcpyAsync(e, M.exp, n * 8, cudaMemcpyDeviceToHost, st);
         cudaMemcpyAsync(s, M.sign, n, cudaMemcpyDeviceToHost, st);
         return cudaGetLastError() == cudaSuccess ? MP_OK : MP_ERR_CUDA;
+    }
+
+    // ----------------------------------------------------------- graph cache
+    // device buffers of one cached signature: the request's operands and
+    // result (plus the pivot vector of an LU solve)
+    static size_t entry_bytes(const mp_request_t &r)
+    {
+        const int p = r.prec;
+        if (r.kind == MP_REQ_GEMM) return mat_size(p, r.m, r.l) + mat_size(p, r.l, r.n) + mat_size(p, r.m, r.n);
+        return mat_size(p, r.m, r.m) + 2 * mat_size(p, r.m, 1) + align256((size_t)r.m * 8);
+    }
+
+    // release an idle entry (scheduler thread, mu held)
+    void evict_locked(GraphEntry *g)
+    {
+        graphs.erase(std::find(graphs.begin(), graphs.end(), g));
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->mem) cudaFree(g->mem);
+        cudaDeviceGraphMemTrim(device);           // return the graph's pool memory
+        used -= g->bytes;
+        graph_bytes -= g->bytes;
+        delete g;
+    }
+
+    GraphEntry *lru_idle_locked()
+    {
+        GraphEntry *best = nullptr;
+        for (GraphEntry *g : graphs)
+            if (!g->busy && (!best || g->last < best->last)) best = g;
+        return best;
+    }
+
+    // Capture the device work of r over new cache-owned buffers (scheduler
+    // thread, mu not held).  nullptr if capture is not possible.
+    GraphEntry *capture(const mp_request_t &r, cudaStream_t st)
+    {
+        GraphEntry *g = new GraphEntry;
+        g->sig = signature(r);
+        g->bytes = footprint(r);
+        if (cudaMalloc((void **)&g->mem, entry_bytes(r)) != cudaSuccess) {
+            cudaGetLastError();
+            delete g;
+            return nullptr;
+        }
+        const int p = r.prec;
+        mp_set_stream(st);
+        mp_set_workspace(nullptr, 0);
+        mp_set_odd_policy(MP_PEEL);
+        if (r.kind == MP_REQ_GEMM) {
+            mat_on(g->A, p, r.m, r.l, g->mem);
+            mat_on(g->B, p, r.l, r.n, g->mem + mat_size(p, r.m, r.l));
+            mat_on(g->C, p, r.m, r.n, g->mem + mat_size(p, r.m, r.l) + mat_size(p, r.l, r.n));
+        } else {
+            const int64_t n = r.m;
+            const size_t sa = mat_size(p, n, n), sv = mat_size(p, n, 1);
+            mat_on(g->A, p, n, n, g->mem);
+            mat_on(g->B, p, n, 1, g->mem + sa);
+            mat_on(g->C, p, n, 1, g->mem + sa + sv);
+            g->piv = (int64_t *)(g->mem + sa + 2 * sv);
+            mp_set_lu(r.lu_panel > 0 ? r.lu_panel : 128, r.algo, r.cutoff > 0 ? r.cutoff : 64);
+        }
+        cudaGraph_t graph = nullptr;
+        int rc = MP_ERR_CUDA;
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            rc = (r.kind == MP_REQ_GEMM)
+                     ? mpgemm(r.m, r.l, r.n, p, r.algo, r.cutoff, &g->A, &g->B, &g->C)
+                     : mplu(r.m, p, &g->A, g->piv, &g->B, &g->C);
+            if (cudaStreamEndCapture(st, &graph) != cudaSuccess) rc = MP_ERR_CUDA;
+        }
+        if (rc == MP_OK && graph && cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) rc = MP_ERR_CUDA;
+        if (graph) cudaGraphDestroy(graph);
+        if (rc != MP_OK || !g->exec) {
+            cudaGetLastError();
+            cudaFree(g->mem);
+            delete g;
+            return nullptr;
+        }
+        return g;
+    }
+
+    // one request through a cached graph
+    int run_graph(GraphEntry *g, Req *q, cudaStream_t st)
+    {
+        const mp_request_t &r = q->r;
+        int rc = h2d(g->A, r.a_limb, r.a_exp, r.a_sign, st);
+        if (rc == MP_OK) rc = h2d(g->B, r.b_limb, r.b_exp, r.b_sign, st);
+        if (rc == MP_OK && cudaGraphLaunch(g->exec, st) != cudaSuccess) rc = MP_ERR_CUDA;
+        if (rc == MP_OK) rc = d2h(g->C, r.c_limb, r.c_exp, r.c_sign, st);
+        return rc;
+    }
+
+    // Run a single request: from the graph cache when its signature is cached
+    // (or seen before and there is room to capture it), else directly.
+    // Scheduler thread, mu not held; the cache is the scheduler's own.
+    int run_request(Unit *u, cudaStream_t st)
+    {
+        Req *q = u->reqs[0];
+        if (graph_slots <= 0) return run_single(q, st);
+        const Sig sig = signature(q->r);
+        GraphEntry *g = nullptr;
+        for (GraphEntry *e : graphs)
+            if (!e->busy && e->sig == sig) { g = e; break; }
+        if (!g) {
+            int &count = seen[sig];
+            if (count++ == 0) return run_single(q, st);            // first sighting
+            // the cache holds the operand buffers and, in the graph's memory
+            // pool, the captured work's temporaries: the whole footprint
+            const size_t need = footprint(q->r);
+            if (need > budget / 16) return run_single(q, st);      // keep the cache small
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                while ((int)graphs.size() >= graph_slots || used + need > budget) {
+                    GraphEntry *v = lru_idle_locked();
+                    if (!v) break;
+                    evict_locked(v);
+                }
+                if ((int)graphs.size() >= graph_slots || used + need > budget) return run_single(q, st);
+                used += need;                      // reserved for the new entry
+                graph_bytes += need;
+                peak = std::max(peak, used);
+            }
+            g = capture(q->r, st);
+            std::lock_guard<std::mutex> lk(mu);
+            if (!g) {
+                used -= need;
+                graph_bytes -= need;
+            } else {
+                graphs.push_back(g);
+                ++n_captures;
+            }
+            if (!g) return run_single(q, st);
+        }
+        g->busy = true;
+        g->last = ++tick;
+        u->graph = g;
+        ++n_replays;
+        return run_graph(g, q, st);
     }
 
     // one request alone on stream st
@@ -263,6 +440,7 @@ struct mp_server {
                 --outstanding;
             }
             used -= un->bytes;
+            if (un->graph) un->graph->busy = false;
             busy[un->slot] = false;
             cudaEventDestroy(un->done);
             delete un;
@@ -301,6 +479,11 @@ struct mp_server {
                 }
                 return u;
             }
+            while (used + h->bytes > budget) {           // cached graphs give way to requests
+                GraphEntry *v = lru_idle_locked();
+                if (!v) break;
+                evict_locked(v);
+            }
             if (used + h->bytes <= budget) {
                 Unit *u = new Unit;
                 u->slot = slot;
@@ -332,7 +515,7 @@ struct mp_server {
                 if (u->reqs.size() > 1 || u->reqs[0]->bucket > 0)
                     u->rc = run_batch(u->reqs, u->reqs[0]->bucket, st);
                 else
-                    u->rc = run_single(u->reqs[0], st);
+                    u->rc = run_request(u, st);
                 cudaEventCreateWithFlags(&u->done, cudaEventDisableTiming);
                 cudaEventRecord(u->done, st);
                 lk.lock();
@@ -469,6 +652,25 @@ int mp_server_stats(mp_server_t *s, int64_t out[8])
     return MP_OK;
 }
 
+int mp_server_set_graphs(mp_server_t *s, int max_graphs)
+{
+    if (!s || max_graphs < 0 || max_graphs > 1024) return MP_ERR_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->graph_slots = max_graphs;
+    return MP_OK;
+}
+
+int mp_server_graph_stats(mp_server_t *s, int64_t out[4])
+{
+    if (!s || !out) return MP_ERR_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    out[0] = s->n_captures;
+    out[1] = s->n_replays;
+    out[2] = (int64_t)s->graphs.size();
+    out[3] = (int64_t)s->graph_bytes;
+    return MP_OK;
+}
+
 void mp_server_destroy(mp_server_t *s)
 {
     if (!s) return;
@@ -479,6 +681,10 @@ void mp_server_destroy(mp_server_t *s)
     }
     s->cv.notify_all();
     if (s->th.joinable()) s->th.join();
+    while (!s->graphs.empty()) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->evict_locked(s->graphs.back());
+    }
     for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
     delete s;
 }

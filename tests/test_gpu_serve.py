@@ -115,3 +115,41 @@ def test_malformed_and_cancelled():
     assert srv.results[13][0] == mp.REQ_CANCELLED
     assert all(srv.results[i][0] == mp.REQ_DONE for i in (10, 11, 12, 14))
     srv.close()
+
+
+@pytest.mark.parametrize("kind", ["gemm", "lu"])
+def test_graph_cache_replays_bit_exact(kind):
+    """Repeated request shapes run from captured CUDA graphs; every result
+    equals the uncached path's (graph cache off) bit for bit."""
+    p = 256
+    reqs = []
+    for i in range(5):
+        if kind == "gemm":
+            A = gen.uniform_pm1(70, 90, p, 5100 + i, -16, 16)
+            B = gen.uniform_pm1(90, 66, p, 5200 + i, -16, 16)
+            reqs.append(("gemm", i, A, B, mp.WINOGRAD))
+        else:
+            A = gen.well_conditioned(48, p, 5300 + i)
+            b = gen.uniform_pm1(48, 1, p, 5400 + i)
+            reqs.append(("lu", i, A, b, mp.SIMPLE))
+    outs = {}
+    for graphs in (0, 8):
+        srv = mp.Server(budget_bytes=8 << 30, slots=2)
+        srv.set_graphs(graphs)
+        for r in reqs:
+            assert _submit(srv, r) == 0
+            if graphs == 0:
+                srv.drain()
+        srv.drain()
+        gs = srv.graph_stats()
+        for r in reqs:
+            st, ms, out = srv.results[r[1]]
+            assert st == mp.REQ_DONE
+            outs.setdefault(r[1], []).append(out)
+        srv.close()
+        if graphs == 0:
+            assert gs["captured"] == 0 and gs["replays"] == 0
+        else:
+            assert gs["captured"] >= 1 and gs["replays"] >= 3
+    for rid, (plain, cached) in outs.items():
+        assert_bits_equal(cached, plain, "request %d from the graph cache" % rid)
