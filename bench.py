@@ -295,6 +295,7 @@ def run_ours(a, rank, world, local):
     mp.check_status("e2e")
 
     extras, extras_lu, serving, by_prec, split_small, other_configs = {}, None, None, {}, None, None
+    serving_repeat = None
     if not a.no_extras and rank == 0:
         for name in ("simple", "block", "strassen", "winograd"):
             if name == a.algo:
@@ -348,6 +349,8 @@ def run_ours(a, rank, world, local):
         mp.set_stream(stream)
         serving = serve_run(a.serve_requests)
         mp.set_stream(stream)
+        serving_repeat = serve_repeat_run()
+        mp.set_stream(stream)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_extras:
@@ -388,6 +391,8 @@ def run_ours(a, rank, world, local):
             line["configs"] = other_configs
         if serving:
             line["serving"] = serving
+        if serving_repeat:
+            line["serving_repeated_shapes"] = serving_repeat
         print(json.dumps(line), flush=True)
     rep.close()
 
@@ -661,6 +666,75 @@ def serve_run(n_req, seed=11, slots=8, budget=150 << 30):
             "peak_gb": round(max(st1["peak_bytes"], st2["peak_bytes"]) / 2 ** 30, 3)}
 
 
+def serve_repeat_run(n_req=96, seed=12, slots=8, budget=150 << 30):
+    """Requests drawn from eight fixed shapes (four GEMMs, four LU solves,
+    256 and 512 bits), each with its own data, through the serving loop with
+    the CUDA-graph cache off and on: closed-loop capacity, then Poisson
+    arrivals at 0.7 x the cache-off capacity, p50 / p99 latency."""
+    import numpy as np
+
+    from paper_1410_1599_gb300 import binding as mp
+    from paper_1410_1599_gb300 import inputs as gen
+
+    rng = np.random.default_rng(seed)
+    shapes = [("gemm", 256, (96, 96, 96), mp.BLOCK), ("gemm", 512, (200, 160, 180), mp.WINOGRAD),
+              ("gemm", 256, (384, 384, 384), mp.WINOGRAD), ("gemm", 512, (64, 512, 64), mp.BLOCK),
+              ("lu", 256, (128,), mp.SIMPLE), ("lu", 512, (96,), mp.SIMPLE),
+              ("lu", 256, (320,), mp.WINOGRAD), ("lu", 512, (200,), mp.SIMPLE)]
+    picks = rng.integers(0, len(shapes), n_req)
+    inputs = []
+    for i, k in enumerate(picks):
+        kind, p, dims, algo = shapes[k]
+        if kind == "gemm":
+            m, l, n = dims
+            inputs.append((kind, p, algo, gen.uniform_pm1(m, l, p, 9000 + i, -16, 16),
+                           gen.uniform_pm1(l, n, p, 19000 + i, -16, 16)))
+        else:
+            n = dims[0]
+            inputs.append((kind, p, algo, gen.well_conditioned(n, p, 29000 + i), gen.uniform_pm1(n, 1, p, 39000 + i)))
+
+    def submit(srv, i):
+        kind, p, algo, X, Y = inputs[i]
+        if kind == "gemm":
+            return srv.submit_gemm(i, X, Y, algo=algo, cutoff=64)
+        return srv.submit_lu(i, X, Y, algo=algo, cutoff=64, panel=128)
+
+    res = {}
+    lam = None
+    for graphs in (0, 8):
+        srv = mp.Server(budget_bytes=budget, slots=slots)
+        srv.set_graphs(graphs)
+        t0 = time.perf_counter()
+        for i in range(n_req):
+            assert submit(srv, i) == 0
+        srv.drain()
+        cap = n_req / (time.perf_counter() - t0)
+        g1 = srv.graph_stats()
+        srv.close()
+        if lam is None:
+            lam = 0.7 * cap
+        gaps = np.random.default_rng(seed + 1).exponential(1.0 / lam, n_req)
+        srv = mp.Server(budget_bytes=budget, slots=slots)
+        srv.set_graphs(graphs)
+        t0 = time.perf_counter()
+        due = t0
+        for i, g in enumerate(gaps):
+            due += g
+            while time.perf_counter() < due:
+                time.sleep(min(0.002, max(0.0, due - time.perf_counter())))
+            assert submit(srv, i) == 0
+        srv.drain()
+        lat = np.array([srv.results[i][1] for i in range(n_req)])
+        ok = all(srv.results[i][0] == mp.REQ_DONE for i in range(n_req))
+        g2 = srv.graph_stats()
+        srv.close()
+        res["graphs_%s" % ("on" if graphs else "off")] = {
+            "all_done": ok, "capacity_req_per_s": round(cap, 2), "p50_ms": round(float(np.percentile(lat, 50)), 2),
+            "p99_ms": round(float(np.percentile(lat, 99)), 2),
+            "graph_replays": g1["replays"] + g2["replays"], "graphs_captured": g1["captured"] + g2["captured"]}
+    return {"requests": n_req, "shapes": len(shapes), "offered_req_per_s": round(lam, 2), **res}
+
+
 def split_run(n=4096, p=1024, with_simple=True):
     """Split form vs the exact limb path (same correctly rounded result) on
     n^3 at p bits, entries U[-1,1)*2^e, e ~ U{-16..16}."""
@@ -801,7 +875,8 @@ def main():
         from paper_1410_1599_gb300 import build as libbuild
         libbuild.build()
         torch.cuda.set_device(local)
-        print(json.dumps({"serving": serve_run(a.serve_requests)}), flush=True)
+        print(json.dumps({"serving": serve_run(a.serve_requests),
+                          "serving_repeated_shapes": serve_repeat_run()}), flush=True)
         return
     if a.configs:
         import torch

@@ -288,7 +288,8 @@ struct mp_server {
         const Sig sig = signature(q->r);
         GraphEntry *g = nullptr;
         for (GraphEntry *e : graphs)
-            if (!e->busy && e->sig == sig) { g = e; break; }
+            if (e->sig == sig) { g = e; break; }
+        if (g && g->busy) return run_single(q, st);     // one entry per signature
         if (!g) {
             int &count = seen[sig];
             if (count++ == 0) return run_single(q, st);            // first sighting
