@@ -24,6 +24,35 @@ struct ThreadState {
 };
 thread_local ThreadState g_ts;
 
+// A second stream per thread and device for work that can overlap the main
+// stream's (the peeled border products of the recursion), with the events
+// that fork it from and join it back to the main stream.  Created on first
+// use and kept for the thread's lifetime.
+struct SideStream {
+    int device = -1;
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+thread_local std::vector<SideStream> g_side;
+
+SideStream *side_stream()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    for (SideStream &x : g_side)
+        if (x.device == dev) return &x;
+    SideStream x;
+    x.device = dev;
+    if (cudaStreamCreateWithFlags(&x.s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&x.join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    g_side.push_back(x);
+    return &g_side.back();
+}
+
 std::mutex g_status_mu;
 std::vector<DevStatus *> g_status;   // one per device
 
@@ -320,12 +349,37 @@ int run_recursion(int algo, const std::vector<LevelDims> &lv, int p, BMat A0, BM
         }
         nodes *= 7;
     }
+    // peeled borders (last row / column of a node with odd m / n, Simple over
+    // its whole l): they need only the node's operands, so they run on a
+    // second stream, overlapping the leaves, and join before the combinations
+    bool any_border = false;
+    for (int k = 0; k < D; ++k)
+        if (lv[k].M < lv[k].m || lv[k].N < lv[k].n) any_border = true;
+    SideStream *ss = any_border ? side_stream() : nullptr;
+    const cudaStream_t bs = ss ? ss->s : s;
+    if (ss) {
+        cudaEventRecord(ss->fork, s);
+        cudaStreamWaitEvent(bs, ss->fork, 0);
+    }
+    if (any_border) {
+        int64_t nk = 1;
+        for (int k = 0; k < D; ++k, nk *= 7) {
+            const LevelDims &d = lv[k];
+            if (!(d.M < d.m || d.N < d.n)) continue;
+            const int64_t mr = std::min(d.M, d.m);
+            const int64_t cnt = (d.M < d.m ? d.n : 0) + (d.N < d.n ? mr : 0);
+            Prof pr(MP_K_FIXUP, (double)nk * cnt * d.l, bs);
+            launch_border<W>(A[k], B[k], C[k], nk, d.m, d.l, d.n, mr, d.M < d.m, d.N < d.n, p, st, bs);
+        }
+    }
+    if (ss) cudaEventRecord(ss->join, bs);
     // leaves: one grouped Block GEMM over all 7^D products
     {
         Prof pr(MP_K_LEAF, (double)nodes * lv[D].m * lv[D].l * lv[D].n, s);
         launch_gemm_block<W>(A[D], B[D], C[D], nodes, lv[D].m, lv[D].l, lv[D].n, p, st, s);
     }
-    // up: combinations, then the peel fix-ups of each level
+    if (ss) cudaStreamWaitEvent(s, ss->join, 0);
+    // up: combinations, then the rank-1 fix-up of an odd l
     for (int k = D - 1; k >= 0; --k) {
         nodes /= 7;
         const LevelDims &d = lv[k];
@@ -337,12 +391,6 @@ int run_recursion(int algo, const std::vector<LevelDims> &lv, int p, BMat A0, BM
         if (d.K < d.l) {
             Prof pr(MP_K_FIXUP, (double)nodes * mr * nr, s);
             launch_rank1<W>(A[k], B[k], C[k], nodes, mr, nr, d.l, p, st, s);
-        }
-        if (d.M < d.m || d.N < d.n) {
-            const int64_t cnt = (d.M < d.m ? d.n : 0) + (d.N < d.n ? mr : 0);
-            Prof pr(MP_K_FIXUP, (double)nodes * cnt * d.l, s);
-            launch_border<W>(A[k], B[k], C[k], nodes, d.m, d.l, d.n, mr, d.M < d.m, d.N < d.n, p,
-                             st, s);
         }
     }
     return launch_status();
