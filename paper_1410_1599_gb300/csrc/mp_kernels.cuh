@@ -349,11 +349,17 @@ MP_DEV void mul_sm(Mp<W> &t, const uint32_t (&am)[W], int64_t ae, uint32_t as, c
 #ifndef MPG_SM16_MINCTAS
 #define MPG_SM16_MINCTAS 3
 #endif
+#ifndef MPG_SM8_MINCTAS
+#define MPG_SM8_MINCTAS 4
+#endif
+#ifndef MPG_SM_MIN_W
+#define MPG_SM_MIN_W 8           // narrowest class on the shared-memory leaf
+#endif
 template <int W> struct BlockSmCfg {
-    static constexpr int BN = 32, BM = (W == 16) ? MPG_SM16_BM : 4;
-    static constexpr int BK = (W == 64) ? 4 : (W == 16 ? MPG_SM16_BK : 8), THREADS = BM * BN;
+    static constexpr int BN = 32, BM = (W <= 16) ? MPG_SM16_BM : 4;
+    static constexpr int BK = (W == 64) ? 4 : (W <= 16 ? MPG_SM16_BK : 8), THREADS = BM * BN;
     static constexpr int RB = W + 4;                 // words per B record
-    static constexpr int MIN_CTAS = (W == 16) ? MPG_SM16_MINCTAS : ((W <= 32) ? 3 : 1);   // resident CTAs per SM to plan registers for
+    static constexpr int MIN_CTAS = (W == 8) ? MPG_SM8_MINCTAS : (W == 16) ? MPG_SM16_MINCTAS : ((W <= 32) ? 3 : 1);   // resident CTAs per SM to plan registers for
     static constexpr size_t smem()
     {
         return (size_t)BK * BN * RB * 4 + (size_t)BM * BK * W * 4 + (size_t)(BM * BK + BK * BN) * 9;
@@ -366,7 +372,7 @@ gemm_block_sm_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, in
                      int64_t tiles_m, int64_t tiles_n, DevStatus *status)
 {
     using Cfg = BlockSmCfg<W>;
-    static_assert(W == 16 || W == 32 || W == 64, "wide leaf");
+    static_assert(W == 8 || W == 16 || W == 32 || W == 64, "leaf class");
     constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK, RB = Cfg::RB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const RoundSpec rs = make_spec<W>(p);
@@ -707,7 +713,7 @@ void launch_gemm_block(BMat A, BMat B, BMat C, int64_t batch, int64_t m, int64_t
 {
     using Cfg = BlockCfg<W>;
     if (batch <= 0 || m <= 0 || n <= 0) return;
-    if constexpr (W >= 16) {
+    if constexpr (W >= MPG_SM_MIN_W) {
         using C64 = BlockSmCfg<W>;
         const int64_t tm = (m + C64::BM - 1) / C64::BM, tn = (n + C64::BN - 1) / C64::BN;
         static bool attr64 = false;
