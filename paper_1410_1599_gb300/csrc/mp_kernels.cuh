@@ -145,111 +145,14 @@ gemm_simple_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int 
 // ---------------------------------------------------- Block (Eq. 2), batched
 // C_b = A_b B_b for a batch of equally shaped products (the leaves of the
 // Strassen/Winograd recursion, or one plain product).  Each CTA owns a
-// BM x BN tile of C (one element per thread) and walks k in slabs of BK:
-// the A and B slabs are staged in shared memory as limb planes, and every
-// c_ij still accumulates in k-ascending order, so the bits equal Simple's.
-template <int W> struct BlockCfg {
-    static constexpr int BN = 32;
-    static constexpr int BM = (W <= 16) ? 8 : (W == 32 ? 4 : 2);
-    static constexpr int BK = (W <= 8) ? 16 : 8;
-    static constexpr int THREADS = BM * BN;
-    static constexpr size_t smem(int L)
-    {
-        return (size_t)(BM * BK + BK * BN) * (size_t)(8 * L + 9);
-    }
-};
-
-template <int W>
-__global__ void __launch_bounds__(BlockCfg<W>::THREADS)
-gemm_block_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p,
-                  int64_t tiles_m, int64_t tiles_n, DevStatus *status)
-{
-    using Cfg = BlockCfg<W>;
-    constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const RoundSpec rs = make_spec<W>(p);
-    const int L = rs.L;
-    // shared layout: A limbs [L][BM][BK], B limbs [L][BK][BN], A exp, B exp, A sign, B sign
-    uint64_t *sAl = reinterpret_cast<uint64_t *>(smem_raw);
-    uint64_t *sBl = sAl + (size_t)L * BM * BK;
-    int64_t *sAe = reinterpret_cast<int64_t *>(sBl + (size_t)L * BK * BN);
-    int64_t *sBe = sAe + BM * BK;
-    int8_t *sAs = reinterpret_cast<int8_t *>(sBe + BK * BN);
-    int8_t *sBs = sAs + BM * BK;
-
-    const int64_t tile = blockIdx.x;
-    const int64_t b = tile / (tiles_m * tiles_n);
-    const int64_t tm = (tile / tiles_n) % tiles_m, tn = tile % tiles_n;
-    const int tx = threadIdx.x % BN, ty = threadIdx.x / BN;
-    const int64_t i = tm * BM + ty, j = tn * BN + tx;
-    const bool valid = (i < m) && (j < n);
-
-    Mp<W> c, a, bb, t;
-    set_zero<W>(c, 0u);
-    for (int64_t k0 = 0; k0 < l; k0 += BK) {
-        const int kc = (int)((l - k0) < BK ? (l - k0) : BK);
-        // stage the A slab (BM x kc) and the B slab (kc x BN)
-        for (int e = threadIdx.x; e < L * BM * BK; e += blockDim.x) {
-            const int kk = e % BK, rr = (e / BK) % BM, limb = e / (BK * BM);
-            const int64_t gi = tm * BM + rr, gk = k0 + kk;
-            sAl[e] = (gi < m && kk < kc)
-                         ? __ldg(A.limb + b * A.bs_limb + (int64_t)limb * A.plane + gi * A.ld + gk)
-                         : 0ull;
-        }
-        for (int e = threadIdx.x; e < L * BK * BN; e += blockDim.x) {
-            const int cc = e % BN, kk = (e / BN) % BK, limb = e / (BN * BK);
-            const int64_t gj = tn * BN + cc, gk = k0 + kk;
-            sBl[e] = (gj < n && kk < kc)
-                         ? __ldg(B.limb + b * B.bs_limb + (int64_t)limb * B.plane + gk * B.ld + gj)
-                         : 0ull;
-        }
-        for (int e = threadIdx.x; e < BM * BK; e += blockDim.x) {
-            const int kk = e % BK, rr = e / BK;
-            const int64_t gi = tm * BM + rr, gk = k0 + kk;
-            const bool ok = gi < m && kk < kc;
-            sAe[e] = ok ? __ldg(A.exp + b * A.bs_es + gi * A.ld + gk) : EXP_ZERO;
-            sAs[e] = ok ? __ldg(A.sign + b * A.bs_es + gi * A.ld + gk) : (int8_t)0;
-        }
-        for (int e = threadIdx.x; e < BK * BN; e += blockDim.x) {
-            const int cc = e % BN, kk = e / BN;
-            const int64_t gj = tn * BN + cc, gk = k0 + kk;
-            const bool ok = gj < n && kk < kc;
-            sBe[e] = ok ? __ldg(B.exp + b * B.bs_es + gk * B.ld + gj) : EXP_ZERO;
-            sBs[e] = ok ? __ldg(B.sign + b * B.bs_es + gk * B.ld + gj) : (int8_t)0;
-        }
-        __syncthreads();
-        if (valid) {
-            for (int kk = 0; kk < kc; ++kk) {
-#pragma unroll
-                for (int q = 0; q < W / 2; ++q) {
-                    const uint64_t va = (q < L) ? sAl[((size_t)q * BM + ty) * BK + kk] : 0ull;
-                    const uint64_t vb = (q < L) ? sBl[((size_t)q * BK + kk) * BN + tx] : 0ull;
-                    a.m[W - 1 - 2 * q] = (uint32_t)(va >> 32);
-                    a.m[W - 2 - 2 * q] = (uint32_t)va;
-                    bb.m[W - 1 - 2 * q] = (uint32_t)(vb >> 32);
-                    bb.m[W - 2 - 2 * q] = (uint32_t)vb;
-                }
-                a.e = sAe[ty * BK + kk];
-                a.s = (uint32_t)(sAs[ty * BK + kk] & 1);
-                bb.e = sBe[kk * BN + tx];
-                bb.s = (uint32_t)(sBs[kk * BN + tx] & 1);
-                mul<W, true>(t, a, bb, rs);
-                add<W, true>(c, c, t, 0u, rs);
-            }
-        }
-        __syncthreads();
-    }
-    if (valid && st<W>(c, C, b, i, j, L)) flag(status, ST_RANGE);
-}
-
-// ------------------------------------------ Block leaf for 2048-bit numbers
-// At W = 64 three register-resident operands do not fit in a thread's 255
-// registers.  Here each thread keeps c and a_ik in registers and reads b_kj
-// word by word from shared memory (four words per 16-byte load) while it
-// forms the product, so nothing goes through local memory.  The slab of B
-// is stored one element per BW-word record (mantissa words little-endian,
-// padded from 64 to 68 words: a warp's 16-byte loads then hit every bank
-// once).  Values and summation order are those of gemm_block_kernel.
+// BM x 32 tile of C (one element per thread) and walks k in slabs of BK; every
+// c_ij accumulates in k-ascending order, so the bits equal Simple's.
+// Each thread keeps c and a_ik in registers and reads b_kj word by word from
+// shared memory (four words per 16-byte load) while it forms the product:
+// three register operands would cost resident CTAs at every precision and do
+// not fit at all at 2048 bits.  The slabs are stored one element per record
+// (mantissa words little-endian; B records padded so that a warp's 16-byte
+// loads hit every bank once).
 
 // top words of the truncated product a * b, b read from shared memory:
 // acc[q] = word W-2+q of sum_{i+j >= W-2} a_i b_j 2^(32(i+j))
@@ -352,14 +255,15 @@ MP_DEV void mul_sm(Mp<W> &t, const uint32_t (&am)[W], int64_t ae, uint32_t as, c
 #ifndef MPG_SM8_MINCTAS
 #define MPG_SM8_MINCTAS 4
 #endif
-#ifndef MPG_SM_MIN_W
-#define MPG_SM_MIN_W 8           // narrowest class on the shared-memory leaf
+#ifndef MPG_SM4_MINCTAS
+#define MPG_SM4_MINCTAS 6
 #endif
 template <int W> struct BlockSmCfg {
     static constexpr int BN = 32, BM = (W <= 16) ? MPG_SM16_BM : 4;
     static constexpr int BK = (W == 64) ? 4 : (W <= 16 ? MPG_SM16_BK : 8), THREADS = BM * BN;
-    static constexpr int RB = W + 4;                 // words per B record
-    static constexpr int MIN_CTAS = (W == 8) ? MPG_SM8_MINCTAS : (W == 16) ? MPG_SM16_MINCTAS : ((W <= 32) ? 3 : 1);   // resident CTAs per SM to plan registers for
+    static constexpr int RB = (W == 4) ? 12 : W + 4;  // words per B record (bank-conflict-free 16-byte loads)
+    static constexpr int MIN_CTAS = (W == 4) ? MPG_SM4_MINCTAS : (W == 8) ? MPG_SM8_MINCTAS
+                                  : (W == 16) ? MPG_SM16_MINCTAS : ((W <= 32) ? 3 : 1);   // resident CTAs per SM to plan registers for
     static constexpr size_t smem()
     {
         return (size_t)BK * BN * RB * 4 + (size_t)BM * BK * W * 4 + (size_t)(BM * BK + BK * BN) * 9;
@@ -372,7 +276,7 @@ gemm_block_sm_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, in
                      int64_t tiles_m, int64_t tiles_n, DevStatus *status)
 {
     using Cfg = BlockSmCfg<W>;
-    static_assert(W == 8 || W == 16 || W == 32 || W == 64, "leaf class");
+    static_assert(W == 4 || W == 8 || W == 16 || W == 32 || W == 64, "leaf class");
     constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK, RB = Cfg::RB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const RoundSpec rs = make_spec<W>(p);
@@ -711,32 +615,17 @@ template <int W>
 void launch_gemm_block(BMat A, BMat B, BMat C, int64_t batch, int64_t m, int64_t l, int64_t n,
                        int p, DevStatus *st, cudaStream_t s)
 {
-    using Cfg = BlockCfg<W>;
     if (batch <= 0 || m <= 0 || n <= 0) return;
-    if constexpr (W >= MPG_SM_MIN_W) {
-        using C64 = BlockSmCfg<W>;
-        const int64_t tm = (m + C64::BM - 1) / C64::BM, tn = (n + C64::BN - 1) / C64::BN;
-        static bool attr64 = false;
-        if (!attr64) {
-            cudaFuncSetAttribute(gemm_block_sm_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)C64::smem());
-            attr64 = true;
-        }
-        gemm_block_sm_kernel<W><<<(unsigned)(batch * tm * tn), C64::THREADS, C64::smem(), s>>>(
-            A, B, C, m, l, n, p, tm, tn, st);
-    } else {
-        const int L = (p + 63) >> 6;
-        const int64_t tm = (m + Cfg::BM - 1) / Cfg::BM, tn = (n + Cfg::BN - 1) / Cfg::BN;
-        const size_t sm = Cfg::smem(L);
-        static bool attr_set = false;
-        if (!attr_set) {
-            cudaFuncSetAttribute(gemm_block_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)Cfg::smem(W / 2));
-            attr_set = true;
-        }
-        gemm_block_kernel<W><<<(unsigned)(batch * tm * tn), Cfg::THREADS, sm, s>>>(
-            A, B, C, m, l, n, p, tm, tn, st);
+    using Cfg = BlockSmCfg<W>;
+    const int64_t tm = (m + Cfg::BM - 1) / Cfg::BM, tn = (n + Cfg::BN - 1) / Cfg::BN;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(gemm_block_sm_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Cfg::smem());
+        attr = true;
     }
+    gemm_block_sm_kernel<W><<<(unsigned)(batch * tm * tn), Cfg::THREADS, Cfg::smem(), s>>>(
+        A, B, C, m, l, n, p, tm, tn, st);
 }
 
 template <int W>
