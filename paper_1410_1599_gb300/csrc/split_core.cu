@@ -40,6 +40,15 @@ int64_t split_row_pad(int64_t l) { return split_lpad(l); }
 namespace {
 
 constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+// cluster geometry: CR row tiles share one B tile, CC column tiles one A tile
+#ifndef MPG_SPLIT_CR
+#define MPG_SPLIT_CR 1
+#endif
+#ifndef MPG_SPLIT_CC
+#define MPG_SPLIT_CC 2
+#endif
+constexpr int CR = MPG_SPLIT_CR, CC = MPG_SPLIT_CC, CSIZE = CR * CC;
+static_assert(CSIZE <= 8 && BM % CC == 0 && BN % CR == 0, "cluster geometry");
 constexpr int KB_PER_CHUNK = SPLIT_CHUNK / BK;                 // 8
 constexpr int CHUNKS_PER_I32 = 255;
 constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
@@ -52,7 +61,7 @@ constexpr long long WAIT_LIMIT = 4000000000ll;                  // ~2 s of clock
 
 struct Sched {
     int S, groups, nkb;
-    int64_t m, n, tiles_n2;     // tiles_n2: pairs of 256-column tiles
+    int64_t m, n, tiles_n2;     // tiles_n2: groups of CC 256-column tiles
     int64_t nitems;             // (2 x 2 tile block, diagonal group) work items
 };
 
@@ -96,20 +105,21 @@ split_slice_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_co
     __shared__ volatile int abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t rank = tc::cluster_rank();                   // r * 2 + c
-    const uint32_t cr = rank >> 1, cc = rank & 1u;
-    const uint16_t mask_a = (uint16_t)(3u << (2 * cr));         // CTAs sharing this A tile
-    const uint16_t mask_b = (uint16_t)((1u << cc) | (4u << cc)); // CTAs sharing this B tile
-    // persistent clusters: work items (2 x 2 tile block, diagonal group) are
+    const uint32_t rank = tc::cluster_rank();                   // cr * CC + cc
+    const uint32_t cr = rank / CC, cc = rank % CC;
+    const uint16_t mask_a = (uint16_t)(((1u << CC) - 1u) << (cr * CC));   // CTAs sharing this A tile
+    uint16_t mask_b = 0;                                                  // CTAs sharing this B tile
+    for (int r = 0; r < CR; ++r) mask_b |= (uint16_t)(1u << (r * CC + cc));
+    // persistent clusters: work items (CR x CC tile block, diagonal group) are
     // taken round-robin; every role walks the same sequence
-    const int64_t cl0 = blockIdx.x >> 2, ncl = gridDim.x >> 2;
+    const int64_t cl0 = blockIdx.x / CSIZE, ncl = gridDim.x / CSIZE;
     // (quads vary fastest: clusters running at the same time walk the same
     // diagonals on neighbouring blocks and share operand tiles through L2)
     auto item = [&](int64_t it, int64_t &i0, int64_t &j0) -> int {
         const int64_t quads = sc.nitems / sc.groups;
         const int64_t quad = it % quads;
-        i0 = (2 * (quad / sc.tiles_n2) + cr) * BM;
-        j0 = (2 * (quad % sc.tiles_n2) + cc) * BN;
+        i0 = (CR * (quad / sc.tiles_n2) + cr) * BM;
+        j0 = (CC * (quad % sc.tiles_n2) + cc) * BN;
         return (int)(it / quads);
     };
     const int S = sc.S, nkb = sc.nkb;
@@ -117,7 +127,7 @@ split_slice_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_co
     if (threadIdx.x == 0) {
         for (int st = 0; st < STAGES; ++st) {
             tc::mbar_init(&full_bar[st], 1);
-            tc::mbar_init(&empty_bar[st], 3);          // this CTA and both peers consumed it
+            tc::mbar_init(&empty_bar[st], CR + CC - 1); // this CTA and its peers consumed it
         }
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(&accf_bar[b], 1);
@@ -157,10 +167,10 @@ split_slice_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_co
                     const int u = u0 + t / nkb, kb = t % nkb;
                     uint8_t *sa = ring + st * STAGE_BYTES, *sb = sa + A_BYTES;
                     tc::mbar_expect_tx(&full_bar[st], STAGE_BYTES);
-                    tc::tma_load_2d_mc(sa + cc * (A_BYTES / 2), &map_a, kb * BK,
-                                       (int32_t)(u * sc.m + i0 + cc * (BM / 2)), &full_bar[st], mask_a);
-                    tc::tma_load_2d_mc(sb + cr * (B_BYTES / 2), &map_b, kb * BK,
-                                       (int32_t)((s - u) * sc.n + j0 + cr * (BN / 2)), &full_bar[st], mask_b);
+                    tc::tma_load_2d_mc(sa + cc * (A_BYTES / CC), &map_a, kb * BK,
+                                       (int32_t)(u * sc.m + i0 + cc * (BM / CC)), &full_bar[st], mask_a);
+                    tc::tma_load_2d_mc(sb + cr * (B_BYTES / CR), &map_b, kb * BK,
+                                       (int32_t)((s - u) * sc.n + j0 + cr * (BN / CR)), &full_bar[st], mask_b);
                 }
             }
             }
@@ -212,7 +222,7 @@ split_slice_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_co
                     for (int k = 0; k < BK / 16; ++k)
                         tc::mma_f16(d, tc::desc_k128(sa + 32 * k), tc::desc_k128(sb + 32 * k), idesc,
                                     (first && k == 0) ? 0u : 1u);
-                    tc::mma_commit_mc(&empty_bar[st], mask_a | mask_b);   // self and both peers
+                    tc::mma_commit_mc(&empty_bar[st], mask_a | mask_b);   // self and its peers
                     if (last) {
                         tc::mma_commit(&accf_bar[buf]);             // the chunk is complete
                         ++c;
@@ -327,7 +337,7 @@ int launch_split_slices(const __half *pa, const __half *pb, int64_t m, int64_t l
     if (((uintptr_t)pa & 15) || ((uintptr_t)pb & 15) || (lp * 2) % 16) return MP_ERR_ARG;
     if ((int64_t)S * m > 0x7fffffff || (int64_t)S * n > 0x7fffffff) return MP_ERR_ARG;
     CUtensorMap ma, mb;
-    if (!make_map(&ma, pa, (int64_t)S * m, lp, BM / 2) || !make_map(&mb, pb, (int64_t)S * n, lp, BN / 2)) {
+    if (!make_map(&ma, pa, (int64_t)S * m, lp, BM / CC) || !make_map(&mb, pb, (int64_t)S * n, lp, BN / CR)) {
         if (std::getenv("MPGEMM_DEBUG")) std::fprintf(stderr, "split: tensor map encoding failed\n");
         return MP_ERR_UNSUPPORTED;
     }
@@ -347,9 +357,9 @@ int launch_split_slices(const __half *pa, const __half *pb, int64_t m, int64_t l
     sc.nkb = (int)((lp + BK - 1) / BK);
     sc.m = m;
     sc.n = n;
-    sc.tiles_n2 = (n + 2 * BN - 1) / (2 * BN);
-    const int64_t quads = ((m + 2 * BM - 1) / (2 * BM)) * sc.tiles_n2;   // 2 x 2 tile blocks
-    // One resident cluster of four per four SMs (as many as fit at once); the
+    sc.tiles_n2 = (n + CC * BN - 1) / (CC * BN);
+    const int64_t quads = ((m + CR * BM - 1) / (CR * BM)) * sc.tiles_n2;   // CR x CC tile blocks
+    // One resident cluster of CSIZE CTAs per CSIZE SMs (as many as fit at once); the
     // diagonals of a block are spread over groups until there are about
     // eight work items per cluster, so that the round-robin leaves little
     // imbalance at the end.
@@ -359,17 +369,17 @@ int launch_split_slices(const __half *pa, const __half *pb, int64_t m, int64_t l
     cfg.stream = s;
     cudaLaunchAttribute attr_cl[1];
     attr_cl[0].id = cudaLaunchAttributeClusterDimension;
-    attr_cl[0].val.clusterDim.x = 4;
+    attr_cl[0].val.clusterDim.x = CSIZE;
     attr_cl[0].val.clusterDim.y = 1;
     attr_cl[0].val.clusterDim.z = 1;
     cfg.attrs = attr_cl;
     cfg.numAttrs = 1;
     static int resident = 0;
     if (resident <= 0) {
-        cfg.gridDim = dim3(4 * 38);
+        cfg.gridDim = dim3(CSIZE * (152 / CSIZE));
         if (cudaOccupancyMaxActiveClusters(&resident, split_slice_tc_kernel, &cfg) != cudaSuccess || resident <= 0) {
             (void)cudaGetLastError();                   // clear a failed query
-            resident = 36;
+            resident = 144 / CSIZE;
         }
     }
     const int64_t clusters = resident;
@@ -378,7 +388,7 @@ int launch_split_slices(const __half *pa, const __half *pb, int64_t m, int64_t l
     sc.groups = groups;
     sc.nitems = quads * groups;
     const int64_t ncl = sc.nitems < clusters ? sc.nitems : clusters;
-    cfg.gridDim = dim3((unsigned)(4 * ncl));
+    cfg.gridDim = dim3((unsigned)(CSIZE * ncl));
     cudaLaunchKernelEx(&cfg, split_slice_tc_kernel, ma, mb, sc, D, st);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess && std::getenv("MPGEMM_DEBUG"))
