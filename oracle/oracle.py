@@ -8,7 +8,9 @@ returned as OMat objects with the same attributes.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
+from fractions import Fraction
 
 import numpy as np
 
@@ -212,14 +214,16 @@ def dot_exact(A, B, rows=None, cols=None, p_out: int | None = None):
     return OMat(*kc, p_out)
 
 
-def lu(A, panel: int = 128, algo: int = SIMPLE, cutoff: int = 64, policy: int = PEEL):
-    """Returns (LU factors, piv, status); status 0 ok, k+1 for a zero pivot in column k."""
+def lu(A, panel: int = 128, algo: int = SIMPLE, cutoff: int = 64, policy: int = PEEL,
+       pivoting: bool = True):
+    """Returns (LU factors, piv, status); status 0 ok, k+1 for a zero pivot in
+    column k.  pivoting=False is the paper's LU (Sec. 4), piv[k] = k."""
     n = A.exp.shape[0]
     M = OMat(A.limb.copy(), A.exp.copy(), A.sign.copy(), A.p)
     piv = np.zeros(n, np.int64)
     km, am = _mat_args(M)
     rc = lib().orc_api_lu(C.c_int64(n), C.c_int(A.p), C.c_int(panel), C.c_int(algo),
-                          C.c_int(cutoff), C.c_int(policy), *am, _p(piv))
+                          C.c_int(cutoff), C.c_int(policy), C.c_int(1 if pivoting else 0), *am, _p(piv))
     return OMat(*km, A.p), piv, rc
 
 
@@ -234,3 +238,78 @@ def lu_solve(LU, piv, b):
     if rc:
         raise ValueError("oracle solve failed: %d" % rc)
     return OMat(*kx, LU.p)
+
+
+# ---------------------------------------------------------------------------
+# Section 4 benchmark matrices: a_ij = sqrt(5) (i + j - 1), b_ij = sqrt(3) (n - i + 1)
+# ---------------------------------------------------------------------------
+def sqrt_product_S(m: int, l: int, n: int) -> list:
+    """The exact product of the Section 4 matrices is c_ij = sqrt(15) S_i with
+    the integer S_i = sum_{k=1..l} (i + k - 1)(n - k + 1) (1-based; the same
+    for every column j).  Returned as Python ints, summed term by term."""
+    return [sum((i + k - 1) * (n - k + 1) for k in range(1, l + 1)) for i in range(1, m + 1)]
+
+
+def _rn_sqrt15(S: int, q: int):
+    """(sign, M, s): sqrt(15) S = (-1)^sign M 2^-s rounded to nearest at q bits
+    (never a tie: sqrt(15) is irrational).  M = 0 for S = 0."""
+    if S == 0:
+        return (0, 0, 0)
+    X = 15 * S * S
+    s = max(0, q + 2 - (X.bit_length() + 1) // 2)
+    R = math.isqrt(X << (2 * s))            # floor(sqrt(15) |S| 2^s), >= q + 2 bits
+    d = R.bit_length() - q
+    keep, low = R >> d, R & ((1 << d) - 1)
+    if low >= 1 << (d - 1):                # the dropped part (plus an irrational tail) is >= half
+        keep += 1
+    if keep >> q:
+        keep >>= 1
+        d += 1
+    return (1 if S < 0 else 0, keep, s - d)
+
+
+def sqrt_product_rows(m: int, l: int, n: int, q: int) -> OMat:
+    """RN_q(c_i) for the m distinct rows of the exact product (an m x 1 matrix)."""
+    out = OMat.empty(m, 1, q)
+    L = (q + 63) // 64
+    for i, S in enumerate(sqrt_product_S(m, l, n)):
+        sg, M, s = _rn_sqrt15(S, q)
+        if M == 0:
+            continue
+        bl = M.bit_length()
+        mant = M << (64 * L - bl)
+        for k in range(L):
+            out.limb[k, i, 0] = (mant >> (64 * (L - 1 - k))) & 0xFFFFFFFFFFFFFFFF
+        out.exp[i, 0] = bl - s
+        out.sign[i, 0] = sg
+    return out
+
+
+def sqrt_rel_errors(Cm, m: int, l: int, n: int) -> np.ndarray:
+    """|c~_ij - c_ij| / |c_ij| for a computed product of the Section 4
+    matrices, entry by entry, evaluated exactly: with x = c~_ij / S_i,
+    |x - sqrt(15)| = |x^2 - 15| / (x + sqrt(15)).  Rows with S_i = 0 give inf
+    unless the entry is 0 too.  For small matrices (Python integers)."""
+    S = sqrt_product_S(m, l, n)
+    L = Cm.limb.shape[0]
+    r15 = math.sqrt(15.0)
+    out = np.zeros((m, n))
+    for i in range(m):
+        for j in range(n):
+            e = int(Cm.exp[i, j])
+            if e == EXP_ZERO:
+                out[i, j] = 0.0 if S[i] == 0 else 1.0
+                continue
+            v = 0
+            for k in range(L):
+                v = (v << 64) | int(Cm.limb[k, i, j])
+            x = Fraction(-v if Cm.sign[i, j] else v, 1 << (64 * L)) * Fraction(2) ** e / S[i] \
+                if S[i] else None
+            if x is None:
+                out[i, j] = math.inf
+                continue
+            if x <= 0:
+                out[i, j] = 1.0 + float(-x) / r15
+                continue
+            out[i, j] = float(abs(x * x - 15)) / ((float(x) + r15) * r15)
+    return out

@@ -96,7 +96,7 @@ int  orc_dot_exact_vec(const orc_num *a, const orc_num *b, int64_t l, int p_in, 
                        orc_num *r);
 
 /* ---- LU (orc_lu.c) ---- */
-int  orc_lu(orc_mat *A, int64_t *piv, int panel, int algo, int cutoff, int policy);
+int  orc_lu(orc_mat *A, int64_t *piv, int panel, int algo, int cutoff, int policy, int pivoting);
 int  orc_lu_solve(const orc_mat *LU, const int64_t *piv, const orc_mat *b, orc_mat *x);
 
 #endif

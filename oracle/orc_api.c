@@ -173,13 +173,14 @@ int orc_api_dot_exact(int64_t m, int64_t l, int64_t n, int p, int p_out, MAT_ARG
     return bad ? -1 : 0;
 }
 
-/* in-place LU of the n x n matrix A (interchange arrays overwritten) */
-int orc_api_lu(int64_t n, int p, int panel, int algo, int cutoff, int policy,
+/* in-place LU of the n x n matrix A (interchange arrays overwritten);
+ * pivoting 0 gives the paper's unpivoted LU */
+int orc_api_lu(int64_t n, int p, int panel, int algo, int cutoff, int policy, int pivoting,
                OUT_ARGS(A), int64_t *piv)
 {
     orc_mat A;
     if (orc_mat_import(&A, n, n, p, Al, Ae, As, Ald, Apl)) return -2;
-    int rc = orc_lu(&A, piv, panel, algo, cutoff, policy);
+    int rc = orc_lu(&A, piv, panel, algo, cutoff, policy, pivoting);
     orc_mat_export(&A, Al, Ae, As, Ald, Apl);
     orc_mat_free(&A);
     return rc;

@@ -6,7 +6,8 @@
  *
  * For each panel of K columns starting at j0 (Sec. 4, steps 1-3):
  *   1. panel factorisation, column k = j0 .. j0+K-1 in order:
- *        pivot row  = the first row i >= k with the largest |a_ik|;
+ *        pivot row  = the first row i >= k with the largest |a_ik|
+ *                     (row k itself when pivoting is off);
  *        swap rows k and pivot over all n columns;
  *        l_ik = RN(a_ik / a_kk) for i > k (one division, not a reciprocal);
  *        a_ij = RN(a_ij - RN(l_ik a_kj)) for i > k and panel columns j > k.
@@ -14,8 +15,8 @@
  *      ascending, a_rj = RN(a_rj - RN(l_rs a_sj)).
  *   3. A22 = RN(A22 - T), T = L21 U12 computed by the chosen GEMM algorithm
  *      (the underlined product of Sec. 4), one rounding for the subtraction.
- * The paper's LU has no pivoting; partial pivoting is added here.  With
- * no row exchange it reduces to the paper's procedure.
+ * The paper's LU has no pivoting (Sec. 4); partial pivoting is added here
+ * and can be switched off, which gives the paper's procedure exactly.
  */
 #include "orc.h"
 #include <stdlib.h>
@@ -34,7 +35,7 @@ static void swap_rows(orc_mat *A, int64_t r1, int64_t r2)
 }
 
 /* Returns 0, or k+1 if the pivot of column k is zero (A singular). */
-int orc_lu(orc_mat *A, int64_t *piv, int panel, int algo, int cutoff, int policy)
+int orc_lu(orc_mat *A, int64_t *piv, int panel, int algo, int cutoff, int policy, int pivoting)
 {
     int64_t n = A->rows;
     int p = A->p;
@@ -48,7 +49,7 @@ int orc_lu(orc_mat *A, int64_t *piv, int panel, int algo, int cutoff, int policy
             int64_t pr = k;
             orc_num best;
             orc_get(A, k, k, &best);
-            for (int64_t i = k + 1; i < n; ++i) {
+            for (int64_t i = k + 1; pivoting && i < n; ++i) {
                 orc_get(A, i, k, &x);
                 if (orc_cmpabs(&x, &best, p) > 0) { pr = i; orc_copy(&best, &x); }
             }

@@ -18,6 +18,7 @@ generator: word i of stream `seed` is mix(seed + (i + 1) * 0x9E3779B97F4A7C15).
 """
 from __future__ import annotations
 
+import math
 from dataclasses import dataclass
 from fractions import Fraction
 
@@ -309,3 +310,46 @@ def small_ints(rows: int, cols: int, p: int, seed: int, bits: int) -> HostMP:
         mag = (x >> 1) & ((1 << bits) - 1)
         vals.append((x & 1 if mag else 0, mag, 0))
     return from_exact_ints(vals, p, (rows, cols))
+
+
+def rn_sqrt(N: int, p: int):
+    """(sign, M, s) with M 2^-s = sqrt(N) rounded to nearest-even at p bits,
+    N >= 1 an integer.  sqrt(N) of a non-square N is irrational, so no tie
+    occurs; for a square the root is exact."""
+    t = (N.bit_length() + 1) // 2                  # sqrt(N) < 2^t
+    s = p + 2 - t if p + 2 > t else 0              # root of N 4^s has >= p + 2 bits
+    X = N << (2 * s)
+    Q = math.isqrt(X)
+    sticky = Q * Q != X
+    d = Q.bit_length() - p
+    if d <= 0:
+        return (0, Q, s)
+    rem, Q = Q & ((1 << d) - 1), Q >> d
+    half = 1 << (d - 1)
+    if rem > half or (rem == half and (sticky or Q & 1)):
+        Q += 1
+    if Q >> p:                                     # rounded up to 2^p
+        Q >>= 1
+        d += 1
+    return (0, Q, s - d)
+
+
+def sqrt_matrices(m: int, l: int, n: int, p: int, b_cols: int | None = None):
+    """The benchmark matrices of the paper's Section 4 ("Benchmark tests of
+    square and rectangle matrix multiplications"): a_ij = sqrt(5) (i + j - 1)
+    (m x l) and b_ij = sqrt(3) (n - i + 1) (l x n), 1-based, with n the
+    literal column count of B.  Each entry is the exact value rounded once
+    to p bits, RN_p(sqrt(5 k^2)).  a_ij depends on i + j only and b_ij on i
+    only: the distinct values are built once and gathered.  b_cols (default
+    n) narrows B to its first columns, which are all alike."""
+    def table(c, ks, idx):
+        """RN_p(sqrt(c) k) for the integers ks, gathered by idx."""
+        ex = [(0, 0, 0) if k == 0 else (1 if k < 0 else 0,) + rn_sqrt(c * k * k, p)[1:] for k in ks]
+        T = from_exact_ints(ex, p, (1, len(ex)))
+        return HostMP(np.ascontiguousarray(T.limb[:, 0, :][:, idx]), T.exp[0, idx].copy(),
+                      T.sign[0, idx].copy(), p)
+
+    A = table(5, range(1, m + l), np.arange(m)[:, None] + np.arange(l)[None, :])     # k = i + j - 1
+    B = table(3, [n - i + 1 for i in range(1, l + 1)],
+              np.broadcast_to(np.arange(l)[:, None], (l, n if b_cols is None else b_cols)))
+    return A, B

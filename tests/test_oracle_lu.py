@@ -101,7 +101,7 @@ def test_well_conditioned_keeps_identity_permutation():
 # ---------------------------------------------------------------------------
 # replay of Sec. 4 with mpmath scalar operations
 # ---------------------------------------------------------------------------
-def _replay_lu(A, p, panel):
+def _replay_lu(A, p, panel, pivoting=True):
     n = len(A)
     A = [row[:] for row in A]
     piv = []
@@ -110,7 +110,7 @@ def _replay_lu(A, p, panel):
         for k in range(j0, je):
             mag = lambda x: exact(mpmath.libmp.mpf_abs(x._mpf_))
             best, pr = mag(A[k][k]), k
-            for i in range(k + 1, n):
+            for i in range(k + 1, n if pivoting else k + 1):
                 if mag(A[i][k]) > best:
                     best, pr = mag(A[i][k]), i
             piv.append(pr)
@@ -145,6 +145,42 @@ def test_replay_blocked_lu(panel):
     for i in range(n):
         for j in range(n):
             assert entry_mpf(F, i, j) == ref[i][j], (i, j)
+
+
+@pytest.mark.parametrize("panel", [1, 3, 9])
+def test_replay_unpivoted_lu(panel):
+    """The paper's LU (Sec. 4, no pivoting) replayed with mpmath scalar ops."""
+    n, p = 9, 128
+    A = gen.uniform_pm1(n, n, p, 84)
+    F, piv, rc = orc.lu(A, panel=panel, algo=orc.SIMPLE, pivoting=False)
+    assert rc == 0 and list(piv) == list(range(n))
+    ref, rpiv = _replay_lu([[entry_mpf(A, i, j) for j in range(n)] for i in range(n)], p, panel, pivoting=False)
+    assert rpiv == list(range(n))
+    for i in range(n):
+        for j in range(n):
+            assert entry_mpf(F, i, j) == ref[i][j], (i, j)
+    # and it differs from the pivoted factorisation on this matrix
+    Fp, pivp, _ = orc.lu(A, panel=panel, algo=orc.SIMPLE)
+    assert list(pivp) != list(range(n))
+
+
+def test_unpivoted_exact_factors_and_zero_pivot():
+    """Without pivoting, [[1,2,3],[4,5,6],[7,8,10]] factors exactly into
+    L = [[1],[4,1],[7,2,1]], U = [[1,2,3],[-3,-6],[1]]; a zero leading entry
+    is a zero pivot (status 1) although the matrix is regular, which partial
+    pivoting avoids."""
+    p = 128
+    A = gen.from_ints([[1, 2, 3], [4, 5, 6], [7, 8, 10]], p)
+    F, piv, rc = orc.lu(A, panel=2, pivoting=False)
+    assert rc == 0 and list(piv) == [0, 1, 2]
+    want = [[1, 2, 3], [4, -3, -6], [7, 2, 1]]
+    assert [[gen.entry_fraction(F, i, j) for j in range(3)] for i in range(3)] == \
+        [[Fraction(v) for v in row] for row in want]
+    Z = gen.from_ints([[0, 1], [1, 1]], p)
+    _, _, rc = orc.lu(Z, panel=2, pivoting=False)
+    assert rc == 1
+    _, piv, rc = orc.lu(Z, panel=2)
+    assert rc == 0 and list(piv) == [1, 1]
 
 
 def test_replay_solve():
