@@ -53,6 +53,10 @@ def parse():
                     help="only the other configurations' runs and the per-algorithm errors")
     ap.add_argument("--lu", action="store_true",
                     help="only the LU runs: n = --lu-n at 256 and 1024 bits, well-conditioned and Lotkin")
+    ap.add_argument("--lu-sweep", action="store_true",
+                    help="only the paper's LU experiment: no pivoting, K = 32 alpha, alpha = 1..10")
+    ap.add_argument("--paper", action="store_true",
+                    help="only the paper's Section 4 benchmark (sqrt matrices, Tables 2-5 shapes)")
     ap.add_argument("--split", action="store_true",
                     help="only the split-form comparison (4096^3 at 1024 bits by default)")
     return ap.parse_args()
@@ -569,6 +573,66 @@ def lu_run(n, p, algo, panel=128, cutoff=64, kind="well"):
             "backward_error": back, "forward_error": fwd}
 
 
+def lu_sweep_run(n=1024, precs=(256, 1024), algos=(0, 2, 3), alphas=range(1, 11), seed=21):
+    """The paper's LU experiment (Sec. 4): no pivoting, a random matrix with
+    entries in [-1, 1) (seeded), x = [0, 1, ..., n-1], b = A x (Simple
+    product at p), block size K = alpha * 32 for alpha = 1..10, the
+    trailing update by Simple, Strassen or Winograd (n_min = 32); plus the
+    column-wise LU (one panel of n columns, no trailing product) as the
+    baseline.  Per run: seconds and the maximum relative error
+    max_i |x~_i - i| / i over i >= 1 (x~_0 enters as |x~_0|)."""
+    import numpy as np
+    import torch
+
+    from paper_1410_1599_gb300 import binding as mp
+    from paper_1410_1599_gb300 import inputs as gen
+
+    names = {0: "simple", 1: "block", 2: "strassen", 3: "winograd"}
+    out = []
+    mp.set_lu_pivoting(False)
+    try:
+        for p in precs:
+            A = gen.uniform_pm1(n, n, p, seed)
+            dA0 = mp.DeviceMP.from_host(A)
+            dxt = mp.DeviceMP.from_host(gen.from_ints([[i] for i in range(n)], p))
+            db = mp.DeviceMP.empty(n, 1, p)
+            mp.mpgemm(dA0, dxt, db, mp.SIMPLE)
+            q = 2 * p
+            wxt = mp.DeviceMP.from_host(gen.from_ints([[i] for i in range(n)], q))
+            runs = [("columnwise", mp.SIMPLE, n)] + [(names[a], a, 32 * al) for a in algos for al in alphas]
+            for name, algo, K in runs:
+                dA = mp.DeviceMP.empty(n, n, p)
+                dA.limb.copy_(dA0.limb)
+                dA.exp.copy_(dA0.exp)
+                dA.sign.copy_(dA0.sign)
+                dx = mp.DeviceMP.empty(n, 1, p)
+                piv = torch.zeros(n, dtype=torch.int64, device="cuda")
+                mp.set_lu(K, algo, 32)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                mp.mplu(dA, piv, db, dx)
+                rc = mp.sync_status()
+                t = time.perf_counter() - t0
+                wx = mp.DeviceMP.empty(n, 1, q)
+                mp.convert(dx, wx)
+                fe = mp.DeviceMP.empty(n, 1, q)
+                mp.elementwise(mp.OP_SUB, wx, wxt, fe)
+                mp.check_status("forward error")
+                torch.cuda.synchronize()
+                H = fe.to_host()
+                lg = np.log2(np.maximum(H.limb[0].astype(np.float64), 1.0) * 2.0 ** -64) + \
+                    np.where(H.exp == gen.EXP_ZERO, -np.inf, H.exp.astype(np.float64))
+                rel = lg[:, 0] - np.log2(np.maximum(np.arange(n), 1))
+                mx = float(np.max(rel))
+                out.append({"prec": p, "update": name, "K": K, "alpha": K // 32 if name != "columnwise" else None,
+                            "seconds": round(t, 4), "status": rc,
+                            "max_rel_err_log10": round(mx * np.log10(2.0), 2) if np.isfinite(mx) else None})
+    finally:
+        mp.set_lu(128, mp.SIMPLE, 64)
+        mp.set_lu_pivoting(True)
+    return {"n": n, "matrix": "uniform [-1,1), no pivoting", "x_true": "0..n-1", "runs": out}
+
+
 def serve_run(n_req, seed=11, slots=8, budget=150 << 30):
     """Config-5 style request stream through the library's serving loop:
     70% GEMM (m, l, n ~ U{16..2048}), 30% LU solve (n ~ U{64..1024}),
@@ -737,7 +801,9 @@ def serve_repeat_run(n_req=96, seed=12, slots=8, budget=150 << 30):
 
 def split_run(n=4096, p=1024, with_simple=True):
     """Split form vs the exact limb path (same correctly rounded result) on
-    n^3 at p bits, entries U[-1,1)*2^e, e ~ U{-16..16}."""
+    n^3 at p bits, entries U[-1,1)*2^e, e ~ U{-16..16}: the truncated split
+    form (default), the full split form (every digit diagonal), the exact
+    limb kernel and, for scale, the per-operation-rounded Simple kernel."""
     import numpy as np
     import torch
 
@@ -749,8 +815,11 @@ def split_run(n=4096, p=1024, with_simple=True):
     dA, dB = mp.DeviceMP.from_host(A), mp.DeviceMP.from_host(B)
     out = {}
     res = {}
-    for name, algo in (("split", mp.SPLIT), ("exact_limb", mp.EXACT)) + ((("simple_limb", mp.SIMPLE),) if with_simple else ()):
+    runs = (("split", mp.SPLIT, True), ("split_full", mp.SPLIT, False), ("exact_limb", mp.EXACT, True)) + \
+        ((("simple_limb", mp.SIMPLE, True),) if with_simple else ())
+    for name, algo, trunc in runs:
         C = mp.DeviceMP.empty(n, n, p)
+        mp.set_split_truncation(trunc)
         torch.cuda.synchronize()
         mp.profile_enable(True)
         t0 = time.perf_counter()
@@ -759,12 +828,15 @@ def split_run(n=4096, p=1024, with_simple=True):
         t = time.perf_counter() - t0
         prof = mp.profile_read()
         mp.profile_enable(False)
+        mp.set_split_truncation(True)
         out[name] = {"seconds": round(t, 3), "eff_gflops": round(2.0 * n ** 3 / t / 1e9, 3), "status": rc,
                      "kernels_ms": {k: round(v[1], 2) for k, v in prof.items() if v[0]}}
-        if name == "split":
+        if algo == mp.SPLIT:
             S = (p + 64 + 7) // 8 + 1
             macs = prof["split_slices"][2]
             out[name]["digits"] = S
+            out[name]["digit_pairs_kept"] = round(macs / (S * S * n * float(-(-n // 32) * 32) * n), 4)
+            out[name]["exact_fallback_outputs"] = mp.split_fallbacks()
             out[name]["tensor_macs"] = macs
             tflops = 2.0 * macs / (prof["split_slices"][1] * 1e-3) / 1e12
             out[name]["slice_tmac_per_s"] = round(tflops / 2.0, 2)
@@ -775,9 +847,10 @@ def split_run(n=4096, p=1024, with_simple=True):
                                      "frac": round(tflops / peak, 4),
                                      "peak_note": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)"}
         res[name] = C
-    same = bool(torch.equal(res["split"].limb, res["exact_limb"].limb) and
-                torch.equal(res["split"].exp, res["exact_limb"].exp) and
-                torch.equal(res["split"].sign, res["exact_limb"].sign))
+    def equal(X, Y):
+        return bool(torch.equal(X.limb, Y.limb) and torch.equal(X.exp, Y.exp) and torch.equal(X.sign, Y.sign))
+
+    same = equal(res["split"], res["exact_limb"]) and equal(res["split_full"], res["exact_limb"])
     exps = A.exp.astype(np.float64)
     wide_rows = int(sum(1 for i in range(n) if (A.exp[i][A.exp[i] != gen.EXP_ZERO]).min()
                         < (A.exp[i][A.exp[i] != gen.EXP_ZERO]).max() - 64))
@@ -787,6 +860,120 @@ def split_run(n=4096, p=1024, with_simple=True):
             "wide_rows": wide_rows, "wide_cols": wide_cols,
             "speedup_split_vs_exact_limb": round(out["exact_limb"]["seconds"] / out["split"]["seconds"], 3),
             **out}
+
+
+# The paper's CPU times (seconds, MPFR on one core of a Core i7 3850; context
+# only): Tables 3 and 4 (square n, n_min = 32: min(Simple, Block), Strassen,
+# Winograd) and Table 5 (m = n = 1024, varying l: Simple, Block(32),
+# Strassen, Winograd).
+PAPER_SQUARE = {
+    128: {255: (1.06, 0.72, 0.63), 256: (1.22, 0.70, 0.57), 257: (1.04, 0.74, 0.60),
+          511: (9.60, 4.84, 4.06), 512: (9.68, 4.77, 3.73), 513: (9.89, 4.92, 3.88),
+          1023: (77.63, 32.02, 25.57), 1024: (77.72, 31.53, 24.10), 1025: (78.41, 32.21, 24.77),
+          2047: (619.21, 211.80, 163.87), 2048: (618.87, 211.19, 155.67), 2049: (623.24, 212.79, 157.52)},
+    1024: {255: (5.46, 2.33, 1.95), 256: (5.53, 2.31, 1.72), 257: (5.61, 2.41, 1.81),
+           511: (43.81, 13.40, 10.57), 512: (44.20, 13.02, 9.44), 513: (44.37, 13.38, 9.81),
+           1023: (352.79, 76.93, 57.98), 1024: (355.99, 74.58, 52.47), 1025: (356.58, 76.36, 54.22),
+           2047: (2820.16, 454.02, 329.41), 2048: (2824.34, 446.87, 302.56), 2049: (2829.95, 456.08, 307.05)},
+}
+PAPER_RECT = {
+    128: {63: (5.09, 5.86, 5.31, 4.29), 64: (5.18, 5.91, 5.03, 3.99), 65: (5.26, 6.30, 5.24, 4.21),
+          127: (10.47, 11.8, 9.43, 6.45), 128: (10.54, 11.86, 8.71, 5.42), 129: (10.63, 12.24, 8.90, 5.65),
+          255: (52.51, 23.69, 14.67, 9.39), 256: (52.27, 23.77, 13.13, 7.51), 257: (52.56, 24.07, 13.39, 7.70),
+          511: (110.75, 47.42, 26.40, 16.55), 512: (106.19, 47.44, 21.85, 11.83), 513: (110.82, 47.96, 22.08, 12.09)},
+    1024: {63: (24.71, 26.74, 19.92, 14.88), 64: (25.77, 27.13, 19.49, 14.31), 65: (26.24, 27.82, 20.04, 14.91),
+           127: (52.37, 53.75, 32.26, 19.02), 128: (53.17, 54.23, 30.69, 16.74), 129: (53.59, 54.97, 30.79, 17.37),
+           255: (105.04, 108.90, 47.43, 24.15), 256: (106.34, 108.64, 43.12, 19.83), 257: (106.92, 109.83, 43.63, 20.48),
+           511: (244.07, 216.82, 71.30, 34.18), 512: (245.69, 216.65, 61.01, 25.22), 513: (247.96, 217.69, 62.14, 25.91)},
+}
+
+
+def paper_run(stream, precs=(128, 1024), square=True, rect=True):
+    """The paper's Section 4 benchmark on the GPU: a_ij = sqrt(5)(i+j-1),
+    b_ij = sqrt(3)(n-i+1); square n in 255..2049 (Tables 2-4) and
+    1024 x l x 1024 (Table 5); Simple, Block, Strassen and Winograd with
+    n_min = 32 and the mixed odd-size policy (Table 1's counts).  Per run:
+    device seconds and the maximum and minimum relative error against the
+    exact product, whose rows are taken from the library's exact-dot kernel
+    at 2p on the same matrices generated at 2p bits (their own error is
+    about 2^-2p, far below the products' 2^-p)."""
+    import numpy as np
+    import torch
+
+    from paper_1410_1599_gb300 import binding as mp
+    from paper_1410_1599_gb300 import inputs as gen
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    algos = (("simple", mp.SIMPLE), ("block", mp.BLOCK), ("strassen", mp.STRASSEN), ("winograd", mp.WINOGRAD))
+    mp.set_odd_policy(mp.MIXED)
+
+    def reference_rows(m, l, n, q):
+        A2, B2 = gen.sqrt_matrices(m, l, n, q, b_cols=1)    # the columns of B are all alike
+        dA2, dB2 = mp.DeviceMP.from_host(A2), mp.DeviceMP.from_host(B2)
+        R = mp.DeviceMP.empty(m, 1, q)
+        mp.mpgemm(dA2, dB2, R, mp.EXACT, 64)
+        mp.check_status("reference rows")
+        return R
+
+    def rel_errors(C, R):
+        m, n, q = C.rows, C.cols, R.p
+        torch.cuda.synchronize()            # R and C come from the library's stream
+        C2 = mp.DeviceMP.empty(m, n, q)
+        mp.convert(C, C2)
+        Rf = mp.DeviceMP(R.limb.expand(-1, -1, n).contiguous(), R.exp.expand(-1, n).contiguous(),
+                         R.sign.expand(-1, n).contiguous(), q, m, n)
+        torch.cuda.synchronize()            # the expansion ran on torch's stream
+        D = mp.DeviceMP.empty(m, n, q)
+        mp.elementwise(mp.OP_SUB, C2, Rf, D)
+        mp.check_status("error difference")
+        torch.cuda.synchronize()
+        top = D.limb[0].cpu().numpy().view(np.uint64).astype(np.float64) * 2.0 ** -64
+        e = D.exp.cpu().numpy()
+        rtop = R.limb[0, :, 0].cpu().numpy().view(np.uint64).astype(np.float64) * 2.0 ** -64
+        re = R.exp[:, 0].cpu().numpy().astype(np.float64)
+        zero = e == gen.EXP_ZERO
+        lg = np.log2(np.where(zero, 1.0, top)) + np.where(zero, 0, e) - (np.log2(rtop) + re)[:, None]
+        err = np.where(zero, 0.0, np.exp2(lg))
+        return float(err.max()), float(err.min())
+
+    def one(m, l, n, p):
+        A, B = gen.sqrt_matrices(m, l, n, p)
+        dA, dB = mp.DeviceMP.from_host(A), mp.DeviceMP.from_host(B)
+        R = reference_rows(m, l, n, 2 * p)
+        row = {"m": m, "l": l, "n": n, "prec": p}
+        for name, algo in algos:
+            C = mp.DeviceMP.empty(m, n, p)
+            mp.mpgemm(dA, dB, C, algo, 32)                 # warm-up
+            torch.cuda.synchronize()
+            e0.record(stream)
+            mp.mpgemm(dA, dB, C, algo, 32)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            rc = mp.sync_status()
+            t = e0.elapsed_time(e1) * 1e-3
+            mx, mn = rel_errors(C, R)
+            row[name] = {"seconds": round(t, 5), "eff_gflops": round(2.0 * m * l * n / t / 1e9, 3),
+                         "max_rel_err": mx, "min_rel_err": mn, "status": rc}
+        return row
+
+    out = {"square": [], "rectangle": []}
+    try:
+        for p in precs:
+            if square:
+                for n in sorted(PAPER_SQUARE[p]):
+                    r = one(n, n, n, p)
+                    r["paper_cpu_seconds"] = dict(zip(("min_simple_block", "strassen", "winograd"),
+                                                      PAPER_SQUARE[p][n]))
+                    out["square"].append(r)
+            if rect:
+                for l in sorted(PAPER_RECT[p]):
+                    r = one(1024, l, 1024, p)
+                    r["paper_cpu_seconds"] = dict(zip(("simple", "block32", "strassen", "winograd"),
+                                                      PAPER_RECT[p][l]))
+                    out["rectangle"].append(r)
+    finally:
+        mp.set_odd_policy(mp.PEEL)
+    return out
 
 
 def cpu_baseline(A, B, seconds):
@@ -869,6 +1056,23 @@ def main():
         libbuild.build()
         torch.cuda.set_device(local)
         print(json.dumps({"split_form": split_run(a.n if a.n != 2048 else 4096, a.prec if a.prec != 512 else 1024)}), flush=True)
+        return
+    if a.lu_sweep:
+        import torch
+        from paper_1410_1599_gb300 import build as libbuild
+        libbuild.build()
+        torch.cuda.set_device(local)
+        print(json.dumps({"lu_sweep": lu_sweep_run(a.lu_n)}), flush=True)
+        return
+    if a.paper:
+        import torch
+        from paper_1410_1599_gb300 import binding as mp
+        from paper_1410_1599_gb300 import build as libbuild
+        libbuild.build()
+        torch.cuda.set_device(local)
+        stream = torch.cuda.Stream()
+        mp.set_stream(stream)
+        print(json.dumps({"paper_section4": paper_run(stream)}), flush=True)
         return
     if a.serve:
         import torch

@@ -78,7 +78,12 @@ enum {
                           tensor cores (exact integer fp16 x fp16 -> fp32
                           chunks folded into int64), exact recombination, one
                           rounding; rows/columns whose exponents spread more
-                          than 64 bits are computed by the MP_EXACT kernel */
+                          than 64 bits are computed by the MP_EXACT kernel.
+                          By default the lowest weight diagonals of digit
+                          products are skipped under a proven bound and the
+                          outputs whose rounding the bound leaves open are
+                          recomputed by the MP_EXACT kernel (same bits;
+                          mp_set_split_truncation) */
 };
 
 /* handling of odd dimensions in the recursion (Sec. 2, last paragraph) */
@@ -112,9 +117,21 @@ int mp_set_workspace(void *ptr, size_t bytes);
 /* Odd-dimension policy for Strassen / Winograd (MP_PEEL or MP_MIXED). */
 int mp_set_odd_policy(int policy);
 
+/* Split form (MP_SPLIT): 1 (default) skips the digit-product diagonals whose
+ * sum is provably below the rounding position of typical outputs and
+ * recomputes exactly every output the bound leaves undecided; 0 computes
+ * all diagonals.  Both give the correctly rounded exact dot product.
+ * MP_ERR_ARG for any other value. */
+int mp_set_split_truncation(int on);
+
 /* LU settings used by mplu: panel width K (Sec. 4 block size, >= 1), the
  * trailing-update algorithm (MP_SIMPLE .. MP_WINOGRAD) and its cutoff. */
 int mp_set_lu(int panel, int algo, int cutoff);
+
+/* Row exchanges in mplu: 1 (default) partial pivoting; 0 the paper's LU
+ * without pivoting (Sec. 4: no exchange, the pivot of column k is a_kk and
+ * piv[k] = k).  MP_ERR_ARG for any other value. */
+int mp_set_lu_pivoting(int on);
 
 /* ---- elementwise arithmetic -------------------------------------------- */
 
@@ -198,7 +215,8 @@ int mpgemm_noalloc(int64_t m, int64_t l, int64_t n, int32_t prec, int32_t algo, 
 size_t mplu_workspace_size(int64_t n, int32_t prec);
 
 /*
- * Blocked right-looking LU with partial pivoting of the n x n matrix A
+ * Blocked right-looking LU with partial pivoting (or none, see
+ * mp_set_lu_pivoting) of the n x n matrix A
  * (overwritten by L\U, unit lower L), then the solve of A x = b.
  *   piv : device int64[n]; piv[k] is the row exchanged with row k at step k;
  *   b   : n x 1 (read only); x : n x 1 (written), may be NULL to factor only.
@@ -328,6 +346,11 @@ int mp_sync_status(void);
 
 /* Column (0-based) of the zero pivot behind the last MP_ERR_SINGULAR. */
 int64_t mp_singular_column(void);
+
+/* Outputs of MP_SPLIT products that the truncated split form left to the
+ * exact limb kernel, counted on the device between the last two
+ * mp_sync_status calls of this thread (read by the later one). */
+int64_t mp_split_fallbacks(void);
 
 const char *mp_strerror(int status);
 

@@ -27,7 +27,8 @@ ERRORS = {-1: "MP_ERR_ARG", -2: "MP_ERR_NOMEM", -3: "MP_ERR_SINGULAR", -4: "MP_E
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
 # every symbol include/mpgemm.h declares
-EXPORTS = ["mp_set_stream", "mp_set_workspace", "mp_set_odd_policy", "mp_set_lu",
+EXPORTS = ["mp_set_stream", "mp_set_workspace", "mp_set_odd_policy", "mp_set_lu", "mp_set_lu_pivoting",
+           "mp_set_split_truncation", "mp_split_fallbacks",
            "mp_elementwise", "mp_convert", "mpgemm_workspace_size", "mpgemm",
            "mplu_workspace_size", "mplu", "mp_sync_status", "mp_singular_column",
            "mp_strerror", "mp_version", "mp_profile_enable", "mp_profile_read",
@@ -98,6 +99,7 @@ def load_library(path: str = LIB_PATH):
             lib.mp_set_stream.argtypes = [C.c_void_p]
             lib.mp_set_workspace.argtypes = [C.c_void_p, C.c_size_t]
             lib.mp_singular_column.restype = C.c_int64
+            lib.mp_split_fallbacks.restype = C.c_int64
             lib.mp_strerror.restype = C.c_char_p
             lib.mp_server_create.restype = C.c_void_p
             lib.mp_server_create.argtypes = [C.c_size_t, C.c_int]
@@ -193,6 +195,20 @@ def set_odd_policy(policy: int) -> None:
 
 def set_lu(panel: int = 128, algo: int = SIMPLE, cutoff: int = 64) -> None:
     _check(load_library().mp_set_lu(panel, algo, cutoff), "lu settings")
+
+
+def set_lu_pivoting(on: bool = True) -> None:
+    _check(load_library().mp_set_lu_pivoting(1 if on else 0), "lu pivoting")
+
+
+def set_split_truncation(on: bool = True) -> None:
+    _check(load_library().mp_set_split_truncation(1 if on else 0), "split truncation")
+
+
+def split_fallbacks() -> int:
+    """Outputs the truncated split form left to the exact kernel, as counted
+    by the last sync_status()."""
+    return load_library().mp_split_fallbacks()
 
 
 def sync_status() -> int:

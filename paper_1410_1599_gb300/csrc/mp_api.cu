@@ -20,7 +20,10 @@ struct ThreadState {
     size_t ws_bytes = 0;
     int odd_policy = MP_PEEL;
     int lu_panel = 128, lu_algo = MP_SIMPLE, lu_cutoff = 64;
+    bool lu_pivoting = true;
+    bool split_truncate = true;
     long long singular_col = -1;
+    long long split_fallbacks = 0;
 };
 thread_local ThreadState g_ts;
 
@@ -65,7 +68,7 @@ DevStatus *status_ptr()
     if (!g_status[dev]) {
         DevStatus *p = nullptr;
         if (cudaMalloc(&p, sizeof(DevStatus)) != cudaSuccess) return nullptr;
-        DevStatus init{0u, 0u, INT64_MAX};
+        DevStatus init{0u, 0u, INT64_MAX, 0ull};
         cudaMemcpy(p, &init, sizeof init, cudaMemcpyHostToDevice);
         g_status[dev] = p;
     }
@@ -396,13 +399,26 @@ int run_recursion(int algo, const std::vector<LevelDims> &lv, int p, BMat A0, BM
     return launch_status();
 }
 
-// split form: digit planes, exponent / spread vectors, diagonal sums
+// first diagonal of the split form under the current settings
+int split_s0(int p, int64_t l, int64_t *ebits)
+{
+    if (!g_ts.split_truncate) {
+        *ebits = -1;
+        return 0;
+    }
+    return split_first_diagonal(p, l, ebits);
+}
+
+// split form: digit planes, exponent / spread vectors, diagonal sums (planes
+// s0 .. 2S-2), the list of outputs left to the exact kernel and its count
 size_t split_ws_bytes(int64_t m, int64_t l, int64_t n, int p)
 {
     const size_t S = (size_t)split_digit_count(p), lp = (size_t)split_row_pad(l);
+    int64_t eb;
+    const size_t s0 = (size_t)split_s0(p, l, &eb);
     return padded(S * m * lp * 2) + padded(S * n * lp * 2) + padded((size_t)m * 8) +
            padded((size_t)n * 8) + padded((size_t)m) + padded((size_t)n) +
-           padded((2 * S - 1) * m * n * 8) + 8 * 256;
+           padded((2 * S - 1 - s0) * m * n * 8) + padded((size_t)m * n * 8) + padded(8) + 8 * 256;
 }
 
 int run_split(int64_t m, int64_t l, int64_t n, int p, BMat A, BMat B, BMat C, Workspace &ws,
@@ -416,7 +432,15 @@ int run_split(int64_t m, int64_t l, int64_t n, int p, BMat A, BMat B, BMat C, Wo
     int64_t *eb = (int64_t *)ws.take((size_t)n * 8);
     uint8_t *wa = (uint8_t *)ws.take((size_t)m);
     uint8_t *wb = (uint8_t *)ws.take((size_t)n);
-    long long *D = (long long *)ws.take((2 * S - 1) * m * n * 8);
+    int64_t ebits;
+    const int s0 = split_s0(p, l, &ebits);
+    long long *D = (long long *)ws.take((2 * S - 1 - (size_t)s0) * m * n * 8);
+    int64_t *list = (int64_t *)ws.take((size_t)m * n * 8);
+    unsigned long long *count = (unsigned long long *)ws.take(8);
+    if (cudaMemsetAsync(count, 0, 8, s) != cudaSuccess) {
+        ws.reset(mk);
+        return MP_ERR_CUDA;
+    }
     {
         Prof pr(MP_K_SPLIT_AUX, (double)(m * l + l * n), s);
         dispatch(p, [&](auto w) {
@@ -424,8 +448,10 @@ int run_split(int64_t m, int64_t l, int64_t n, int p, BMat A, BMat B, BMat C, Wo
         });
     }
     {
-        Prof pr(MP_K_SPLIT, (double)S * S * m * (double)lp * n, s);
-        const int rs = launch_split_slices(pa, pb, m, l, n, p, D, st, s);
+        double pairs = 0;                                   // digit pairs on the kept diagonals
+        for (int d = s0; d <= 2 * (int)S - 2; ++d) pairs += std::min<int>(d + 1, 2 * (int)S - 1 - d);
+        Prof pr(MP_K_SPLIT, pairs * m * (double)lp * n, s);
+        const int rs = launch_split_slices(pa, pb, m, l, n, p, s0, D, st, s);
         if (rs != MP_OK) {
             ws.reset(mk);
             return rs;
@@ -434,7 +460,13 @@ int run_split(int64_t m, int64_t l, int64_t n, int p, BMat A, BMat B, BMat C, Wo
     {
         Prof pr(MP_K_SPLIT_AUX, (double)m * n, s);
         dispatch(p, [&](auto w) {
-            launch_split_finish<decltype(w)::value>(D, m, n, p, ea, eb, wa, wb, C, st, s);
+            launch_split_finish<decltype(w)::value>(D, m, n, p, s0, ebits, ea, eb, wa, wb, C, list, count, st, s);
+        });
+    }
+    if (ebits >= 0) {
+        Prof pr(MP_K_SPLIT_AUX, 0.0, s);
+        dispatch(p, [&](auto w) {
+            launch_gemm_exact_list<decltype(w)::value>(A, B, C, n, l, p, st, s, list, count);
         });
     }
     {
@@ -631,6 +663,13 @@ int mp_set_lu(int panel, int algo, int cutoff)
     return MP_OK;
 }
 
+int mp_set_lu_pivoting(int on)
+{
+    if (on != 0 && on != 1) return MP_ERR_ARG;
+    g_ts.lu_pivoting = on == 1;
+    return MP_OK;
+}
+
 const char *mp_strerror(int status)
 {
     switch (status) {
@@ -655,10 +694,11 @@ int mp_sync_status(void)
     if (!st) return MP_ERR_CUDA;
     DevStatus h{};
     if (cudaMemcpy(&h, st, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess) return MP_ERR_CUDA;
-    if (h.flags) {
-        DevStatus init{0u, 0u, INT64_MAX};
+    if (h.flags || h.split_fallbacks) {
+        DevStatus init{0u, 0u, INT64_MAX, 0ull};
         cudaMemcpy(st, &init, sizeof init, cudaMemcpyHostToDevice);
     }
+    g_ts.split_fallbacks = (long long)h.split_fallbacks;
     g_ts.singular_col = (h.singular_col == INT64_MAX) ? -1 : h.singular_col;
     if (h.flags & ST_TIMEOUT) return MP_ERR_TIMEOUT;
     if (h.flags & ST_SINGULAR) return MP_ERR_SINGULAR;
@@ -669,6 +709,15 @@ int mp_sync_status(void)
 }
 
 int64_t mp_singular_column(void) { return g_ts.singular_col; }
+
+int64_t mp_split_fallbacks(void) { return g_ts.split_fallbacks; }
+
+int mp_set_split_truncation(int on)
+{
+    if (on != 0 && on != 1) return MP_ERR_ARG;
+    g_ts.split_truncate = on == 1;
+    return MP_OK;
+}
 
 int mp_profile_enable(int on)
 {
@@ -824,6 +873,7 @@ int mplu(int64_t n, int32_t prec, mpmat_t *A, int64_t *piv, const mpmat_t *b, mp
     if (!st) return MP_ERR_CUDA;
     const int K = g_ts.lu_panel, algo = g_ts.lu_algo, cutoff = g_ts.lu_cutoff;
     const int policy = g_ts.odd_policy;
+    const bool pivoting = g_ts.lu_pivoting;
     const int L = limbs_of(prec);
     Workspace ws;
     int rc = ws.acquire(lu_ws_bytes(n, prec, K, algo, cutoff, policy), s);
@@ -845,13 +895,13 @@ int mplu(int64_t n, int32_t prec, mpmat_t *A, int64_t *piv, const mpmat_t *b, mp
                 Prof pr(MP_K_LU, (double)(je - j0) * (n - j0), s);
                 if (fused) {
                     // exchanges on the panel's columns now, on the rest after the panel
-                    launch_lu_pivot<WW>(A0, n, j0, piv, prec, st, s, j0, je);
+                    launch_lu_pivot<WW>(A0, n, j0, piv, prec, st, s, j0, je, pivoting);
                     for (int64_t k = j0; k < je; ++k)
-                        launch_lu_column<WW>(A0, n, j0, k, je, piv, prec, st, cand, ticket, s);
+                        launch_lu_column<WW>(A0, n, j0, k, je, piv, prec, st, cand, ticket, s, pivoting);
                     launch_lu_laswp<WW>(A0, n, j0, je, piv, prec, s);
                 } else {
                     for (int64_t k = j0; k < je; ++k) {
-                        launch_lu_pivot<WW>(A0, n, k, piv, prec, st, s, 0, n);
+                        launch_lu_pivot<WW>(A0, n, k, piv, prec, st, s, 0, n, pivoting);
                         launch_lu_divide<WW>(A0, n, k, prec, s);
                         launch_lu_rank1<WW>(A0, k, k + 1, n, k + 1, je, prec, st, s);
                     }

@@ -173,6 +173,30 @@ __device__ __noinline__ void exact_one(const BMat &A, const BMat &B, const BMat 
     if (st<W>(c, C, 0, i, j, rs.L)) flag(status, ST_RANGE);
 }
 
+// the outputs t = i n + j listed in list[0 .. *count), one thread each
+template <int W>
+__global__ void __launch_bounds__(ExactCfg<W>::THREADS)
+gemm_exact_list_kernel(BMat A, BMat B, BMat C, int64_t n, int64_t l, int p, DevStatus *status,
+                       const int64_t *list, const unsigned long long *count)
+{
+    const RoundSpec rs = make_spec<W>(p);
+    const int64_t cnt = (int64_t)*count;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && cnt) atomicAdd(&status->split_fallbacks, (unsigned long long)cnt);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < cnt;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = list[q];
+        exact_one<W>(A, B, C, t / n, t % n, l, rs, status);
+    }
+}
+
+template <int W>
+void launch_gemm_exact_list(BMat A, BMat B, BMat C, int64_t n, int64_t l, int p, DevStatus *st,
+                            cudaStream_t s, const int64_t *list, const unsigned long long *count)
+{
+    constexpr int T = ExactCfg<W>::THREADS;
+    gemm_exact_list_kernel<W><<<152 * 4, T, 0, s>>>(A, B, C, n, l, p, st, list, count);
+}
+
 template <int W>
 void launch_gemm_exact(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p,
                        DevStatus *st, cudaStream_t s, const uint8_t *rowsel, const uint8_t *colsel)
@@ -186,6 +210,9 @@ void launch_gemm_exact(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, 
 #define MPG_INSTANTIATE_EXACT(W)                                                                \
     template void launch_gemm_exact<W>(BMat, BMat, BMat, int64_t, int64_t, int64_t, int,        \
                                        DevStatus *, cudaStream_t, const uint8_t *,              \
-                                       const uint8_t *);
+                                       const uint8_t *);                                        \
+    template void launch_gemm_exact_list<W>(BMat, BMat, BMat, int64_t, int64_t, int, DevStatus *, \
+                                            cudaStream_t, const int64_t *,                      \
+                                            const unsigned long long *);
 
 }  // namespace mpg

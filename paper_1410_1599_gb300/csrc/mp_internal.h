@@ -30,6 +30,7 @@ struct DevStatus {
     unsigned flags;
     unsigned pad;
     long long singular_col;   // smallest column index with a zero pivot
+    unsigned long long split_fallbacks;   // split-form outputs recomputed exactly
 };
 
 // Launchers, one instantiation per word-capacity class W in {4, 8, 16, 32, 64}.
@@ -78,26 +79,37 @@ void launch_gemm_exact(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, 
                        DevStatus *st, cudaStream_t s, const uint8_t *rowsel = nullptr,
                        const uint8_t *colsel = nullptr);
 
+// One thread per listed output t = i n + j (list[0 .. *count)): c_ij by the
+// exact limb kernel; *count is added to status->split_fallbacks.
+template <int W>
+void launch_gemm_exact_list(BMat A, BMat B, BMat C, int64_t n, int64_t l, int p, DevStatus *st,
+                            cudaStream_t s, const int64_t *list, const unsigned long long *count);
+
 // split form of C = RN_p(exact A B) (mp_split.cuh): digit planes, slice
 // products by weight diagonal, recombination; rows/columns beyond the
-// spread budget are recomputed by launch_gemm_exact with rowsel/colsel
+// spread budget are recomputed by launch_gemm_exact with rowsel/colsel.
+// With truncation the diagonals below s0 are skipped (D holds planes
+// s0 .. 2S-2), their sum is below 2^eb in units of the lowest digit, and
+// outputs whose rounding that bound leaves open are listed for the exact
+// limb kernel (eb < 0: nothing skipped, nothing listed).
 int split_digit_count(int p);
 int64_t split_row_pad(int64_t l);
+int split_first_diagonal(int p, int64_t l, int64_t *ebits);
 template <int W>
 void launch_split_prep(BMat A, BMat B, int64_t m, int64_t l, int64_t n, int p, __half *pa,
                        __half *pb, int64_t *ea, int64_t *eb, uint8_t *wa, uint8_t *wb, cudaStream_t s);
 int launch_split_slices(const __half *pa, const __half *pb, int64_t m, int64_t l, int64_t n, int p,
-                        long long *D, DevStatus *st, cudaStream_t s);
+                        int s0, long long *D, DevStatus *st, cudaStream_t s);
 template <int W>
-void launch_split_finish(const long long *D, int64_t m, int64_t n, int p, const int64_t *ea,
-                         const int64_t *eb, const uint8_t *wa, const uint8_t *wb, BMat C,
-                         DevStatus *st, cudaStream_t s);
+void launch_split_finish(const long long *D, int64_t m, int64_t n, int p, int s0, int64_t ebits,
+                         const int64_t *ea, const int64_t *eb, const uint8_t *wa, const uint8_t *wb,
+                         BMat C, int64_t *list, unsigned long long *count, DevStatus *st, cudaStream_t s);
 
 // LU (Sec. 4): pivot search + row exchange of column k; l_ik = a_ik / a_kk;
 // one elimination step a_ij -= a_ik a_kj on [r0, r1) x [c0, c1); solves
 template <int W>
 void launch_lu_pivot(BMat A, int64_t n, int64_t k, int64_t *piv, int p, DevStatus *st,
-                     cudaStream_t s, int64_t c0, int64_t c1);
+                     cudaStream_t s, int64_t c0, int64_t c1, bool pivoting);
 template <int W>
 void launch_lu_divide(BMat A, int64_t n, int64_t k, int p, cudaStream_t s);
 template <int W>
@@ -115,7 +127,7 @@ template <int W>
 bool lu_fused_ok(int64_t panel);
 template <int W>
 void launch_lu_column(BMat A, int64_t n, int64_t j0, int64_t k, int64_t je, int64_t *piv, int p,
-                      DevStatus *st, int64_t *cand, unsigned *ticket, cudaStream_t s);
+                      DevStatus *st, int64_t *cand, unsigned *ticket, cudaStream_t s, bool pivoting);
 template <int W>
 void launch_lu_laswp(BMat A, int64_t n, int64_t j0, int64_t je, const int64_t *piv, int p, cudaStream_t s);
 template <int W>

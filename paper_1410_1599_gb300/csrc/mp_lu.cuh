@@ -19,7 +19,8 @@ MP_DEV bool absgreater(const Mp<W> &x, const Mp<W> &y)
     return cmpabs<W>(x, y) > 0;
 }
 
-// One CTA: pivot = first row i in [k, n) of largest |a_ik|; record it, then
+// One CTA: pivot = first row i in [k, iend) of largest |a_ik| (iend = n
+// with partial pivoting, k + 1 for the paper's unpivoted LU); record it, then
 // exchange rows k and pivot over the columns [c0, c1) (all n, or the panel
 // when the other columns are exchanged later by lu_laswp_kernel).  A zero
 // pivot column is recorded (smallest such column wins) and nothing is
@@ -31,7 +32,7 @@ MP_DEV bool absgreater(const Mp<W> &x, const Mp<W> &y)
 // candidate carries the largest key list it, and one thread settles the list
 // (usually one entry) by full comparison, lower row first among equals.
 template <int W>
-__global__ void __launch_bounds__(LuCfg<W>::PIVOT) lu_pivot_kernel(BMat A, int64_t n, int64_t k, int64_t *piv,
+__global__ void __launch_bounds__(LuCfg<W>::PIVOT) lu_pivot_kernel(BMat A, int64_t iend, int64_t k, int64_t *piv,
                                                         int p, DevStatus *status, int64_t c0, int64_t c1)
 {
     constexpr int NT = LuCfg<W>::PIVOT, NW = NT / 32;
@@ -45,7 +46,7 @@ __global__ void __launch_bounds__(LuCfg<W>::PIVOT) lu_pivot_kernel(BMat A, int64
     int64_t best = -1;
     Mp<W> bx, x;
     set_zero<W>(bx, 0u);
-    for (int64_t i = k + tid; i < n; i += NT) {
+    for (int64_t i = k + tid; i < iend; i += NT) {
         ld_rw<W>(x, A, 0, i, k, rs.L);
         if (best < 0 || absgreater<W>(x, bx)) {
             best = i;
@@ -290,7 +291,7 @@ __device__ void cta_swap_rows(const BMat &A, int64_t c0, int64_t c1, int64_t r1,
 template <int W>
 __global__ void __launch_bounds__(LU_COL_WARPS * 32)
 lu_column_kernel(BMat A, int64_t n, int64_t j0, int64_t k, int64_t je, int64_t *piv, int p,
-                 DevStatus *status, int64_t *cand, unsigned *ticket)
+                 DevStatus *status, int64_t *cand, unsigned *ticket, int pivoting)
 {
     static_assert(W <= 32, "warp-per-row column step");
     constexpr int NT = LU_COL_WARPS * 32;
@@ -332,7 +333,7 @@ lu_column_kernel(BMat A, int64_t n, int64_t j0, int64_t k, int64_t je, int64_t *
             mul<W, true>(z, l, u, rs);
             add<W, true>(y, y, z, 1u, rs);
             bad |= st<W>(y, A, 0, i, j, rs.L);
-            if (j == k + 1 && (best < 0 || absgreater<W>(y, bx))) {
+            if (j == k + 1 && (pivoting || i == k + 1) && (best < 0 || absgreater<W>(y, bx))) {
                 best = i;
                 bx = y;
             }
@@ -602,9 +603,9 @@ __global__ void lu_laswp_kernel(BMat A, int64_t n, int64_t j0, int64_t je, const
 // ================================================================ launchers
 template <int W>
 void launch_lu_pivot(BMat A, int64_t n, int64_t k, int64_t *piv, int p, DevStatus *st,
-                     cudaStream_t s, int64_t c0, int64_t c1)
+                     cudaStream_t s, int64_t c0, int64_t c1, bool pivoting)
 {
-    lu_pivot_kernel<W><<<1, LuCfg<W>::PIVOT, 0, s>>>(A, n, k, piv, p, st, c0, c1);
+    lu_pivot_kernel<W><<<1, LuCfg<W>::PIVOT, 0, s>>>(A, pivoting ? n : k + 1, k, piv, p, st, c0, c1);
 }
 
 template <int W>
@@ -654,7 +655,7 @@ bool lu_fused_ok(int64_t panel)
 
 template <int W>
 void launch_lu_column(BMat A, int64_t n, int64_t j0, int64_t k, int64_t je, int64_t *piv, int p,
-                      DevStatus *st, int64_t *cand, unsigned *ticket, cudaStream_t s)
+                      DevStatus *st, int64_t *cand, unsigned *ticket, cudaStream_t s, bool pivoting)
 {
     if constexpr (W <= 32) {
         const int64_t rows = n - k - 1;
@@ -662,7 +663,7 @@ void launch_lu_column(BMat A, int64_t n, int64_t j0, int64_t k, int64_t je, int6
         int64_t g = (rows + LU_COL_WARPS - 1) / LU_COL_WARPS;
         if (g > LU_COL_MAX_CTAS) g = LU_COL_MAX_CTAS;
         lu_column_kernel<W><<<(unsigned)g, LU_COL_WARPS * 32, 0, s>>>(A, n, j0, k, je, piv, p, st, cand,
-                                                                     ticket);
+                                                                     ticket, pivoting ? 1 : 0);
     }
 }
 
@@ -687,7 +688,7 @@ void launch_lu_u12(BMat A, int64_t n, int64_t j0, int64_t je, int p, DevStatus *
 
 #define MPG_INSTANTIATE_LU(W)                                                                   \
     template void launch_lu_pivot<W>(BMat, int64_t, int64_t, int64_t *, int, DevStatus *,       \
-                                     cudaStream_t, int64_t, int64_t);                           \
+                                     cudaStream_t, int64_t, int64_t, bool);                     \
     template void launch_lu_divide<W>(BMat, int64_t, int64_t, int, cudaStream_t);               \
     template void launch_lu_rank1<W>(BMat, int64_t, int64_t, int64_t, int64_t, int64_t, int,    \
                                      DevStatus *, cudaStream_t);                                \
@@ -695,7 +696,7 @@ void launch_lu_u12(BMat A, int64_t n, int64_t j0, int64_t je, int p, DevStatus *
                                      int64_t *, int, DevStatus *, cudaStream_t);                \
     template bool lu_fused_ok<W>(int64_t);                                                      \
     template void launch_lu_column<W>(BMat, int64_t, int64_t, int64_t, int64_t, int64_t *, int, \
-                                      DevStatus *, int64_t *, unsigned *, cudaStream_t);        \
+                                      DevStatus *, int64_t *, unsigned *, cudaStream_t, bool);  \
     template void launch_lu_laswp<W>(BMat, int64_t, int64_t, int64_t, const int64_t *, int,     \
                                      cudaStream_t);                                             \
     template void launch_lu_u12<W>(BMat, int64_t, int64_t, int64_t, int, DevStatus *, cudaStream_t);

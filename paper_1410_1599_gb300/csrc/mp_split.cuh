@@ -17,6 +17,13 @@
 // 3. Recombination (split_finish_kernel): the exact sum
 //    sum_s D_s 256^s * 2^(emaxA(i) + emaxB(j) - 2F) is carried into a
 //    two's complement fixed-point integer and rounded once to p bits.
+// Truncation: the diagonals s < s0 lie far below the rounding position of a
+// typical output and are skipped.  Their sum is below
+// l S 2^14 256^s0 <= 2^eb (|digit product| <= 2^14, at most S pairs per
+// diagonal, sum_{s<s0} 256^s < 256^s0).  The rounding of the kept sum V is
+// then the rounding of the exact sum unless V +- 2^eb reaches a midpoint
+// between p-bit neighbours; such outputs (and those too close to zero) are
+// recomputed exactly (a Ziv-style test: the result is identical either way).
 // No floating-point rounding enters anywhere: every fp16 and fp32 value is
 // an exactly represented integer.
 #pragma once
@@ -150,9 +157,27 @@ __global__ void split_prep_cols(BMat B, int64_t l, int64_t n, int64_t lp, int p,
     }
 }
 
-// value = acc (two's complement, na words) * 2^e0, rounded once to p bits
+// bits [lo, hi) of acc (na words, lo >= 0) all equal to v (0 or 1)
+MP_DEV bool bits_all(const uint32_t *acc, int na, int64_t lo, int64_t hi, uint32_t v)
+{
+    const uint32_t want = v ? 0xffffffffu : 0u;
+    for (int64_t b = lo; b < hi;) {
+        const int w = (int)(b >> 5), o = (int)(b & 31);
+        const int64_t take = (hi - b) < (32 - o) ? (hi - b) : (32 - o);
+        const uint32_t mask = (take == 32 ? 0xffffffffu : ((1u << take) - 1u)) << o;
+        const uint32_t x = w < na ? acc[w] : 0u;
+        if ((x & mask) != (want & mask)) return false;
+        b += take;
+    }
+    return true;
+}
+
+// value = acc (two's complement, na words) * 2^e0, rounded once to p bits.
+// With ebits >= 0 the exact value is acc + d for an unknown |d| < 2^ebits;
+// returns false (c untouched) when that leaves the rounding open.
 template <int W>
-MP_DEV void round_fixed(uint32_t *acc, int na, int64_t e0, const RoundSpec &rs, Mp<W> &c)
+MP_DEV bool round_fixed(uint32_t *acc, int na, int64_t e0, const RoundSpec &rs, Mp<W> &c,
+                        int64_t ebits = -1)
 {
     set_zero<W>(c, 0u);
     const bool negative = (acc[na - 1] >> 31) != 0u;
@@ -166,9 +191,16 @@ MP_DEV void round_fixed(uint32_t *acc, int na, int64_t e0, const RoundSpec &rs, 
     }
     int top = na - 1;
     while (top >= 0 && acc[top] == 0u) --top;
-    if (top < 0) return;                                  // exact zero: +0
+    if (top < 0) return ebits < 0;                        // exact zero: +0
     const int lz = __clz(acc[top]);
     const int64_t lb = 32 * (int64_t)top + (31 - lz);
+    if (ebits >= 0) {
+        // round bit at lb - p; the midpoints have it set and zeros below
+        const int64_t rb = lb - rs.p;
+        if (rb < ebits + 2) return false;
+        const uint32_t rbit = (acc[rb >> 5] >> (rb & 31)) & 1u;
+        if (bits_all(acc, na, ebits, rb, rbit ? 0u : 1u)) return false;
+    }
     auto bits_at = [&](int64_t lo) -> uint32_t {
         if (lo <= -32) return 0u;
         if (lo < 0) return acc[0] << (-lo);
@@ -191,18 +223,22 @@ MP_DEV void round_fixed(uint32_t *acc, int na, int64_t e0, const RoundSpec &rs, 
     c.e = e0 + lb + 1;
     c.s = negative ? 1u : 0u;
     round_mant<W>(c.m, c.e, below, sticky, rs);
+    return true;
 }
 
 template <int W> struct SplitCfg {
     static constexpr int NWD = (2 * ((32 * W + SPLIT_SB + 7) / 8 + 1) + 8) / 4 + 4;
 };
 
-// c_ij from the diagonal sums (rows/columns beyond the spread budget skipped)
+// c_ij from the diagonal sums D (planes s0 .. 2S-2; rows/columns beyond the
+// spread budget skipped).  ebits >= 0: the skipped diagonals sum to less
+// than 2^ebits; outputs whose rounding that leaves open go to list.
 template <int W>
 __global__ void __launch_bounds__(64)
-split_finish_kernel(const long long *__restrict__ D, int64_t m, int64_t n, int S, int p,
-                    const int64_t *emaxA, const int64_t *emaxB, const uint8_t *wideA,
-                    const uint8_t *wideB, BMat C, DevStatus *status)
+split_finish_kernel(const long long *__restrict__ D, int64_t m, int64_t n, int S, int p, int s0,
+                    int64_t ebits, const int64_t *emaxA, const int64_t *emaxB, const uint8_t *wideA,
+                    const uint8_t *wideB, BMat C, int64_t *list, unsigned long long *count,
+                    DevStatus *status)
 {
     constexpr int NWD = SplitCfg<W>::NWD;
     const RoundSpec rs = make_spec<W>(p);
@@ -221,8 +257,8 @@ split_finish_kernel(const long long *__restrict__ D, int64_t m, int64_t n, int S
         for (int w = 0; w < NWD; ++w) acc[w] = 0u;
         long long carry = 0;
         const int nd = 2 * S - 1;
-        for (int s = 0; s < nd; ++s) {
-            const long long v = carry + D[(int64_t)s * total + t];
+        for (int s = s0; s < nd; ++s) {
+            const long long v = carry + D[(int64_t)(s - s0) * total + t];
             acc[s >> 2] |= ((uint32_t)v & 0xffu) << (8 * (s & 3));
             carry = v >> 8;                                   // arithmetic: floor division
         }
@@ -232,7 +268,10 @@ split_finish_kernel(const long long *__restrict__ D, int64_t m, int64_t n, int S
             carry >>= 8;
         }
         const int64_t F = p + SPLIT_SB;
-        round_fixed<W>(acc, NWD, emaxA[i] + emaxB[j] - 2 * F, rs, c);
+        if (!round_fixed<W>(acc, NWD, emaxA[i] + emaxB[j] - 2 * F, rs, c, ebits)) {
+            list[atomicAdd(count, 1ull)] = t;                 // decided by the exact kernel
+            continue;
+        }
         if (st<W>(c, C, 0, i, j, rs.L)) flag(status, ST_RANGE);
     }
 }
@@ -249,20 +288,21 @@ void launch_split_prep(BMat A, BMat B, int64_t m, int64_t l, int64_t n, int p, _
 }
 
 template <int W>
-void launch_split_finish(const long long *D, int64_t m, int64_t n, int p, const int64_t *ea,
-                         const int64_t *eb, const uint8_t *wa, const uint8_t *wb, BMat C,
-                         DevStatus *st, cudaStream_t s)
+void launch_split_finish(const long long *D, int64_t m, int64_t n, int p, int s0, int64_t ebits,
+                         const int64_t *ea, const int64_t *eb, const uint8_t *wa, const uint8_t *wb,
+                         BMat C, int64_t *list, unsigned long long *count, DevStatus *st, cudaStream_t s)
 {
-    split_finish_kernel<W><<<grid_for(m * n, 64), 64, 0, s>>>(D, m, n, split_digits(p), p, ea, eb,
-                                                               wa, wb, C, st);
+    split_finish_kernel<W><<<grid_for(m * n, 64), 64, 0, s>>>(D, m, n, split_digits(p), p, s0, ebits, ea,
+                                                               eb, wa, wb, C, list, count, st);
 }
 
 #define MPG_INSTANTIATE_SPLIT(W)                                                                \
     template void launch_split_prep<W>(BMat, BMat, int64_t, int64_t, int64_t, int, __half *,    \
                                        __half *, int64_t *, int64_t *, uint8_t *, uint8_t *,    \
                                        cudaStream_t);                                           \
-    template void launch_split_finish<W>(const long long *, int64_t, int64_t, int,              \
+    template void launch_split_finish<W>(const long long *, int64_t, int64_t, int, int, int64_t, \
                                          const int64_t *, const int64_t *, const uint8_t *,     \
-                                         const uint8_t *, BMat, DevStatus *, cudaStream_t);
+                                         const uint8_t *, BMat, int64_t *, unsigned long long *, \
+                                         DevStatus *, cudaStream_t);
 
 }  // namespace mpg

@@ -37,6 +37,26 @@ namespace mpg {
 int split_digit_count(int p) { return split_digits(p); }
 int64_t split_row_pad(int64_t l) { return split_lpad(l); }
 
+// Lowest diagonal kept by the truncated form and the bound 2^ebits on the
+// skipped part (see mp_split.cuh).  A typical output's leading bit lies at
+// 2F - 2 or above (its largest products have both factors aligned to the top
+// digit); the skipped part is placed SPLIT_GUARD bits under that output's
+// round bit at 2F - 2 - p, so an output must sit about SPLIT_GUARD - 32 bits
+// lower before its rounding is left open with any real probability.
+int split_first_diagonal(int p, int64_t l, int64_t *ebits)
+{
+    constexpr int SPLIT_GUARD = 72;
+    const int S = split_digits(p);
+    const int64_t F = p + SPLIT_SB;
+    int hb = 0;                                          // ceil(log2(lp S))
+    while (((int64_t)1 << hb) < split_lpad(l) * S) ++hb;
+    const int64_t room = 2 * F - 2 - p - SPLIT_GUARD - hb - 14;
+    int s0 = room > 0 ? (int)(room / 8) : 0;
+    if (s0 > 2 * S - 2) s0 = 2 * S - 2;
+    *ebits = s0 > 0 ? hb + 14 + 8 * (int64_t)s0 : -1;
+    return s0;
+}
+
 namespace {
 
 constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
@@ -60,7 +80,7 @@ constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024;
 constexpr long long WAIT_LIMIT = 4000000000ll;                  // ~2 s of clock
 
 struct Sched {
-    int S, groups, nkb;
+    int S, s0, groups, nkb;     // diagonals s0 .. 2S-2 are computed
     int64_t m, n, tiles_n2;     // tiles_n2: groups of CC 256-column tiles
     int64_t nitems;             // (2 x 2 tile block, diagonal group) work items
 };
@@ -157,7 +177,7 @@ split_slice_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_co
             for (int64_t it = cl0; it < sc.nitems && !abort_flag; it += ncl) {
             int64_t i0, j0;
             const int grp = item(it, i0, j0);
-            for (int s = grp; s <= 2 * S - 2 && !abort_flag; s += sc.groups) {
+            for (int s = sc.s0 + grp; s <= 2 * S - 2 && !abort_flag; s += sc.groups) {
                 int u0, u1;
                 diag_range(s, S, u0, u1);
                 const int total = (u1 - u0 + 1) * nkb;
@@ -196,7 +216,7 @@ split_slice_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_co
             for (int64_t it = cl0; it < sc.nitems && !abort_flag; it += ncl) {
             int64_t i0, j0;
             const int grp = item(it, i0, j0);
-            for (int s = grp; s <= 2 * S - 2 && !abort_flag; s += sc.groups) {
+            for (int s = sc.s0 + grp; s <= 2 * S - 2 && !abort_flag; s += sc.groups) {
                 int u0, u1;
                 diag_range(s, S, u0, u1);
                 const int total = (u1 - u0 + 1) * nkb;
@@ -250,12 +270,12 @@ split_slice_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_co
         int64_t i0, j0;
         const int grp = item(it, i0, j0);
         const int64_t i = i0 + quarter * 32 + lane;
-        for (int s = grp; s <= 2 * S - 2 && !abort_flag; s += sc.groups) {
+        for (int s = sc.s0 + grp; s <= 2 * S - 2 && !abort_flag; s += sc.groups) {
             int u0, u1;
             diag_range(s, S, u0, u1);
             const int total = (u1 - u0 + 1) * nkb;
             const int nch = (total + KB_PER_CHUNK - 1) / KB_PER_CHUNK;
-            long long *Ds = D + (int64_t)s * sc.m * sc.n;
+            long long *Ds = D + (int64_t)(s - sc.s0) * sc.m * sc.n;
             // segments of at most 255 chunks: int32 sums, then one int64 flush
             for (int seg = 0; seg < nch && !abort_flag; seg += CHUNKS_PER_I32) {
                 const int seg_end = seg + CHUNKS_PER_I32 < nch ? seg + CHUNKS_PER_I32 : nch;
@@ -329,9 +349,10 @@ bool make_map(CUtensorMap *map, const __half *base, int64_t rows, int64_t lp, ui
 }  // namespace
 
 int launch_split_slices(const __half *pa, const __half *pb, int64_t m, int64_t l, int64_t n, int p,
-                        long long *D, DevStatus *st, cudaStream_t s)
+                        int s0, long long *D, DevStatus *st, cudaStream_t s)
 {
     const int S = split_digits(p);
+    if (s0 < 0 || s0 > 2 * S - 2) return MP_ERR_ARG;
     const int64_t lp = split_lpad(l);
     // TMA: 16-byte aligned bases and row strides (lp is a multiple of 32)
     if (((uintptr_t)pa & 15) || ((uintptr_t)pb & 15) || (lp * 2) % 16) return MP_ERR_ARG;
@@ -354,6 +375,7 @@ int launch_split_slices(const __half *pa, const __half *pb, int64_t m, int64_t l
     }
     Sched sc;
     sc.S = S;
+    sc.s0 = s0;
     sc.nkb = (int)((lp + BK - 1) / BK);
     sc.m = m;
     sc.n = n;
@@ -384,7 +406,7 @@ int launch_split_slices(const __half *pa, const __half *pb, int64_t m, int64_t l
     }
     const int64_t clusters = resident;
     int groups = 1;
-    while (quads * groups < 8 * clusters && groups * 2 <= 2 * S - 1) groups *= 2;
+    while (quads * groups < 8 * clusters && groups * 2 <= 2 * S - 1 - s0) groups *= 2;
     sc.groups = groups;
     sc.nitems = quads * groups;
     const int64_t ncl = sc.nitems < clusters ? sc.nitems : clusters;

@@ -28,3 +28,33 @@ def gemm(A: HostMP, B: HostMP, algo, cutoff=64):
     mp.mpgemm(dA, dB, dC, algo, cutoff)
     mp.check_status("gemm")
     return dC.to_host()
+
+
+def rel_errors_vs_rows(C: "mp.DeviceMP", R) -> np.ndarray:
+    """|c~_ij - r_i| / |r_i| for a device result C (m x n, p bits) against
+    reference rows R (m x 1 at q >= p bits, host): C is widened to q bits
+    (exactly) and the difference is taken on the device at q bits, so the
+    error is read to ~2^(p-q) relative accuracy from the top limb."""
+    import torch
+
+    m, n, q = C.rows, C.cols, R.p
+    torch.cuda.synchronize()
+    C2 = mp.DeviceMP.empty(m, n, q)
+    mp.convert(C, C2)
+    dR = mp.DeviceMP.from_host(HostMP(np.asarray(R.limb), np.asarray(R.exp), np.asarray(R.sign), q))
+    Rf = mp.DeviceMP(dR.limb.expand(-1, -1, n).contiguous(), dR.exp.expand(-1, n).contiguous(),
+                     dR.sign.expand(-1, n).contiguous(), q, m, n)
+    torch.cuda.synchronize()
+    D = mp.DeviceMP.empty(m, n, q)
+    mp.elementwise(mp.OP_SUB, C2, Rf, D)
+    mp.check_status("error difference")
+    torch.cuda.synchronize()
+    top = D.limb[0].cpu().numpy().view(np.uint64).astype(np.float64) * 2.0 ** -64
+    e = D.exp.cpu().numpy()
+    rtop = np.asarray(R.limb)[0, :, 0].astype(np.float64) * 2.0 ** -64
+    re = np.asarray(R.exp)[:, 0]
+    zero = e == np.iinfo(np.int64).min
+    with np.errstate(divide="ignore", over="ignore"):
+        lg = np.log2(np.where(zero, 1.0, top)) + np.where(zero, 0, e).astype(np.float64) \
+            - (np.log2(rtop) + re.astype(np.float64))[:, None]
+    return np.where(zero, 0.0, np.exp2(lg))

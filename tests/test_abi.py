@@ -36,6 +36,10 @@ def test_host_only_calls():
     assert lib.mp_strerror(-3) == b"zero pivot: matrix is singular"
     assert lib.mp_set_odd_policy(7) == -1
     assert lib.mp_set_lu(0, 0, 64) == -1
+    assert lib.mp_set_lu_pivoting(2) == -1
+    assert lib.mp_set_lu_pivoting(0) == 0 and lib.mp_set_lu_pivoting(1) == 0
+    assert lib.mp_set_split_truncation(3) == -1
+    assert lib.mp_set_split_truncation(0) == 0 and lib.mp_set_split_truncation(1) == 0
     # Simple and Block need no workspace; the recursion does
     assert lib.mpgemm_workspace_size(1024, 1024, 1024, 512, 0, 64) == 0
     assert lib.mpgemm_workspace_size(1024, 1024, 1024, 512, 3, 64) > 0

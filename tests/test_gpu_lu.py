@@ -12,18 +12,20 @@ from tests.gpu_util import assert_bits_equal, dev
 pytestmark = pytest.mark.gpu
 
 
-def gpu_lu(A, b, panel, algo, cutoff):
+def gpu_lu(A, b, panel, algo, cutoff, pivoting=True):
     n = A.shape[0]
     dA = dev(A)
     db = dev(b)
     dx = mp.DeviceMP.empty(n, 1, A.p)
     piv = torch.zeros(n, dtype=torch.int64, device="cuda")
     mp.set_lu(panel, algo, cutoff)
+    mp.set_lu_pivoting(pivoting)
     try:
         mp.mplu(dA, piv, db, dx)
         rc = mp.sync_status()
     finally:
         mp.set_lu(128, mp.SIMPLE, 64)
+        mp.set_lu_pivoting(True)
     return dA.to_host(), piv.cpu().numpy(), dx.to_host(), rc
 
 
@@ -33,12 +35,12 @@ def b_of(A):
     return orc.gemm(orc.SIMPLE, A, gen.ones(n, 1, A.p))
 
 
-def check(A, panel, algo, cutoff):
+def check(A, panel, algo, cutoff, pivoting=True):
     b = b_of(A)
     bB = gen.HostMP(b.limb, b.exp, b.sign, b.p)
-    F, piv, x, rc = gpu_lu(A, bB, panel, algo, cutoff)
+    F, piv, x, rc = gpu_lu(A, bB, panel, algo, cutoff, pivoting)
     assert rc == 0
-    Fo, pivo, rco = orc.lu(A, panel=panel, algo=algo, cutoff=cutoff)
+    Fo, pivo, rco = orc.lu(A, panel=panel, algo=algo, cutoff=cutoff, pivoting=pivoting)
     assert rco == 0
     assert list(piv) == list(pivo)
     assert_bits_equal(F, Fo, "factors")
@@ -79,3 +81,27 @@ def test_singular_reported():
     _, _, _, rc = gpu_lu(A, b, 4, mp.SIMPLE, 64)
     assert rc == -3
     assert mp.load_library().mp_singular_column() == 5
+
+
+@pytest.mark.parametrize("p,n", [(256, 90), (1024, 70), (2048, 40)])
+@pytest.mark.parametrize("panel", [1, 8, 128])
+def test_unpivoted_paper_lu(p, n, panel):
+    """The paper's LU without pivoting (Sec. 4) on a random matrix, where
+    partial pivoting would exchange rows: factors, piv = identity and the
+    solution bit for bit (fused column steps up to 1024 bits, separate
+    pivot / divide / rank-1 launches at 2048)."""
+    A = gen.uniform_pm1(n, n, p, 31)
+    check(A, panel, mp.WINOGRAD, 8, pivoting=False)
+
+
+def test_unpivoted_zero_pivot_reported():
+    p = 256
+    A = gen.uniform_pm1(10, 10, p, 32)
+    A.exp[0, 0] = gen.EXP_ZERO                   # a_11 = 0: regular, but no pivot without exchanges
+    A.limb[:, 0, 0] = 0
+    b = gen.uniform_pm1(10, 1, p, 33)
+    _, _, _, rc = gpu_lu(A, b, 4, mp.SIMPLE, 64, pivoting=False)
+    assert rc == -3
+    assert mp.load_library().mp_singular_column() == 0
+    _, _, _, rc = gpu_lu(A, b, 4, mp.SIMPLE, 64, pivoting=True)
+    assert rc == 0

@@ -69,3 +69,72 @@ def test_split_many_chunks_per_diagonal():
     assert_bits_equal(s, gemm(A, B, mp.EXACT), "split vs exact kernel, long k")
     rows, cols = np.array([0, 7, 19]), np.array([0, 11, 23])
     assert_bits_equal(s.sub(rows, cols), orc.dot_exact(A, B, rows=rows, cols=cols), "oracle sample, long k")
+
+
+def _split(A, B, truncate):
+    mp.set_split_truncation(truncate)
+    try:
+        out = gemm(A, B, mp.SPLIT)
+        fb = mp.split_fallbacks()
+    finally:
+        mp.set_split_truncation(True)
+    return out, fb
+
+
+@pytest.mark.parametrize("p", [53, 128, 512, 1024, 2048])
+def test_truncated_equals_full_split(p):
+    """Skipping the low diagonals changes no bit: truncated and full split
+    forms agree everywhere, and on these inputs (exponents in [-16, 16]) no
+    output needs the exact fallback."""
+    m, l, n = (70, 200, 90) if p >= 1024 else (150, 300, 140)
+    A = gen.uniform_pm1(m, l, p, 81, -16, 16)
+    B = gen.uniform_pm1(l, n, p, 82, -16, 16)
+    full, fb0 = _split(A, B, False)
+    trunc, fb1 = _split(A, B, True)
+    assert fb0 == 0 and fb1 == 0
+    assert_bits_equal(trunc, full, "truncated vs full split p=%d" % p)
+    rows, cols = np.arange(0, m, 7), np.arange(3, n, 11)
+    assert_bits_equal(trunc.sub(rows, cols), orc.dot_exact(A, B, rows=rows, cols=cols), "oracle sample")
+
+
+def _cancelling(m, h, n, p, seed, rows_cancel):
+    """A = [X, X'] with X' = X on the rows in rows_cancel, B = [Y; -(1 - 2^-100) Y]
+    with small integers Y: on those rows the exact sum is 2^-100 sum_k x_ik y_kj,
+    about 100 bits under the products' own size (and every exponent spread
+    stays within the 64-bit budget); other rows take an independent X'."""
+    X = gen.uniform_pm1(m, h, p, seed)
+    X2 = gen.uniform_pm1(m, h, p, seed + 1)
+    Y = gen.small_ints(h, n, p, seed + 2, 20)
+    A = gen.HostMP.zeros(m, 2 * h, p)
+    A.limb[:, :, :h], A.exp[:, :h], A.sign[:, :h] = X.limb, X.exp, X.sign
+    A.limb[:, :, h:], A.exp[:, h:], A.sign[:, h:] = X2.limb, X2.exp, X2.sign
+    for i in rows_cancel:
+        A.limb[:, i, h:], A.exp[i, h:], A.sign[i, h:] = X.limb[:, i], X.exp[i], X.sign[i]
+    vals = []
+    for k in range(h):
+        for j in range(n):
+            y = int(gen.entry_fraction(Y, k, j))
+            vals.append((0 if y <= 0 else 1, abs(y) * ((1 << 100) - 1), 100))
+    Yn = gen.from_exact_ints(vals, p, (h, n))
+    B = gen.HostMP.zeros(2 * h, n, p)
+    B.limb[:, :h], B.exp[:h], B.sign[:h] = Y.limb, Y.exp, Y.sign
+    B.limb[:, h:], B.exp[h:], B.sign[h:] = Yn.limb, Yn.exp, Yn.sign
+    return A, B
+
+
+@pytest.mark.parametrize("p", [128, 1024])
+def test_truncation_falls_back_on_cancellation(p):
+    """Outputs whose exact value cancels to ~2^-100 of the products are left
+    undecided by the truncated sum and recomputed by the exact kernel: the
+    fallback count is exactly those outputs, and every bit still equals the
+    oracle's exact dot product (and the full split form's)."""
+    m, h, n = 24, 40, 19
+    cancel = list(range(0, m, 2))
+    A, B = _cancelling(m, h, n, p, 90, cancel)
+    got, fb = _split(A, B, True)
+    assert fb == len(cancel) * n
+    want = orc.dot_exact(A, B)
+    assert_bits_equal(got, want, "truncated split with cancellation")
+    full, fb0 = _split(A, B, False)
+    assert fb0 == 0
+    assert_bits_equal(full, want, "full split with cancellation")
