@@ -28,7 +28,7 @@
 #define ORC_EXP_ZERO INT64_MIN
 #define ORC_EXP_MAX  ((int64_t)1 << 62)
 #define ORC_EXP_MIN  (-((int64_t)1 << 62))
-#define ORC_MAXW     128            /* 32-bit words: mantissas up to 4096 bits */
+#define ORC_MAXW     272            /* 32-bit words: mantissas up to 8704 bits */
 #define ORC_MAXP     (32 * ORC_MAXW)
 
 typedef struct {

@@ -85,6 +85,28 @@ def test_integer_inputs_reproduce_simple(algo, policy, dims, cutoff):
     assert np.array_equal(S.sign, R.sign)
 
 
+@pytest.mark.parametrize("p", [4000, 8650])
+def test_wide_precision_integer_and_replay(p):
+    """Above 2048 bits: Strassen and Winograd reproduce Simple on integer
+    inputs, and an mpmath replay of Winograd's printed formulas on random
+    p-bit inputs gives the same bits."""
+    A = gen.small_ints(9, 11, p, 33, bits=20)
+    B = gen.small_ints(11, 10, p, 34, bits=20)
+    S = orc.gemm(orc.SIMPLE, A, B)
+    for algo in (orc.STRASSEN, orc.WINOGRAD):
+        R = orc.gemm(algo, A, B, cutoff=2, policy=orc.MIXED)
+        assert np.array_equal(S.limb, R.limb) and np.array_equal(S.exp, R.exp)
+    X = gen.uniform_pm1(5, 7, p, 35, -8, 8)
+    Y = gen.uniform_pm1(7, 6, p, 36, -8, 8)
+    for algo in (orc.SIMPLE, orc.WINOGRAD):
+        R = orc.gemm(algo, X, Y, cutoff=2, policy=orc.PEEL)
+        ref = _simple(_mat(X), _mat(Y), p) if algo == orc.SIMPLE else \
+            _rec(_mat(X), _mat(Y), p, algo, 2, orc.PEEL, 5, 7, 6)
+        for i in range(5):
+            for j in range(6):
+                assert entry_mpf(R, i, j) == ref[i][j], (algo, i, j)
+
+
 def test_block_equals_simple_and_identity():
     p = 256
     A = gen.uniform_pm1(45, 37, p, 41, -16, 16)

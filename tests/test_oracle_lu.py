@@ -45,8 +45,9 @@ def _factorable(n, p, seed):
 
 @pytest.mark.parametrize("panel", [1, 3, 8, 128])
 @pytest.mark.parametrize("algo,cutoff", [(orc.SIMPLE, 64), (orc.STRASSEN, 2), (orc.WINOGRAD, 2)])
-def test_exactly_factorable(panel, algo, cutoff):
-    n, p = 13, 256
+@pytest.mark.parametrize("p", [256, 8650])
+def test_exactly_factorable(panel, algo, cutoff, p):
+    n = 13
     A, Lf, U = _factorable(n, p, 3)
     F, piv, rc = orc.lu(A, panel=panel, algo=algo, cutoff=cutoff)
     assert rc == 0

@@ -48,11 +48,11 @@ def test_p53_matches_ieee_double(op):
     assert np.array_equal(got, ref), np.nonzero(got != ref)[0][:10]
 
 
-@pytest.mark.parametrize("p", [128, 200, 256, 512, 1024, 2048])
+@pytest.mark.parametrize("p", [128, 200, 256, 512, 1024, 2048, 4000, 8192, 8650, 8704])
 @pytest.mark.parametrize("op", ["add", "sub", "mul", "div"])
 def test_matches_mpmath(op, p):
     rnd = random.Random(p * 7 + len(op))
-    n = 300 if p <= 512 else 120
+    n = 300 if p <= 512 else (120 if p <= 2048 else 40)
     xs, ys = [], []
     for i in range(n):
         bx = rnd.randint(1, p)
