@@ -53,6 +53,8 @@ def parse():
                     help="only the other configurations' runs and the per-algorithm errors")
     ap.add_argument("--lu", action="store_true",
                     help="only the LU runs: n = --lu-n at 256 and 1024 bits, well-conditioned and Lotkin")
+    ap.add_argument("--lotkin", action="store_true",
+                    help="only the Lotkin LU at 8192 and 8650 bits (n = --lu-n)")
     ap.add_argument("--lu-sweep", action="store_true",
                     help="only the paper's LU experiment: no pivoting, K = 32 alpha, alpha = 1..10")
     ap.add_argument("--paper", action="store_true",
@@ -573,14 +575,18 @@ def lu_run(n, p, algo, panel=128, cutoff=64, kind="well"):
             "backward_error": back, "forward_error": fwd}
 
 
-def lu_sweep_run(n=1024, precs=(256, 1024), algos=(0, 2, 3), alphas=range(1, 11), seed=21):
+def lu_sweep_run(n=1024, precs=(256, 1024), algos=(0, 2, 3), alphas=range(1, 11), seed=21,
+                 kind="random", runs_for=None):
     """The paper's LU experiment (Sec. 4): no pivoting, a random matrix with
-    entries in [-1, 1) (seeded), x = [0, 1, ..., n-1], b = A x (Simple
-    product at p), block size K = alpha * 32 for alpha = 1..10, the
-    trailing update by Simple, Strassen or Winograd (n_min = 32); plus the
-    column-wise LU (one panel of n columns, no trailing product) as the
-    baseline.  Per run: seconds and the maximum relative error
-    max_i |x~_i - i| / i over i >= 1 (x~_0 enters as |x~_0|)."""
+    entries in [-1, 1) (seeded) or the Lotkin matrix, x = [0, 1, ..., n-1],
+    b = A x (Simple product at p), block size K = alpha * 32 for
+    alpha = 1..10, the trailing update by Simple, Strassen or Winograd
+    (n_min = 32); plus the column-wise LU (one panel of n columns, no
+    trailing product) as the baseline.  runs_for(p) may replace the run list
+    of a precision.  Per run: seconds and the maximum relative error
+    max_i |x~_i - i| / i over i >= 1 (x~_0 enters as |x~_0|), the
+    difference taken at 2p (exact widening) or, above 4352 bits, at p
+    (exact by Sterbenz's lemma while x~_i is within a factor 2 of i)."""
     import numpy as np
     import torch
 
@@ -592,14 +598,16 @@ def lu_sweep_run(n=1024, precs=(256, 1024), algos=(0, 2, 3), alphas=range(1, 11)
     mp.set_lu_pivoting(False)
     try:
         for p in precs:
-            A = gen.uniform_pm1(n, n, p, seed)
+            A = gen.uniform_pm1(n, n, p, seed) if kind == "random" else gen.lotkin(n, p)
             dA0 = mp.DeviceMP.from_host(A)
             dxt = mp.DeviceMP.from_host(gen.from_ints([[i] for i in range(n)], p))
             db = mp.DeviceMP.empty(n, 1, p)
             mp.mpgemm(dA0, dxt, db, mp.SIMPLE)
-            q = 2 * p
+            q = 2 * p if 2 * p <= 8704 else p
             wxt = mp.DeviceMP.from_host(gen.from_ints([[i] for i in range(n)], q))
             runs = [("columnwise", mp.SIMPLE, n)] + [(names[a], a, 32 * al) for a in algos for al in alphas]
+            if runs_for is not None:
+                runs = runs_for(p)
             for name, algo, K in runs:
                 dA = mp.DeviceMP.empty(n, n, p)
                 dA.limb.copy_(dA0.limb)
@@ -630,7 +638,19 @@ def lu_sweep_run(n=1024, precs=(256, 1024), algos=(0, 2, 3), alphas=range(1, 11)
     finally:
         mp.set_lu(128, mp.SIMPLE, 64)
         mp.set_lu_pivoting(True)
-    return {"n": n, "matrix": "uniform [-1,1), no pivoting", "x_true": "0..n-1", "runs": out}
+    return {"n": n, "matrix": ("uniform [-1,1)" if kind == "random" else "Lotkin") + ", no pivoting",
+            "x_true": "0..n-1", "runs": out}
+
+
+def lotkin_run(n=1024, alphas=(1, 2, 4, 8)):
+    """The paper's ill-conditioned case (Sec. 4, its Figure 2): the Lotkin
+    matrix without pivoting at 8192 bits (column-wise LU and Winograd
+    updates) and at 8650 bits (Winograd updates, the precision the paper
+    adds to recover the 138 digits Winograd loses)."""
+    def runs_for(p):
+        r = [("winograd", 3, 32 * a) for a in alphas]
+        return ([("columnwise", 0, n)] + r) if p == 8192 else r
+    return lu_sweep_run(n, precs=(8192, 8650), kind="lotkin", runs_for=runs_for)
 
 
 def serve_run(n_req, seed=11, slots=8, budget=150 << 30):
@@ -1056,6 +1076,13 @@ def main():
         libbuild.build()
         torch.cuda.set_device(local)
         print(json.dumps({"split_form": split_run(a.n if a.n != 2048 else 4096, a.prec if a.prec != 512 else 1024)}), flush=True)
+        return
+    if a.lotkin:
+        import torch
+        from paper_1410_1599_gb300 import build as libbuild
+        libbuild.build()
+        torch.cuda.set_device(local)
+        print(json.dumps({"lotkin": lotkin_run(a.lu_n)}), flush=True)
         return
     if a.lu_sweep:
         import torch

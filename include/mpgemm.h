@@ -50,7 +50,8 @@ extern "C" {
 
 #define MP_EXP_ZERO  INT64_MIN
 #define MP_PREC_MIN  2
-#define MP_PREC_MAX  2048
+#define MP_PREC_MAX  8704       /* Sec. 4 runs its ill-conditioned LU at 8192 and 8650 bits */
+#define MP_PREC_EXACT_MAX 2048  /* MP_EXACT and MP_SPLIT: MP_ERR_UNSUPPORTED above */
 
 typedef struct mpmat {
     int32_t   prec;      /* p, the mantissa precision in bits */
@@ -162,7 +163,10 @@ size_t mpgemm_workspace_size(int64_t m, int64_t l, int64_t n, int32_t prec,
  * MP_EXACT forms each dot product exactly in a fixed-point accumulator and
  * rounds once; an exact zero sum is +0; a row/column pair whose products'
  * exponents spread wider than the accumulator (about 2p bits) is left +0 and
- * mp_sync_status() returns MP_ERR_UNSUPPORTED.
+ * mp_sync_status() returns MP_ERR_UNSUPPORTED.  MP_EXACT and MP_SPLIT take
+ * prec <= MP_PREC_EXACT_MAX and return MP_ERR_UNSUPPORTED above it.
+ * Precisions above 2048 bits run the same algorithms with the numbers in
+ * local memory (a slower, wide capacity class).
  * C must not overlap A or B (MP_ERR_ARG).  l = 0 gives C = +0.
  */
 int mpgemm(int64_t m, int64_t l, int64_t n, int32_t prec, int32_t algo, int32_t cutoff,

@@ -77,7 +77,7 @@ DevStatus *status_ptr()
 
 int limbs_of(int p) { return (p + 63) / 64; }
 
-// word-capacity class: smallest W in {4, 8, 16, 32, 64} with 32 W >= 64 L
+// word-capacity class: smallest W in {4, 8, 16, 32, 64, BIG_W} with 32 W >= 64 L
 int wclass(int p)
 {
     const int L = limbs_of(p);
@@ -85,11 +85,27 @@ int wclass(int p)
     if (L <= 4) return 8;
     if (L <= 8) return 16;
     if (L <= 16) return 32;
-    return 64;
+    if (L <= 32) return 64;
+    return mpg::BIG_W;
 }
 
 template <typename F>
 void dispatch(int p, F &&f)
+{
+    switch (wclass(p)) {
+    case 4: f(std::integral_constant<int, 4>{}); break;
+    case 8: f(std::integral_constant<int, 8>{}); break;
+    case 16: f(std::integral_constant<int, 16>{}); break;
+    case 32: f(std::integral_constant<int, 32>{}); break;
+    case 64: f(std::integral_constant<int, 64>{}); break;
+    default: f(std::integral_constant<int, mpg::BIG_W>{}); break;
+    }
+}
+
+// the classes up to 2048 bits only (exact and split kernels); callers reject
+// wider precisions first
+template <typename F>
+void dispatch_narrow(int p, F &&f)
 {
     switch (wclass(p)) {
     case 4: f(std::integral_constant<int, 4>{}); break;
@@ -443,7 +459,7 @@ int run_split(int64_t m, int64_t l, int64_t n, int p, BMat A, BMat B, BMat C, Wo
     }
     {
         Prof pr(MP_K_SPLIT_AUX, (double)(m * l + l * n), s);
-        dispatch(p, [&](auto w) {
+        dispatch_narrow(p, [&](auto w) {
             launch_split_prep<decltype(w)::value>(A, B, m, l, n, p, pa, pb, ea, eb, wa, wb, s);
         });
     }
@@ -459,19 +475,19 @@ int run_split(int64_t m, int64_t l, int64_t n, int p, BMat A, BMat B, BMat C, Wo
     }
     {
         Prof pr(MP_K_SPLIT_AUX, (double)m * n, s);
-        dispatch(p, [&](auto w) {
+        dispatch_narrow(p, [&](auto w) {
             launch_split_finish<decltype(w)::value>(D, m, n, p, s0, ebits, ea, eb, wa, wb, C, list, count, st, s);
         });
     }
     if (ebits >= 0) {
         Prof pr(MP_K_SPLIT_AUX, 0.0, s);
-        dispatch(p, [&](auto w) {
+        dispatch_narrow(p, [&](auto w) {
             launch_gemm_exact_list<decltype(w)::value>(A, B, C, n, l, p, st, s, list, count);
         });
     }
     {
         Prof pr(MP_K_SPLIT_AUX, 0.0, s);
-        dispatch(p, [&](auto w) {
+        dispatch_narrow(p, [&](auto w) {
             launch_gemm_exact<decltype(w)::value>(A, B, C, m, l, n, p, st, s, wa, wb);
         });
     }
@@ -508,12 +524,13 @@ int gemm_core(int algo, int cutoff, int policy, int64_t m, int64_t l, int64_t n,
         });
         return launch_status();
     }
+    if ((algo == MP_SPLIT || algo == MP_EXACT) && p > MP_PREC_EXACT_MAX) return MP_ERR_UNSUPPORTED;
     if (algo == MP_SPLIT) {
         return run_split(m, l, n, p, A, B, C, ws, st, s);
     }
     if (algo == MP_EXACT) {
         Prof pr(MP_K_EXACT, (double)m * l * n, s);
-        dispatch(p, [&](auto w) {
+        dispatch_narrow(p, [&](auto w) {
             launch_gemm_exact<decltype(w)::value>(A, B, C, m, l, n, p, st, s);
         });
         return launch_status();

@@ -9,8 +9,16 @@
 // Every operation returns the exact result rounded once to p bits, ties to
 // even (arXiv 1410.1599, Sec. 1 and 3: MPFR semantics), so results do not
 // depend on W: a p-bit operation gives the same bits in any W >= 2*ceil(p/64).
+//
+// Classes up to W = 64 (2048 bits) are written for registers: every loop over
+// the words is unrolled so that indices are constants.  The wide class above
+// 2048 bits (W = BIG_W, the paper's precisions up to 8650 bits) keeps its
+// numbers in local memory and takes the same steps in plain loops (the
+// big_* routines below), which keeps its code small enough to compile.
 #pragma once
 #include <cstdint>
+
+#include "mp_internal.h"
 
 #define MP_DEV __device__ __forceinline__
 
@@ -18,6 +26,8 @@ namespace mpg {
 
 constexpr int64_t EXP_ZERO = INT64_MIN;
 constexpr int64_t EXP_LIMIT = (int64_t)1 << 62;
+template <int W>
+constexpr bool is_big() { return W > 64; }
 
 // ---------------------------------------------------------------- carry chains
 MP_DEV uint32_t add_cc(uint32_t a, uint32_t b) { uint32_t r; asm volatile("add.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b)); return r; }
@@ -62,10 +72,333 @@ struct Mp {
 template <int W>
 MP_DEV void set_zero(Mp<W> &x, uint32_t sign)
 {
+    if constexpr (is_big<W>()) {
+#pragma unroll 4
+        for (int i = 0; i < W; ++i) x.m[i] = 0u;
+    } else {
 #pragma unroll
-    for (int i = 0; i < W; ++i) x.m[i] = 0u;
+        for (int i = 0; i < W; ++i) x.m[i] = 0u;
+    }
     x.e = EXP_ZERO;
     x.s = sign;
+}
+
+// ------------------------------------------------------ wide class (W > 64)
+// The steps of round_mant, add_impl, mul_impl, div_impl and cmpabs below,
+// written as plain loops over the words (numbers in local memory).
+
+// round m (W words, top bit set) to p bits, nearest-even (see round_mant)
+template <int W>
+__device__ __noinline__ void big_round(uint32_t *m, int64_t &e, uint32_t below, bool sticky,
+                                       const RoundSpec &rs)
+{
+    uint32_t rbit, st, lsb;
+    if (rs.r == 0) {
+        rbit = below >> 31;
+        st = (below << 1) | (sticky ? 1u : 0u);
+        lsb = m[0] & 1u;
+    } else {
+        const int q = rs.r - 1, qw = q >> 5, qb = q & 31;
+        rbit = (m[qw] >> qb) & 1u;
+        st = below | (sticky ? 1u : 0u) | (m[qw] & ((1u << qb) - 1u));
+        for (int i = 0; i < qw; ++i) st |= m[i];
+        for (int i = 0; i < rs.rw; ++i) m[i] = 0u;
+        m[rs.rw] &= ~((1u << rs.rb) - 1u);
+        lsb = (m[rs.rw] >> rs.rb) & 1u;
+    }
+    if (rbit && (st | lsb)) {
+        uint64_t c = (uint64_t)1 << rs.rb;               // m += 2^r
+        for (int i = rs.rw; i < W && c; ++i) {
+            c += m[i];
+            m[i] = (uint32_t)c;
+            c >>= 32;
+        }
+        if (c) {                                         // carried out of the top
+            for (int i = 0; i < W; ++i) m[i] = 0u;
+            m[W - 1] = 0x80000000u;
+            e += 1;
+        }
+    }
+}
+
+// x (N words) >>= sh bits, 0 <= sh <= 32N; returns the OR of the bits shifted out
+MP_DEV uint32_t big_shr_sticky(uint32_t *x, int N, int sh)
+{
+    const int q = sh >> 5, b = sh & 31;
+    uint32_t st = 0u;
+    if (q >= N) {
+        for (int i = 0; i < N; ++i) {
+            st |= x[i];
+            x[i] = 0u;
+        }
+        return st;
+    }
+    for (int i = 0; i < q; ++i) st |= x[i];
+    for (int i = 0; i < N; ++i) x[i] = (i + q < N) ? x[i + q] : 0u;
+    st |= x[0] & ((1u << b) - 1u);
+    for (int i = 0; i < N - 1; ++i) x[i] = __funnelshift_r(x[i], x[i + 1], b);
+    x[N - 1] >>= b;
+    return st;
+}
+
+// x (N words) <<= sh bits, 0 <= sh < 32N
+MP_DEV void big_shl(uint32_t *x, int N, int sh)
+{
+    const int q = sh >> 5, b = sh & 31;
+    for (int i = N - 1; i >= 0; --i) x[i] = (i - q >= 0) ? x[i - q] : 0u;
+    for (int i = N - 1; i > 0; --i) x[i] = __funnelshift_l(x[i - 1], x[i], b);
+    x[0] <<= b;
+}
+
+// leading zero bits of an N-word number (32N when zero)
+MP_DEV int big_clz(const uint32_t *x, int N)
+{
+    for (int i = N - 1; i >= 0; --i)
+        if (x[i]) return 32 * (N - 1 - i) + __clz(x[i]);
+    return 32 * N;
+}
+
+template <int W>
+__device__ __noinline__ int big_cmpabs(const Mp<W> &a, const Mp<W> &b)
+{
+    const bool az = a.e == EXP_ZERO, bz = b.e == EXP_ZERO;
+    if (az | bz) return (az && bz) ? 0 : (az ? -1 : 1);
+    if (a.e != b.e) return a.e < b.e ? -1 : 1;
+    for (int i = W - 1; i >= 0; --i)
+        if (a.m[i] != b.m[i]) return a.m[i] < b.m[i] ? -1 : 1;
+    return 0;
+}
+
+// r = RN_p(x + (-1)^neg_y y), the steps of add_impl; r may alias x or y
+template <int W>
+__device__ __noinline__ void big_add(Mp<W> &r, const Mp<W> &x, const Mp<W> &y, uint32_t neg_y,
+                                     const RoundSpec &rs)
+{
+    const uint32_t ys = y.s ^ neg_y;
+    const bool xz = x.e == EXP_ZERO, yz = y.e == EXP_ZERO;
+    if (xz | yz) {
+        if (xz & yz) {
+            const uint32_t zs = x.s & ys;
+            for (int i = 0; i < W; ++i) r.m[i] = 0u;
+            r.e = EXP_ZERO;
+            r.s = zs;
+            return;
+        }
+        if (xz) {
+            for (int i = 0; i < W; ++i) r.m[i] = y.m[i];
+            r.e = y.e;
+            r.s = ys;
+        } else if (&r != &x) {
+            for (int i = 0; i < W; ++i) r.m[i] = x.m[i];
+            r.e = x.e;
+            r.s = x.s;
+        }
+        return;
+    }
+    int mc = 0;
+    for (int i = W - 1; i >= 0 && mc == 0; --i)
+        if (x.m[i] != y.m[i]) mc = x.m[i] < y.m[i] ? -1 : 1;
+    const bool sw = (y.e > x.e) || (y.e == x.e && mc < 0);
+    uint32_t X[W + 1], Y[W + 1];
+    X[0] = 0u;
+    Y[0] = 0u;
+    for (int i = 0; i < W; ++i) {
+        X[i + 1] = sw ? y.m[i] : x.m[i];
+        Y[i + 1] = sw ? x.m[i] : y.m[i];
+    }
+    int64_t e = sw ? y.e : x.e;
+    const int64_t d64 = sw ? (y.e - x.e) : (x.e - y.e);
+    const uint32_t sx = sw ? ys : x.s;
+    const uint32_t eff_sub = (x.s ^ ys) & 1u;
+    const int d = d64 > 32 * (W + 1) ? 32 * (W + 1) : (int)d64;
+    const uint32_t st = big_shr_sticky(Y, W + 1, d);
+    const uint32_t mask = 0u - eff_sub;
+    uint64_t c = eff_sub & (st == 0u ? 1u : 0u);
+    for (int i = 0; i <= W; ++i) {
+        c += (uint64_t)X[i] + (uint64_t)(Y[i] ^ mask);
+        X[i] = (uint32_t)c;
+        c >>= 32;
+    }
+    const uint32_t rsh = (eff_sub ^ 1u) & (uint32_t)c & 1u;
+    bool sticky = st != 0u;
+    if (rsh) {
+        sticky |= (X[0] & 1u) != 0u;
+        for (int i = 0; i < W; ++i) X[i] = __funnelshift_r(X[i], X[i + 1], 1);
+        X[W] = (X[W] >> 1) | 0x80000000u;
+        e += 1;
+    }
+    const int lz = big_clz(X, W + 1);
+    if (lz == 32 * (W + 1)) {                     // exact cancellation: +0
+        for (int i = 0; i < W; ++i) r.m[i] = 0u;
+        r.e = EXP_ZERO;
+        r.s = 0u;
+        return;
+    }
+    big_shl(X, W + 1, lz);
+    e -= lz;
+    for (int i = 0; i < W; ++i) r.m[i] = X[i + 1];
+    big_round<W>(r.m, e, X[0], sticky, rs);
+    r.e = e;
+    r.s = sx;
+}
+
+// r = RN_p(a * b) from the full 2W-word product; r may alias a or b
+template <int W>
+__device__ __noinline__ void big_mul(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, const RoundSpec &rs)
+{
+    const uint32_t s = a.s ^ b.s;
+    if (a.e == EXP_ZERO || b.e == EXP_ZERO) {
+        for (int i = 0; i < W; ++i) r.m[i] = 0u;
+        r.e = EXP_ZERO;
+        r.s = s;
+        return;
+    }
+    int64_t e = a.e + b.e;
+    // Schoolbook product, CH words of a at a time held in registers: rows of
+    // b run through a register window of CH + 1 words, and each finished
+    // window word is added into P (local memory) once, with a running carry,
+    // so P is touched once per CH partial products.
+    constexpr int CH = 16;
+    static_assert(W % CH == 0, "chunked product");
+    uint32_t P[2 * W];
+    for (int i = 0; i < 2 * W; ++i) P[i] = 0u;
+    for (int i0 = 0; i0 < W; i0 += CH) {
+        uint32_t ac[CH], w[CH + 1];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            ac[u] = a.m[i0 + u];
+            w[u] = 0u;
+        }
+        w[CH] = 0u;
+        uint64_t cp = 0;
+        for (int j = 0; j < W; ++j) {
+            const uint32_t bj = b.m[j];
+            uint64_t c = 0;
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                const uint64_t t = (uint64_t)ac[u] * bj + w[u] + c;
+                w[u] = (uint32_t)t;
+                c = t >> 32;
+            }
+            w[CH] = (uint32_t)c;
+            const uint64_t sm = (uint64_t)P[i0 + j] + w[0] + cp;   // position i0 + j is final
+            P[i0 + j] = (uint32_t)sm;
+            cp = sm >> 32;
+#pragma unroll
+            for (int u = 0; u < CH; ++u) w[u] = w[u + 1];
+            w[CH] = 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {                // the window's last words
+            const uint64_t sm = (uint64_t)P[i0 + W + u] + w[u] + cp;
+            P[i0 + W + u] = (uint32_t)sm;
+            cp = sm >> 32;
+        }
+        for (int k = i0 + W + CH; k < 2 * W && cp; ++k) {
+            const uint64_t sm = (uint64_t)P[k] + cp;
+            P[k] = (uint32_t)sm;
+            cp = sm >> 32;
+        }
+    }
+    uint32_t low = 0u;
+    for (int i = 0; i < W - 2; ++i) low |= P[i];
+    uint32_t below = P[W - 1], below2 = P[W - 2];
+    if (!(P[2 * W - 1] >> 31)) {                  // product in [1/4, 1/2): shift left one
+        for (int i = 2 * W - 1; i > W; --i) P[i] = __funnelshift_l(P[i - 1], P[i], 1);
+        P[W] = __funnelshift_l(below, P[W], 1);
+        below = __funnelshift_l(below2, below, 1);
+        below2 <<= 1;
+        e -= 1;
+    }
+    for (int i = 0; i < W; ++i) r.m[i] = P[W + i];
+    big_round<W>(r.m, e, below, (low | below2) != 0u, rs);
+    r.e = e;
+    r.s = s;
+}
+
+// r = RN_p(a / b), b != 0: the long division of div_impl
+template <int W>
+__device__ __noinline__ void big_div(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, const RoundSpec &rs)
+{
+    const uint32_t s = a.s ^ b.s;
+    if (a.e == EXP_ZERO || b.e == EXP_ZERO) {
+        for (int i = 0; i < W; ++i) r.m[i] = 0u;
+        r.e = EXP_ZERO;
+        r.s = s;
+        return;
+    }
+    uint32_t R[W + 1], Q[W + 2];
+    uint32_t br = 0u;
+    for (int i = 0; i < W; ++i) {                 // R = A - D when A >= D
+        const uint64_t df = (uint64_t)a.m[i] - b.m[i] - br;
+        R[i] = (uint32_t)df;
+        br = (uint32_t)(df >> 63);
+    }
+    const uint32_t q0 = br ? 0u : 1u;
+    if (!q0)
+        for (int i = 0; i < W; ++i) R[i] = a.m[i];
+    R[W] = 0u;
+    for (int i = 0; i < W + 2; ++i) Q[i] = 0u;
+    Q[0] = q0;
+    const uint32_t d1 = b.m[W - 1], d2 = b.m[W - 2];
+    const uint32_t v = (uint32_t)(0xffffffffffffffffull / d1 - 0x100000000ull);
+    for (int t = 0; t <= W; ++t) {
+        for (int i = W; i > 0; --i) R[i] = R[i - 1];
+        R[0] = 0u;
+        const uint32_t u1 = R[W], u0 = R[W - 1];
+        uint64_t qh, rh;
+        if (u1 >= d1) {
+            qh = 0xffffffffull;
+            rh = (((uint64_t)u1 << 32) | u0) - qh * d1;
+        } else {
+            const uint64_t tt = (uint64_t)v * u1 + (((uint64_t)u1 << 32) | u0);
+            uint32_t q1 = (uint32_t)(tt >> 32) + 1u;
+            const uint32_t ql = (uint32_t)tt;
+            uint32_t rr = u0 - q1 * d1;
+            if (rr > ql) { q1 -= 1u; rr += d1; }
+            if (rr >= d1) { q1 += 1u; rr -= d1; }
+            qh = q1;
+            rh = rr;
+        }
+        for (int c = 0; c < 2 && rh <= 0xffffffffull && qh * d2 > ((rh << 32) | R[W - 2]); ++c) {
+            --qh;
+            rh += d1;
+        }
+        const uint32_t q = (uint32_t)qh;
+        uint64_t cy = 0;
+        uint32_t bw = 0u;
+        for (int i = 0; i < W; ++i) {
+            const uint64_t pr = (uint64_t)b.m[i] * q + cy;
+            cy = pr >> 32;
+            const uint64_t df = (uint64_t)R[i] - (uint32_t)pr - bw;
+            R[i] = (uint32_t)df;
+            bw = (uint32_t)(df >> 63);
+        }
+        const uint64_t dt = (uint64_t)R[W] - cy - bw;
+        R[W] = (uint32_t)dt;
+        uint32_t qd = q;
+        if (dt >> 63) {                           // one too large: add D back
+            uint64_t c = 0;
+            for (int i = 0; i < W; ++i) {
+                c += (uint64_t)R[i] + b.m[i];
+                R[i] = (uint32_t)c;
+                c >>= 32;
+            }
+            R[W] += (uint32_t)c;
+            qd -= 1u;
+        }
+        for (int i = W + 1; i > 0; --i) Q[i] = Q[i - 1];
+        Q[0] = qd;
+    }
+    bool rem = false;
+    for (int i = 0; i < W; ++i) rem |= R[i] != 0u;
+    const int lz = q0 ? 31 : 32;
+    big_shl(Q, W + 2, lz);
+    int64_t e = a.e - b.e + 32 - lz;
+    for (int i = 0; i < W; ++i) r.m[i] = Q[i + 2];
+    big_round<W>(r.m, e, Q[1], rem || Q[0] != 0u, rs);
+    r.e = e;
+    r.s = s;
 }
 
 // ------------------------------------------------------------- load / store
@@ -75,7 +408,7 @@ template <int W>
 MP_DEV void load(Mp<W> &x, const uint64_t *__restrict__ limb, const int64_t *__restrict__ exp,
                  const int8_t *__restrict__ sign, int64_t off, int64_t plane, int L)
 {
-#pragma unroll
+#pragma unroll (is_big<W>() ? 4 : W / 2)
     for (int k = 0; k < W / 2; ++k) {
         uint64_t v = (k < L) ? __ldg(limb + (int64_t)k * plane + off) : 0ull;
         x.m[W - 1 - 2 * k] = (uint32_t)(v >> 32);
@@ -99,7 +432,7 @@ template <int W>
 MP_DEV void store(const Mp<W> &x, uint64_t *__restrict__ limb, int64_t *__restrict__ exp,
                   int8_t *__restrict__ sign, int64_t off, int64_t plane, int L)
 {
-#pragma unroll
+#pragma unroll (is_big<W>() ? 4 : W / 2)
     for (int k = 0; k < W / 2; ++k)
         if (k < L)
             limb[(int64_t)k * plane + off] =
@@ -121,8 +454,8 @@ MP_DEV bool out_of_range(const Mp<W> &x)
 // that.  Bits of m under the kept LSB are cleared.  A carry out of the top
 // renormalises to 1/2 and increments e.
 template <int W>
-MP_DEV void round_mant(uint32_t (&m)[W], int64_t &e, uint32_t below, bool sticky,
-                       const RoundSpec &rs)
+MP_DEV void round_mant_reg(uint32_t (&m)[W], int64_t &e, uint32_t below, bool sticky,
+                           const RoundSpec &rs)
 {
     if (rs.r == 0) {
         // p = 32 W: the kept LSB is bit 0 of m[0]; the round bit tops `below`
@@ -184,6 +517,14 @@ MP_DEV void round_mant(uint32_t (&m)[W], int64_t &e, uint32_t below, bool sticky
             e += 1;
         }
     }
+}
+
+template <int W>
+MP_DEV void round_mant(uint32_t (&m)[W], int64_t &e, uint32_t below, bool sticky,
+                       const RoundSpec &rs)
+{
+    if constexpr (is_big<W>()) big_round<W>(m, e, below, sticky, rs);
+    else round_mant_reg<W>(m, e, below, sticky, rs);
 }
 
 // ------------------------------------------------------------ multiplication
@@ -286,7 +627,7 @@ MP_DEV void mul_top(uint32_t (&hi)[W], uint32_t &pw1, uint32_t &pw2, bool &low_n
 
 // r = RN_p(a * b)
 template <int W>
-MP_DEV void mul_impl(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, const RoundSpec &rs)
+MP_DEV void mul_impl_reg(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, const RoundSpec &rs)
 {
     const uint32_t s = a.s ^ b.s;
     if (a.e == EXP_ZERO || b.e == EXP_ZERO) {
@@ -367,6 +708,13 @@ MP_DEV void mul_impl(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, const RoundSpec &
     }
     r.e = e;
     r.s = s;
+}
+
+template <int W>
+MP_DEV void mul_impl(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, const RoundSpec &rs)
+{
+    if constexpr (is_big<W>()) big_mul<W>(r, a, b, rs);
+    else mul_impl_reg<W>(r, a, b, rs);
 }
 
 // --------------------------------------------------------------- add / sub
@@ -464,7 +812,7 @@ MP_DEV int clz_words(const uint32_t (&x)[N])
 // is renormalised by one bit to the right (carry out of an addition) or by
 // the leading-zero count to the left (cancellation), then rounded once.
 template <int W>
-MP_DEV void add_impl(Mp<W> &r, const Mp<W> &x, const Mp<W> &y, uint32_t neg_y, const RoundSpec &rs)
+MP_DEV void add_impl_reg(Mp<W> &r, const Mp<W> &x, const Mp<W> &y, uint32_t neg_y, const RoundSpec &rs)
 {
     const uint32_t ys = y.s ^ neg_y;
     const bool xz = x.e == EXP_ZERO, yz = y.e == EXP_ZERO;
@@ -535,9 +883,16 @@ MP_DEV void add_impl(Mp<W> &r, const Mp<W> &x, const Mp<W> &y, uint32_t neg_y, c
     r.s = sx;
 }
 
+template <int W>
+MP_DEV void add_impl(Mp<W> &r, const Mp<W> &x, const Mp<W> &y, uint32_t neg_y, const RoundSpec &rs)
+{
+    if constexpr (is_big<W>()) big_add<W>(r, x, y, neg_y, rs);
+    else add_impl_reg<W>(r, x, y, neg_y, rs);
+}
+
 // |a| vs |b| (-1, 0, 1); zero is the smallest magnitude
 template <int W>
-MP_DEV int cmpabs(const Mp<W> &a, const Mp<W> &b)
+MP_DEV int cmpabs_reg(const Mp<W> &a, const Mp<W> &b)
 {
     const bool az = a.e == EXP_ZERO, bz = b.e == EXP_ZERO;
     if (az | bz) return (az && bz) ? 0 : (az ? -1 : 1);
@@ -549,12 +904,19 @@ MP_DEV int cmpabs(const Mp<W> &a, const Mp<W> &b)
     return c;
 }
 
+template <int W>
+MP_DEV int cmpabs(const Mp<W> &a, const Mp<W> &b)
+{
+    if constexpr (is_big<W>()) return big_cmpabs<W>(a, b);
+    else return cmpabs_reg<W>(a, b);
+}
+
 // --------------------------------------------------------------- division
 // r = RN_p(a / b), b != 0: exact long division of the mantissas (the
 // quotient of two fractions in [1/2, 1) lies in (1/2, 2)), then one rounding
 // with the remainder as sticky.
 template <int W>
-MP_DEV void div_impl(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, const RoundSpec &rs)
+MP_DEV void div_impl_reg(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, const RoundSpec &rs)
 {
     const uint32_t s = a.s ^ b.s;
     if (a.e == EXP_ZERO || b.e == EXP_ZERO) { set_zero<W>(r, s); return; }   // callers reject b = 0
@@ -649,6 +1011,13 @@ MP_DEV void div_impl(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, const RoundSpec &
     round_mant<W>(r.m, e, Q[1], rem || Q[0] != 0u, rs);
     r.e = e;
     r.s = s;
+}
+
+template <int W>
+MP_DEV void div_impl(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, const RoundSpec &rs)
+{
+    if constexpr (is_big<W>()) big_div<W>(r, a, b, rs);
+    else div_impl_reg<W>(r, a, b, rs);
 }
 
 // ------------------------------------------------------------ entry points

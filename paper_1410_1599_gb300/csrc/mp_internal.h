@@ -7,6 +7,9 @@
 
 namespace mpg {
 
+// capacity class above 2048 bits: 272 words (8704 bits)
+constexpr int BIG_W = 272;
+
 // A batch of equally shaped matrices in device memory.  Element (b, r, c):
 //   limb k : limb[b * bs_limb + k * plane + r * ld + c]
 //   exp    : exp [b * bs_es + r * ld + c],  sign likewise

@@ -21,7 +21,7 @@ template <int W>
 MP_DEV void ld(Mp<W> &x, const BMat &M, int64_t b, int64_t r, int64_t c, int L)
 {
     const int64_t lo = lim_off(M, b, r, c), eo = es_off(M, b, r, c);
-#pragma unroll
+#pragma unroll (is_big<W>() ? 4 : W / 2)
     for (int k = 0; k < W / 2; ++k) {
         uint64_t v = (k < L) ? __ldg(M.limb + lo + (int64_t)k * M.plane) : 0ull;
         x.m[W - 1 - 2 * k] = (uint32_t)(v >> 32);
@@ -36,7 +36,7 @@ template <int W>
 MP_DEV void ld_rw(Mp<W> &x, const BMat &M, int64_t b, int64_t r, int64_t c, int L)
 {
     const int64_t lo = lim_off(M, b, r, c), eo = es_off(M, b, r, c);
-#pragma unroll
+#pragma unroll (is_big<W>() ? 4 : W / 2)
     for (int k = 0; k < W / 2; ++k) {
         uint64_t v = (k < L) ? M.limb[lo + (int64_t)k * M.plane] : 0ull;
         x.m[W - 1 - 2 * k] = (uint32_t)(v >> 32);
@@ -58,7 +58,7 @@ template <int W>
 MP_DEV bool st(const Mp<W> &x, const BMat &M, int64_t b, int64_t r, int64_t c, int L)
 {
     const int64_t lo = lim_off(M, b, r, c), eo = es_off(M, b, r, c);
-#pragma unroll
+#pragma unroll (is_big<W>() ? 4 : W / 2)
     for (int k = 0; k < W / 2; ++k)
         if (k < L)
             M.limb[lo + (int64_t)k * M.plane] =
@@ -120,26 +120,35 @@ __global__ void convert_kernel(BMat X, int px, BMat R, int pr, int64_t rows, int
 }
 
 // ---------------------------------------------------------- Simple (Eq. 1)
-// One thread per c_ij; operands read straight from global memory (through
-// the read-only cache), k ascending: c = RN(c + RN(a_ik b_kj)).
+// One thread per c_ij of product blockIdx.z of a batch; operands read
+// straight from global memory (through the read-only cache), k ascending:
+// c = RN(c + RN(a_ik b_kj)).  The wide class also takes its Block leaves
+// here (same bits): its numbers live in local memory either way, and this
+// kernel keeps four CTAs per SM where the shared-memory leaf fits one.
+template <int W> struct SimpleCfg {
+    static constexpr int TY = (W <= 16) ? 8 : (W == 32 ? 4 : (W == 64 ? 2 : 4));
+    static constexpr int MIN_CTAS = (W <= 16) ? 3 : (is_big<W>() ? 4 : 1);
+};
+
 template <int W>
-__global__ void __launch_bounds__(W <= 16 ? 256 : (W == 32 ? 128 : 64), W <= 16 ? 3 : 1)
+__global__ void __launch_bounds__(32 * SimpleCfg<W>::TY, SimpleCfg<W>::MIN_CTAS)
 gemm_simple_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p,
                    DevStatus *status)
 {
     const RoundSpec rs = make_spec<W>(p);
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t i = blockIdx.y * (int64_t)blockDim.y + threadIdx.y;
+    const int64_t bt = blockIdx.z;
     if (i >= m || j >= n) return;
     Mp<W> c, a, b, t;
     set_zero<W>(c, 0u);
     for (int64_t k = 0; k < l; ++k) {
-        ld<W>(a, A, 0, i, k, rs.L);
-        ld<W>(b, B, 0, k, j, rs.L);
+        ld<W>(a, A, bt, i, k, rs.L);
+        ld<W>(b, B, bt, k, j, rs.L);
         mul<W, true>(t, a, b, rs);
         add<W, true>(c, c, t, 0u, rs);
     }
-    if (st<W>(c, C, 0, i, j, rs.L)) flag(status, ST_RANGE);
+    if (st<W>(c, C, bt, i, j, rs.L)) flag(status, ST_RANGE);
 }
 
 // ---------------------------------------------------- Block (Eq. 2), batched
@@ -276,7 +285,7 @@ gemm_block_sm_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, in
                      int64_t tiles_m, int64_t tiles_n, DevStatus *status)
 {
     using Cfg = BlockSmCfg<W>;
-    static_assert(W == 4 || W == 8 || W == 16 || W == 32 || W == 64, "leaf class");
+    static_assert(W == 4 || W == 8 || W == 16 || W == 32 || W == 64, "leaf class (the wide class takes the Simple kernel)");
     constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK, RB = Cfg::RB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const RoundSpec rs = make_spec<W>(p);
@@ -605,7 +614,7 @@ void launch_gemm_simple(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n,
                         DevStatus *st, cudaStream_t s)
 {
     if (m <= 0 || n <= 0) return;
-    const int ty = (W <= 16) ? 8 : (W == 32 ? 4 : 2);
+    constexpr int ty = SimpleCfg<W>::TY;
     dim3 block(32, ty);
     dim3 grid((unsigned)((n + 31) / 32), (unsigned)((m + ty - 1) / ty));
     gemm_simple_kernel<W><<<grid, block, 0, s>>>(A, B, C, m, l, n, p, st);
@@ -616,16 +625,31 @@ void launch_gemm_block(BMat A, BMat B, BMat C, int64_t batch, int64_t m, int64_t
                        int p, DevStatus *st, cudaStream_t s)
 {
     if (batch <= 0 || m <= 0 || n <= 0) return;
-    using Cfg = BlockSmCfg<W>;
-    const int64_t tm = (m + Cfg::BM - 1) / Cfg::BM, tn = (n + Cfg::BN - 1) / Cfg::BN;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(gemm_block_sm_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Cfg::smem());
-        attr = true;
+    if constexpr (is_big<W>()) {
+        // wide class: the batched Simple kernel, up to 65535 products a launch
+        constexpr int ty = SimpleCfg<W>::TY;
+        for (int64_t b0 = 0; b0 < batch; b0 += 65535) {
+            const int64_t nb = batch - b0 < 65535 ? batch - b0 : 65535;
+            BMat Ab = A, Bb = B, Cb = C;
+            Ab.limb += b0 * A.bs_limb; Ab.exp += b0 * A.bs_es; Ab.sign += b0 * A.bs_es;
+            Bb.limb += b0 * B.bs_limb; Bb.exp += b0 * B.bs_es; Bb.sign += b0 * B.bs_es;
+            Cb.limb += b0 * C.bs_limb; Cb.exp += b0 * C.bs_es; Cb.sign += b0 * C.bs_es;
+            dim3 block(32, ty);
+            dim3 grid((unsigned)((n + 31) / 32), (unsigned)((m + ty - 1) / ty), (unsigned)nb);
+            gemm_simple_kernel<W><<<grid, block, 0, s>>>(Ab, Bb, Cb, m, l, n, p, st);
+        }
+    } else {
+        using Cfg = BlockSmCfg<W>;
+        const int64_t tm = (m + Cfg::BM - 1) / Cfg::BM, tn = (n + Cfg::BN - 1) / Cfg::BN;
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(gemm_block_sm_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Cfg::smem());
+            attr = true;
+        }
+        gemm_block_sm_kernel<W><<<(unsigned)(batch * tm * tn), Cfg::THREADS, Cfg::smem(), s>>>(
+            A, B, C, m, l, n, p, tm, tn, st);
     }
-    gemm_block_sm_kernel<W><<<(unsigned)(batch * tm * tn), Cfg::THREADS, Cfg::smem(), s>>>(
-        A, B, C, m, l, n, p, tm, tn, st);
 }
 
 template <int W>

@@ -59,10 +59,11 @@ def _edge_pairs(p, n, seed):
     return X, Y
 
 
-@pytest.mark.parametrize("p", [2, 53, 64, 127, 128, 200, 256, 300, 512, 1000, 1024, 2048])
+@pytest.mark.parametrize("p", [2, 53, 64, 127, 128, 200, 256, 300, 512, 1000, 1024, 2048,
+                               2049, 4000, 8192, 8650, 8704])
 @pytest.mark.parametrize("op", ["add", "sub", "mul", "div"])
 def test_elementwise_matches_oracle(op, p):
-    n = 2000 if p <= 1024 else 600
+    n = 2000 if p <= 1024 else (600 if p <= 2048 else 150)
     X, Y = _edge_pairs(p, n, p * 13 + len(op))
     if op == "div":
         z = Y.exp == gen.EXP_ZERO
@@ -103,7 +104,8 @@ def test_p53_matches_ieee_double(op):
     assert np.array_equal(got, ref)
 
 
-@pytest.mark.parametrize("pf,pt", [(256, 512), (512, 256), (2048, 128), (128, 2048), (200, 199)])
+@pytest.mark.parametrize("pf,pt", [(256, 512), (512, 256), (2048, 128), (128, 2048), (200, 199),
+                                   (8650, 4000), (4000, 8650), (8704, 8192), (1024, 8650)])
 def test_convert_matches_oracle(pf, pt):
     X = gen.uniform_pm1(7, 33, pf, 9, -30, 30)
     want = orc.convert(X, pt)

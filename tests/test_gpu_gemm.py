@@ -26,10 +26,10 @@ def test_config1_simple_64_256bit():
         assert_bits_equal(gemm(A, B, algo), want, "config1 algo %d" % algo)
 
 
-@pytest.mark.parametrize("p", [128, 200, 256, 512, 1024, 2048])
+@pytest.mark.parametrize("p", [128, 200, 256, 512, 1024, 2048, 4000, 8650])
 @pytest.mark.parametrize("algo", ["simple", "block"])
 def test_simple_block_ragged(algo, p):
-    m, l, n = (37, 29, 45) if p >= 1024 else (67, 45, 83)
+    m, l, n = (67, 45, 83) if p < 1024 else ((37, 29, 45) if p <= 2048 else (19, 13, 37))
     A = gen.uniform_pm1(m, l, p, 11, -16, 16)
     B = gen.uniform_pm1(l, n, p, 12, -16, 16)
     want = orc.gemm(orc.SIMPLE, A, B)
@@ -40,7 +40,8 @@ def test_simple_block_ragged(algo, p):
 @pytest.mark.parametrize("algo", ["strassen", "winograd"])
 @pytest.mark.parametrize("dims,cutoff,p", [((130, 97, 71), 16, 256), ((128, 128, 128), 16, 512),
                                            ((67, 99, 35), 8, 128), ((33, 33, 33), 4, 1024),
-                                           ((150, 151, 149), 32, 512), ((27, 19, 23), 3, 2048)])
+                                           ((150, 151, 149), 32, 512), ((27, 19, 23), 3, 2048),
+                                           ((19, 17, 21), 4, 8192), ((14, 15, 13), 3, 8650)])
 def test_recursion_matches_oracle(algo, policy, dims, cutoff, p):
     m, l, n = dims
     A = gen.uniform_pm1(m, l, p, 21, -16, 16)
@@ -108,3 +109,13 @@ def test_batched_equals_individual():
             want = orc.gemm(orc.SIMPLE, As[b], Bs[b])
             got = C.sub(np.arange(b * m, (b + 1) * m), np.arange(n))
             assert_bits_equal(got, want, "batch %d" % b)
+
+
+@pytest.mark.parametrize("algo", [mp.EXACT, mp.SPLIT])
+def test_exact_and_split_reject_wide_precision(algo):
+    """MP_EXACT and MP_SPLIT stop at 2048 bits: MP_ERR_UNSUPPORTED above."""
+    A = gen.uniform_pm1(4, 4, 4000, 1)
+    dC = mp.DeviceMP.empty(4, 4, 4000)
+    with pytest.raises(mp.MPError) as e:
+        mp.mpgemm(dev(A), dev(A), dC, algo)
+    assert e.value.code == -7

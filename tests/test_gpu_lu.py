@@ -83,7 +83,7 @@ def test_singular_reported():
     assert mp.load_library().mp_singular_column() == 5
 
 
-@pytest.mark.parametrize("p,n", [(256, 90), (1024, 70), (2048, 40)])
+@pytest.mark.parametrize("p,n", [(256, 90), (1024, 70), (2048, 40), (8650, 24)])
 @pytest.mark.parametrize("panel", [1, 8, 128])
 def test_unpivoted_paper_lu(p, n, panel):
     """The paper's LU without pivoting (Sec. 4) on a random matrix, where
@@ -105,3 +105,13 @@ def test_unpivoted_zero_pivot_reported():
     assert mp.load_library().mp_singular_column() == 0
     _, _, _, rc = gpu_lu(A, b, 4, mp.SIMPLE, 64, pivoting=True)
     assert rc == 0
+
+
+@pytest.mark.parametrize("p", [8192, 8650])
+@pytest.mark.parametrize("pivoting", [False, True])
+def test_lotkin_wide_precision(p, pivoting):
+    """The paper's ill-conditioned case at its own precisions (Sec. 4: 8192
+    and 8650 bits): Lotkin matrix, blocked LU with Winograd trailing
+    products, factors and solution bit for bit against the oracle."""
+    A = gen.lotkin(32, p)
+    check(A, 8, mp.WINOGRAD, 4, pivoting=pivoting)
