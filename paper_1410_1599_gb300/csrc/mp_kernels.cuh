@@ -130,7 +130,7 @@ template <int W> struct SimpleCfg {
     static constexpr int MIN_CTAS = (W <= 16) ? 3 : (is_big<W>() ? 4 : 1);
 };
 
-template <int W>
+template <int W, bool BATCHED = false>
 __global__ void __launch_bounds__(32 * SimpleCfg<W>::TY, SimpleCfg<W>::MIN_CTAS)
 gemm_simple_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p,
                    DevStatus *status)
@@ -138,7 +138,7 @@ gemm_simple_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int 
     const RoundSpec rs = make_spec<W>(p);
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t i = blockIdx.y * (int64_t)blockDim.y + threadIdx.y;
-    const int64_t bt = blockIdx.z;
+    const int64_t bt = BATCHED ? (int64_t)blockIdx.z : 0;
     if (i >= m || j >= n) return;
     Mp<W> c, a, b, t;
     set_zero<W>(c, 0u);
@@ -636,7 +636,7 @@ void launch_gemm_block(BMat A, BMat B, BMat C, int64_t batch, int64_t m, int64_t
             Cb.limb += b0 * C.bs_limb; Cb.exp += b0 * C.bs_es; Cb.sign += b0 * C.bs_es;
             dim3 block(32, ty);
             dim3 grid((unsigned)((n + 31) / 32), (unsigned)((m + ty - 1) / ty), (unsigned)nb);
-            gemm_simple_kernel<W><<<grid, block, 0, s>>>(Ab, Bb, Cb, m, l, n, p, st);
+            gemm_simple_kernel<W, true><<<grid, block, 0, s>>>(Ab, Bb, Cb, m, l, n, p, st);
         }
     } else {
         using Cfg = BlockSmCfg<W>;

@@ -101,7 +101,7 @@ def test_budget_is_respected_and_oversized_rejected():
 def test_malformed_and_cancelled():
     srv = mp.Server(budget_bytes=1 << 30, slots=1)
     A = gen.uniform_pm1(4, 4, 128, 1)
-    bad = mp.HostMP(A.limb, A.exp, A.sign, 5000)          # precision out of range
+    bad = mp.HostMP(A.limb, A.exp, A.sign, 9000)          # precision out of range (> 8704)
     assert srv.submit_gemm(1, bad, bad) == -1
     # a long head request keeps the single slot busy; cancel a queued one
     H = gen.uniform_pm1(300, 300, 1024, 2)
