@@ -819,7 +819,7 @@ def serve_repeat_run(n_req=96, seed=12, slots=8, budget=150 << 30):
     return {"requests": n_req, "shapes": len(shapes), "offered_req_per_s": round(lam, 2), **res}
 
 
-def split_run(n=4096, p=1024, with_simple=True):
+def split_run(n=4096, p=1024, with_simple=True, exp_lo=-16, exp_hi=16, with_exact=True):
     """Split form vs the exact limb path (same correctly rounded result) on
     n^3 at p bits, entries U[-1,1)*2^e, e ~ U{-16..16}: the truncated split
     form (default), the full split form (every digit diagonal), the exact
@@ -830,12 +830,13 @@ def split_run(n=4096, p=1024, with_simple=True):
     from paper_1410_1599_gb300 import binding as mp
     from paper_1410_1599_gb300 import inputs as gen
 
-    A = gen.uniform_pm1(n, n, p, 13, -16, 16)
-    B = gen.uniform_pm1(n, n, p, 14, -16, 16)
+    A = gen.uniform_pm1(n, n, p, 13, exp_lo, exp_hi)
+    B = gen.uniform_pm1(n, n, p, 14, exp_lo, exp_hi)
     dA, dB = mp.DeviceMP.from_host(A), mp.DeviceMP.from_host(B)
     out = {}
     res = {}
-    runs = (("split", mp.SPLIT, True), ("split_full", mp.SPLIT, False), ("exact_limb", mp.EXACT, True)) + \
+    runs = (("split", mp.SPLIT, True), ("split_full", mp.SPLIT, False)) + \
+        ((("exact_limb", mp.EXACT, True),) if with_exact else ()) + \
         ((("simple_limb", mp.SIMPLE, True),) if with_simple else ())
     for name, algo, trunc in runs:
         C = mp.DeviceMP.empty(n, n, p)
@@ -870,16 +871,18 @@ def split_run(n=4096, p=1024, with_simple=True):
     def equal(X, Y):
         return bool(torch.equal(X.limb, Y.limb) and torch.equal(X.exp, Y.exp) and torch.equal(X.sign, Y.sign))
 
-    same = equal(res["split"], res["exact_limb"]) and equal(res["split_full"], res["exact_limb"])
-    exps = A.exp.astype(np.float64)
+    ref = res["exact_limb"] if with_exact else res["split_full"]
+    same = equal(res["split"], ref) and equal(res["split_full"], ref)
     wide_rows = int(sum(1 for i in range(n) if (A.exp[i][A.exp[i] != gen.EXP_ZERO]).min()
                         < (A.exp[i][A.exp[i] != gen.EXP_ZERO]).max() - 64))
     wide_cols = int(sum(1 for j in range(n) if (B.exp[:, j][B.exp[:, j] != gen.EXP_ZERO]).min()
                         < (B.exp[:, j][B.exp[:, j] != gen.EXP_ZERO]).max() - 64))
-    return {"n": n, "prec": p, "split_equals_exact_limb_all_outputs": same,
-            "wide_rows": wide_rows, "wide_cols": wide_cols,
-            "speedup_split_vs_exact_limb": round(out["exact_limb"]["seconds"] / out["split"]["seconds"], 3),
-            **out}
+    line = {"n": n, "prec": p, "entries": "U[-1,1)*2^e, e~U{%d..%d}" % (exp_lo, exp_hi),
+            ("split_equals_exact_limb_all_outputs" if with_exact else "split_equals_full_split_all_outputs"): same,
+            "wide_rows": wide_rows, "wide_cols": wide_cols}
+    if with_exact:
+        line["speedup_split_vs_exact_limb"] = round(out["exact_limb"]["seconds"] / out["split"]["seconds"], 3)
+    return {**line, **out}
 
 
 # The paper's CPU times (seconds, MPFR on one core of a Core i7 3850; context
@@ -1075,7 +1078,10 @@ def main():
         from paper_1410_1599_gb300 import build as libbuild
         libbuild.build()
         torch.cuda.set_device(local)
-        print(json.dumps({"split_form": split_run(a.n if a.n != 2048 else 4096, a.prec if a.prec != 512 else 1024)}), flush=True)
+        n_s, p_s = (a.n if a.n != 2048 else 4096), (a.prec if a.prec != 512 else 1024)
+        print(json.dumps({"split_form": split_run(n_s, p_s),
+                          "split_form_u11": split_run(n_s, p_s, with_simple=False, exp_lo=0, exp_hi=0,
+                                                      with_exact=False)}), flush=True)
         return
     if a.lotkin:
         import torch

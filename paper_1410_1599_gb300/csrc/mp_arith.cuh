@@ -316,7 +316,10 @@ __device__ __noinline__ void big_mul(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, c
     r.s = s;
 }
 
-// r = RN_p(a / b), b != 0: the long division of div_impl
+// r = RN_p(a / b), b != 0: the long division of div_impl.  The remainder is
+// a window R = buf[base .. base + W] that moves down one word per digit
+// (R <- R 2^32 without moving words) and the digits go straight to their
+// place in Q.
 template <int W>
 __device__ __noinline__ void big_div(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, const RoundSpec &rs)
 {
@@ -327,24 +330,24 @@ __device__ __noinline__ void big_div(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, c
         r.s = s;
         return;
     }
-    uint32_t R[W + 1], Q[W + 2];
+    uint32_t buf[2 * W + 2], Q[W + 2];
+    int base = W + 1;
     uint32_t br = 0u;
     for (int i = 0; i < W; ++i) {                 // R = A - D when A >= D
         const uint64_t df = (uint64_t)a.m[i] - b.m[i] - br;
-        R[i] = (uint32_t)df;
+        buf[base + i] = (uint32_t)df;
         br = (uint32_t)(df >> 63);
     }
     const uint32_t q0 = br ? 0u : 1u;
     if (!q0)
-        for (int i = 0; i < W; ++i) R[i] = a.m[i];
-    R[W] = 0u;
-    for (int i = 0; i < W + 2; ++i) Q[i] = 0u;
-    Q[0] = q0;
+        for (int i = 0; i < W; ++i) buf[base + i] = a.m[i];
+    buf[base + W] = 0u;
+    Q[W + 1] = q0;
     const uint32_t d1 = b.m[W - 1], d2 = b.m[W - 2];
     const uint32_t v = (uint32_t)(0xffffffffffffffffull / d1 - 0x100000000ull);
     for (int t = 0; t <= W; ++t) {
-        for (int i = W; i > 0; --i) R[i] = R[i - 1];
-        R[0] = 0u;
+        buf[--base] = 0u;                         // R <- R 2^32 (its top word was zero)
+        uint32_t *R = buf + base;
         const uint32_t u1 = R[W], u0 = R[W - 1];
         uint64_t qh, rh;
         if (u1 >= d1) {
@@ -387,11 +390,10 @@ __device__ __noinline__ void big_div(Mp<W> &r, const Mp<W> &a, const Mp<W> &b, c
             R[W] += (uint32_t)c;
             qd -= 1u;
         }
-        for (int i = W + 1; i > 0; --i) Q[i] = Q[i - 1];
-        Q[0] = qd;
+        Q[W - t] = qd;
     }
     bool rem = false;
-    for (int i = 0; i < W; ++i) rem |= R[i] != 0u;
+    for (int i = 0; i < W; ++i) rem |= buf[base + i] != 0u;
     const int lz = q0 ? 31 : 32;
     big_shl(Q, W + 2, lz);
     int64_t e = a.e - b.e + 32 - lz;
