@@ -567,6 +567,147 @@ __global__ void lu_bwd_update_kernel(BMat LU, BMat y, BMat x, int64_t c0, int64_
     if (st<W>(yi, y, 0, i, 0, rs.L)) flag(status, ST_RANGE);
 }
 
+// --------------------------------- solves by warps (512 to 1024 bits)
+// The same blocked order as above, but each row belongs to a warp (lane =
+// word) and every multiply-add and division is formed by warp_mul,
+// warp_add and warp_div: the solves are chains of dependent operations,
+// so the latency of one operation is what counts.  Diagonal blocks of SBW
+// rows; the row that becomes final publishes its value through shared
+// memory.
+constexpr int SBW = 16;
+
+template <int W>
+__global__ void __launch_bounds__(SBW * 32) lu_fwd_diag_warp(BMat LU, BMat y, int64_t c0, int64_t c1, int p,
+                                                            DevStatus *status)
+{
+    const RoundSpec rs = make_spec<W>(p);
+    const int lane = (int)(threadIdx.x & 31u), wid = (int)(threadIdx.x >> 5);
+    const int64_t i = c0 + wid;
+    const bool mine = i < c1;
+    __shared__ uint32_t s_m[32];
+    __shared__ int64_t s_e;
+    __shared__ uint32_t s_s;
+    int64_t ye = EXP_ZERO;
+    uint32_t ys = 0u, ym = 0u;
+    if (mine) ym = wld<W>(y, 0, i, 0, rs.L, ye, ys);
+    for (int64_t j = c0; j + 1 < c1; ++j) {
+        if (i == j) {                            // y_j is final
+            s_m[lane] = ym;
+            if (lane == 0) {
+                s_e = ye;
+                s_s = ys;
+            }
+        }
+        __syncthreads();
+        if (mine && i > j) {
+            int64_t le, te;
+            uint32_t ls, ts;
+            const uint32_t lm = wld<W>(LU, 0, i, j, rs.L, le, ls);
+            const uint32_t tm = warp_mul<W>(lm, le, ls, s_m[lane], s_e, s_s, te, ts, rs);
+            ym = warp_add<W>(ym, ye, ys, tm, te, ts, 1u, ye, ys, rs);
+        }
+        __syncthreads();
+    }
+    if (mine && i > c0 && wst<W>(ym, ye, ys, y, 0, i, 0, rs.L) && lane == 0) flag(status, ST_RANGE);
+}
+
+// forward, rows [c1, n) take columns [c0, c1): one warp per row
+template <int W>
+__global__ void __launch_bounds__(128) lu_fwd_update_warp(BMat LU, BMat y, int64_t n, int64_t c0, int64_t c1,
+                                                          int p, DevStatus *status)
+{
+    const RoundSpec rs = make_spec<W>(p);
+    const int lane = (int)(threadIdx.x & 31u);
+    const int64_t i = c1 + (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (i >= n) return;
+    int64_t ye;
+    uint32_t ys;
+    uint32_t ym = wld<W>(y, 0, i, 0, rs.L, ye, ys);
+    for (int64_t j = c0; j < c1; ++j) {
+        int64_t ve, le, te;
+        uint32_t vs, ls, ts;
+        const uint32_t vm = wld<W>(y, 0, j, 0, rs.L, ve, vs);
+        const uint32_t lm = wld<W>(LU, 0, i, j, rs.L, le, ls);
+        const uint32_t tm = warp_mul<W>(lm, le, ls, vm, ve, vs, te, ts, rs);
+        ym = warp_add<W>(ym, ye, ys, tm, te, ts, 1u, ye, ys, rs);
+    }
+    if (wst<W>(ym, ye, ys, y, 0, i, 0, rs.L) && lane == 0) flag(status, ST_RANGE);
+}
+
+// backward, diagonal block [c0, c1): x_j = y_j / u_jj for j = c1-1 down to
+// c0 (a zero u_jj gives x_j = +0 and reports the matrix singular)
+template <int W>
+__global__ void __launch_bounds__(SBW * 32) lu_bwd_diag_warp(BMat LU, BMat y, BMat x, int64_t c0, int64_t c1,
+                                                            int p, DevStatus *status)
+{
+    const RoundSpec rs = make_spec<W>(p);
+    const int lane = (int)(threadIdx.x & 31u), wid = (int)(threadIdx.x >> 5);
+    const int64_t i = c0 + wid;
+    const bool mine = i < c1;
+    __shared__ uint32_t s_m[32];
+    __shared__ int64_t s_e;
+    __shared__ uint32_t s_s;
+    int64_t ye = EXP_ZERO;
+    uint32_t ys = 0u, ym = 0u;
+    bool bad = false, zero = false;
+    if (mine) ym = wld<W>(y, 0, i, 0, rs.L, ye, ys);
+    for (int64_t j = c1 - 1; j >= c0; --j) {
+        if (i == j) {                            // y_j is final: x_j = y_j / u_jj
+            int64_t ue, qe;
+            uint32_t us, qs;
+            const uint32_t um = wld<W>(LU, 0, j, j, rs.L, ue, us);
+            uint32_t qm = 0u;
+            if (ue == EXP_ZERO) {
+                zero = true;
+                qe = EXP_ZERO;
+                qs = 0u;
+            } else {
+                qm = warp_div<W>(ym, ye, ys, um, ue, us, qe, qs, rs);
+            }
+            bad |= wst<W>(qm, qe, qs, x, 0, j, 0, rs.L);
+            s_m[lane] = qm;
+            if (lane == 0) {
+                s_e = qe;
+                s_s = qs;
+            }
+        }
+        __syncthreads();
+        if (mine && i < j) {
+            int64_t ue, te;
+            uint32_t us, ts;
+            const uint32_t um = wld<W>(LU, 0, i, j, rs.L, ue, us);
+            const uint32_t tm = warp_mul<W>(um, ue, us, s_m[lane], s_e, s_s, te, ts, rs);
+            ym = warp_add<W>(ym, ye, ys, tm, te, ts, 1u, ye, ys, rs);
+        }
+        __syncthreads();
+    }
+    if (lane == 0 && zero) atomicOr(&status->flags, ST_SINGULAR);
+    if (lane == 0 && bad) flag(status, ST_RANGE);
+}
+
+// backward, rows [0, c0) take columns c1-1 down to c0: one warp per row
+template <int W>
+__global__ void __launch_bounds__(128) lu_bwd_update_warp(BMat LU, BMat y, BMat x, int64_t c0, int64_t c1,
+                                                          int p, DevStatus *status)
+{
+    const RoundSpec rs = make_spec<W>(p);
+    const int lane = (int)(threadIdx.x & 31u);
+    const int64_t i = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (i >= c0) return;
+    int64_t ye;
+    uint32_t ys;
+    uint32_t ym = wld<W>(y, 0, i, 0, rs.L, ye, ys);
+    for (int64_t j = c1 - 1; j >= c0; --j) {
+        int64_t ve, ue, te;
+        uint32_t vs, us, ts;
+        const uint32_t vm = wld<W>(x, 0, j, 0, rs.L, ve, vs);
+        const uint32_t um = wld<W>(LU, 0, i, j, rs.L, ue, us);
+        const uint32_t tm = warp_mul<W>(um, ue, us, vm, ve, vs, te, ts, rs);
+        ym = warp_add<W>(ym, ye, ys, tm, te, ts, 1u, ye, ys, rs);
+    }
+    if (wst<W>(ym, ye, ys, y, 0, i, 0, rs.L) && lane == 0) flag(status, ST_RANGE);
+}
+
 // Row exchanges k = j0 .. je-1 (rows k and piv[k], in order) on the columns
 // outside the panel, [0, j0) and [je, n): one thread per column.  Exchanges
 // of whole rows commute with the panel's work, which touches only the
@@ -634,6 +775,20 @@ void launch_lu_solve(BMat LU, int64_t n, const int64_t *piv, BMat b, BMat y, BMa
 {
     constexpr int T = 64;
     lu_permute_kernel<W><<<1, 1024, 0, s>>>(n, piv, b, y, perm, p);
+    if constexpr (W >= 16 && W <= 32) {          // one thread per row is as fast below 512 bits
+        for (int64_t c0 = 0; c0 < n; c0 += SBW) {
+            const int64_t c1 = c0 + SBW < n ? c0 + SBW : n;
+            lu_fwd_diag_warp<W><<<1, SBW * 32, 0, s>>>(LU, y, c0, c1, p, st);
+            if (c1 < n)
+                lu_fwd_update_warp<W><<<(unsigned)((n - c1 + 3) / 4), 128, 0, s>>>(LU, y, n, c0, c1, p, st);
+        }
+        for (int64_t c0 = ((n - 1) / SBW) * SBW; c0 >= 0; c0 -= SBW) {
+            const int64_t c1 = c0 + SBW < n ? c0 + SBW : n;
+            lu_bwd_diag_warp<W><<<1, SBW * 32, 0, s>>>(LU, y, x, c0, c1, p, st);
+            if (c0 > 0) lu_bwd_update_warp<W><<<(unsigned)((c0 + 3) / 4), 128, 0, s>>>(LU, y, x, c0, c1, p, st);
+        }
+        return;
+    }
     for (int64_t c0 = 0; c0 < n; c0 += SB) {
         const int64_t c1 = c0 + SB < n ? c0 + SB : n;
         lu_fwd_diag_kernel<W><<<1, SB, 0, s>>>(LU, y, c0, c1, p, st);

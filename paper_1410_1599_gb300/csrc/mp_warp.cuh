@@ -1,6 +1,7 @@
-// mp_warp.cuh -- one MP division computed by the 32 lanes of a warp together,
-// for latency-bound call sites (the LU pivot-column scaling and the
-// back substitution, where one division sits on the critical path).
+// mp_warp.cuh -- MP division, multiplication and addition computed by the 32
+// lanes of a warp together, for latency-bound call sites (the LU
+// pivot-column scaling and the triangular solves, where one operation after
+// another sits on the critical path).
 //
 // A mantissa of W <= 32 words is spread one word per lane (lane i holds word
 // i, least significant first; lanes >= W hold 0).  Carries and borrows cross
@@ -39,6 +40,47 @@ MP_DEV uint32_t wadd(uint32_t a, uint32_t b, uint32_t &cout)
     const uint64_t c = (x + g) ^ x ^ g;
     cout = (uint32_t)(c >> W) & 1u;
     return s + ((uint32_t)(c >> lane) & 1u);
+}
+
+// Round a mantissa held one word per lane (top bit of word W-1 set, lanes
+// >= W zero) to p bits, nearest-even: `below` is the word under it and
+// `sticky` says whether anything lies lower (both the same in every lane).
+// A carry out of the top renormalises and increments e.
+template <int W>
+MP_DEV uint32_t warp_round(uint32_t M, uint32_t below, bool sticky, int64_t &e, const RoundSpec &rs)
+{
+    const int lane = (int)(threadIdx.x & 31u);
+    // round to p bits, nearest-even
+    const int r = rs.r;
+    uint32_t up;
+    if (r == 0) {
+        const uint32_t lsb = __shfl_sync(FULL_MASK, M, 0) & 1u;
+        const uint32_t st = ((below << 1) != 0u || sticky) ? 1u : 0u;
+        up = (below >> 31) & (st | lsb);
+    } else {
+        const int rw = r >> 5, rb = r & 31, r1 = r - 1;
+        const uint32_t lsb = (__shfl_sync(FULL_MASK, M, rw) >> rb) & 1u;
+        const uint32_t rbit = (__shfl_sync(FULL_MASK, M, r1 >> 5) >> (r1 & 31)) & 1u;
+        // bits of M under the round bit
+        uint32_t mask = 0u;
+        if (32 * lane + 32 <= r1) mask = 0xffffffffu;
+        else if (32 * lane < r1) mask = (1u << (r1 - 32 * lane)) - 1u;
+        const bool low = __ballot_sync(FULL_MASK, (M & mask) != 0u) != 0u;
+        const uint32_t st = (low || below != 0u || sticky) ? 1u : 0u;
+        up = rbit & (st | lsb);
+    }
+    if (up) {                                    // uniform branch
+        uint32_t c;
+        M = wadd<W>(M, lane == (r >> 5) ? (1u << (r & 31)) : 0u, c);
+        if (c) {
+            M = (lane == W - 1) ? 0x80000000u : 0u;
+            e += 1;
+        }
+    }
+    // clear the bits under the kept LSB (and the lanes beyond W)
+    if (lane >= W || 32 * lane + 32 <= r) M = 0u;
+    else if (32 * lane < r) M &= ~((1u << (r - 32 * lane)) - 1u);
+    return M;
 }
 
 // r = RN_p(a / b) for b != 0, by the whole warp.  In: lane i holds word i of
@@ -130,37 +172,208 @@ MP_DEV uint32_t warp_div(uint32_t am, int64_t ae, uint32_t as, uint32_t bm, int6
     const uint32_t below = q0 ? __funnelshift_r(qlow, q1w, 1) : qlow;
     const bool sticky = rem || (q0 && (qlow & 1u));
     int64_t e = ae - be + (q0 ? 1 : 0);
-    // round to p bits, nearest-even
-    const int r = rs.r;
-    uint32_t up;
-    if (r == 0) {
-        const uint32_t lsb = __shfl_sync(FULL_MASK, M, 0) & 1u;
-        const uint32_t st = ((below << 1) != 0u || sticky) ? 1u : 0u;
-        up = (below >> 31) & (st | lsb);
-    } else {
-        const int rw = r >> 5, rb = r & 31, r1 = r - 1;
-        const uint32_t lsb = (__shfl_sync(FULL_MASK, M, rw) >> rb) & 1u;
-        const uint32_t rbit = (__shfl_sync(FULL_MASK, M, r1 >> 5) >> (r1 & 31)) & 1u;
-        // bits of M under the round bit
-        uint32_t mask = 0u;
-        if (32 * lane + 32 <= r1) mask = 0xffffffffu;
-        else if (32 * lane < r1) mask = (1u << (r1 - 32 * lane)) - 1u;
-        const bool low = __ballot_sync(FULL_MASK, (M & mask) != 0u) != 0u;
-        const uint32_t st = (low || below != 0u || sticky) ? 1u : 0u;
-        up = rbit & (st | lsb);
+    M = warp_round<W>(M, below, sticky, e, rs);
+    re = e;
+    return M;
+}
+
+// r = RN_p(a * b) by the whole warp (lane i: word i of each mantissa).
+// Lane L forms the column sums of product positions L and L + 32,
+// sum_{i+j=k} a_i b_j (a broadcast, b gathered), as 96-bit values; the
+// three 32-bit digits of each column are added into their words, and the
+// remaining one-bit carries ripple by carry-lookahead on ballots.  The top
+// W words (one bit lower when the product is below 1/2) are then rounded
+// once with the next word and an OR of the rest.
+template <int W>
+MP_DEV uint32_t warp_mul(uint32_t am, int64_t ae, uint32_t as, uint32_t bm, int64_t be, uint32_t bs,
+                         int64_t &re, uint32_t &rsg, const RoundSpec &rs)
+{
+    static_assert(W >= 4 && W <= 32, "one word per lane");
+    const int lane = (int)(threadIdx.x & 31u);
+    rsg = as ^ bs;
+    if (ae == EXP_ZERO || be == EXP_ZERO) {
+        re = EXP_ZERO;
+        return 0u;
     }
-    if (up) {                                    // uniform branch
-        uint32_t c;
-        M = wadd<W>(M, lane == (r >> 5) ? (1u << (r & 31)) : 0u, c);
-        if (c) {
-            M = (lane == W - 1) ? 0x80000000u : 0u;
-            e += 1;
+    constexpr bool TWO = 2 * W > 32;               // positions beyond 31 exist
+    uint64_t s1 = 0, s2 = 0;
+    uint32_t h1 = 0u, h2 = 0u;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        const uint32_t ai = __shfl_sync(FULL_MASK, am, i);
+        const int j1 = lane - i;
+        const uint32_t b1r = __shfl_sync(FULL_MASK, bm, j1 & 31);
+        const uint64_t p1 = (uint64_t)ai * ((j1 >= 0 && j1 < W) ? b1r : 0u);
+        s1 += p1;
+        h1 += (s1 < p1) ? 1u : 0u;
+        if constexpr (TWO) {
+            const int j2 = lane + 32 - i;
+            const uint32_t b2r = __shfl_sync(FULL_MASK, bm, j2 & 31);
+            const uint64_t p2 = (uint64_t)ai * ((j2 < W) ? b2r : 0u);
+            s2 += p2;
+            h2 += (s2 < p2) ? 1u : 0u;
         }
     }
-    // clear the bits under the kept LSB (and the lanes beyond W)
-    if (lane >= W || 32 * lane + 32 <= r) M = 0u;
-    else if (32 * lane < r) M &= ~((1u << (r - 32 * lane)) - 1u);
+    // word k = c0[k] + c1[k-1] + c2[k-2] (< 3 * 2^32), digits of the columns
+    const uint32_t c01 = (uint32_t)s1, c11 = (uint32_t)(s1 >> 32), c21 = h1;
+    const uint32_t c02 = (uint32_t)s2, c12 = (uint32_t)(s2 >> 32), c22 = h2;
+    const uint32_t up11 = __shfl_up_sync(FULL_MASK, c11, 1), up21 = __shfl_up_sync(FULL_MASK, c21, 2);
+    const uint64_t t1 = (uint64_t)c01 + (lane >= 1 ? up11 : 0u) + (lane >= 2 ? up21 : 0u);
+    uint64_t t2 = 0;
+    if constexpr (TWO) {
+        const uint32_t up12 = __shfl_up_sync(FULL_MASK, c12, 1), up22 = __shfl_up_sync(FULL_MASK, c22, 2);
+        const uint32_t c11_31 = __shfl_sync(FULL_MASK, c11, 31);
+        const uint32_t c21_30 = __shfl_sync(FULL_MASK, c21, 30), c21_31 = __shfl_sync(FULL_MASK, c21, 31);
+        t2 = (uint64_t)c02 + (lane >= 1 ? up12 : c11_31) +
+             (lane >= 2 ? up22 : (lane == 1 ? c21_31 : c21_30));
+    }
+    // fold the 0..2 carries one word up, then the one-bit carries
+    const uint32_t hi1 = (uint32_t)(t1 >> 32), hi2 = (uint32_t)(t2 >> 32);
+    const uint32_t uh1 = __shfl_up_sync(FULL_MASK, hi1, 1);
+    const uint64_t u1 = (uint64_t)(uint32_t)t1 + (lane >= 1 ? uh1 : 0u);
+    uint64_t u2 = 0;
+    if constexpr (TWO) {
+        const uint32_t uh2 = __shfl_up_sync(FULL_MASK, hi2, 1);
+        const uint32_t hi1_31 = __shfl_sync(FULL_MASK, hi1, 31);
+        u2 = (uint64_t)(uint32_t)t2 + (lane >= 1 ? uh2 : hi1_31);
+    }
+    const uint32_t l1 = (uint32_t)u1, l2 = (uint32_t)u2;
+    const uint64_t G = (uint64_t)__ballot_sync(FULL_MASK, (u1 >> 32) != 0u) |
+                       ((uint64_t)__ballot_sync(FULL_MASK, (u2 >> 32) != 0u) << 32);
+    const uint64_t P = (uint64_t)__ballot_sync(FULL_MASK, l1 == 0xffffffffu) |
+                       ((uint64_t)__ballot_sync(FULL_MASK, TWO && l2 == 0xffffffffu) << 32);
+    const uint64_t X = G | P;
+    const uint64_t C = (X + G) ^ X ^ G;            // bit k: carry into position k
+    const uint32_t w1 = l1 + (uint32_t)((C >> lane) & 1u);
+    const uint32_t w2 = TWO ? l2 + (uint32_t)((C >> (lane + 32)) & 1u) : 0u;
+    // word at product position pos (per lane), 0 outside [0, 2W)
+    auto word = [&](int pos) -> uint32_t {
+        const uint32_t v1 = __shfl_sync(FULL_MASK, w1, pos & 31);
+        const uint32_t v2 = TWO ? __shfl_sync(FULL_MASK, w2, pos & 31) : 0u;
+        if (pos < 0 || pos >= 2 * W) return 0u;
+        return pos < 32 ? v1 : v2;
+    };
+    const uint32_t top = word(2 * W - 1);
+    const int sh = (top >> 31) ? 0 : 1;            // product in [1/4, 1/2): one bit left
+    const uint32_t x = word(W + lane), xl = word(W + lane - 1);
+    uint32_t M = sh ? ((x << 1) | (xl >> 31)) : x;
+    if (lane >= W) M = 0u;
+    const uint32_t bw = word(W - 1), bw2 = word(W - 2);
+    const uint32_t below = sh ? ((bw << 1) | (bw2 >> 31)) : bw;
+    const int lim = sh ? W - 2 : W - 1;            // whole words under `below`
+    bool sticky = __ballot_sync(FULL_MASK, (lane < lim && w1 != 0u) || (TWO && lane + 32 < lim && w2 != 0u)) != 0u;
+    if (sh) sticky = sticky || (bw2 & 0x7fffffffu) != 0u;
+    int64_t e = ae + be - sh;
+    M = warp_round<W>(M, below, sticky, e, rs);
     re = e;
+    return M;
+}
+
+// r = RN_p(x + (-1)^neg y) by the whole warp, the steps of the scalar
+// addition: the larger magnitude X, the other operand aligned to it with a
+// guard word and a sticky bit, one carry-lookahead addition (or subtraction
+// with the sticky borrow), renormalisation, one rounding.
+template <int W>
+MP_DEV uint32_t warp_add(uint32_t xm, int64_t xe, uint32_t xs, uint32_t ym, int64_t ye, uint32_t ys,
+                         uint32_t neg, int64_t &re, uint32_t &rsg, const RoundSpec &rs)
+{
+    static_assert(W >= 4 && W <= 32, "one word per lane");
+    const int lane = (int)(threadIdx.x & 31u);
+    ys ^= neg;
+    const bool xz = xe == EXP_ZERO, yz = ye == EXP_ZERO;
+    if (xz && yz) {
+        re = EXP_ZERO;
+        rsg = xs & ys;
+        return 0u;
+    }
+    if (xz) {
+        re = ye;
+        rsg = ys;
+        return ym;
+    }
+    if (yz) {
+        re = xe;
+        rsg = xs;
+        return xm;
+    }
+    const uint32_t ne = __ballot_sync(FULL_MASK, xm != ym);
+    bool mlt = false;
+    if (ne) mlt = __shfl_sync(FULL_MASK, xm < ym ? 1u : 0u, 31 - __clz(ne)) != 0u;
+    const bool sw = (ye > xe) || (ye == xe && mlt);
+    const uint32_t X = sw ? ym : xm, Y = sw ? xm : ym;
+    int64_t e = sw ? ye : xe;
+    const int64_t d64 = sw ? (ye - xe) : (xe - ye);
+    const uint32_t sx = sw ? ys : xs;
+    const uint32_t eff_sub = (xs ^ ys) & 1u;
+    // Y aligned: word `lane`, the guard word under it and the sticky rest
+    uint32_t Ys, guard;
+    bool sticky;
+    auto yw = [&](int k) -> uint32_t {            // word k of Y, 0 outside [0, W)
+        const uint32_t v = __shfl_sync(FULL_MASK, Y, k & 31);
+        return (k >= 0 && k < W) ? v : 0u;
+    };
+    if (d64 >= 32 * (W + 1)) {
+        Ys = 0u;
+        guard = 0u;
+        sticky = __ballot_sync(FULL_MASK, Y != 0u) != 0u;
+    } else {
+        const int d = (int)d64, q = d >> 5, b = d & 31;
+        Ys = __funnelshift_r(yw(lane + q), yw(lane + q + 1), b);
+        if (lane >= W) Ys = 0u;
+        guard = __funnelshift_r(yw(q - 1), yw(q), b);
+        sticky = __ballot_sync(FULL_MASK, lane < W && ((lane < q - 1 && Y != 0u) ||
+                                                       (lane == q - 1 && b != 0 && (Y & ((1u << b) - 1u)) != 0u))) != 0u;
+    }
+    // S = X + (Y ^ mask) + cin over the guard word and W words
+    const uint32_t mask = 0u - eff_sub;
+    const uint64_t tg = (uint64_t)(guard ^ mask) + (eff_sub & (sticky ? 0u : 1u));
+    uint32_t gsum = (uint32_t)tg;
+    const uint64_t sm = (lane < W) ? (uint64_t)X + (Ys ^ mask) : 0ull;
+    const uint32_t lo = (uint32_t)sm;
+    const uint64_t G = __ballot_sync(FULL_MASK, (sm >> 32) != 0u);
+    const uint64_t P = __ballot_sync(FULL_MASK, lane < W && lo == 0xffffffffu);
+    const uint64_t XG = G | P;
+    const uint64_t C = (XG + G + (tg >> 32)) ^ XG ^ G;   // bit i: carry into word i
+    uint32_t S = lo + (uint32_t)((C >> lane) & 1u);
+    if (lane >= W) S = 0u;
+    const uint32_t carry = (uint32_t)((C >> W) & 1u);
+    if ((eff_sub ^ 1u) & carry) {                 // an addition carried out: one bit right
+        sticky = sticky || (gsum & 1u) != 0u;
+        const uint32_t s0 = __shfl_sync(FULL_MASK, S, 0);
+        gsum = (gsum >> 1) | (s0 << 31);
+        const uint32_t nx = __shfl_down_sync(FULL_MASK, S, 1);
+        S = (S >> 1) | ((lane == W - 1 ? 1u : nx) << 31);
+        if (lane >= W) S = 0u;
+        e += 1;
+    }
+    // leading zeros of [S_{W-1} .. S_0, guard]; exact cancellation gives +0
+    const uint32_t nz = __ballot_sync(FULL_MASK, S != 0u);
+    if (nz == 0u && gsum == 0u) {
+        re = EXP_ZERO;
+        rsg = 0u;
+        return 0u;
+    }
+    int lz;
+    if (nz) {
+        const int tw = 31 - __clz(nz);
+        lz = 32 * (W - 1 - tw) + __clz(__shfl_sync(FULL_MASK, S, tw));
+    } else {
+        lz = 32 * W + __clz(gsum);
+    }
+    // shift left by lz over the virtual words V[0] = guard, V[k] = S_{k-1}
+    const int q = lz >> 5, b = lz & 31;
+    auto vw = [&](int k) -> uint32_t {
+        const uint32_t v = __shfl_sync(FULL_MASK, S, (k - 1) & 31);
+        if (k == 0) return gsum;
+        return (k >= 1 && k <= W) ? v : 0u;
+    };
+    uint32_t M = __funnelshift_l(vw(lane - q), vw(lane + 1 - q), b);
+    if (lane >= W) M = 0u;
+    const uint32_t below = (q == 0) ? (gsum << b) : 0u;
+    e -= lz;
+    M = warp_round<W>(M, below, sticky, e, rs);
+    re = e;
+    rsg = sx;
     return M;
 }
 
