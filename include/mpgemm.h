@@ -126,7 +126,8 @@ int mp_set_odd_policy(int policy);
 int mp_set_split_truncation(int on);
 
 /* LU settings used by mplu: panel width K (Sec. 4 block size, >= 1), the
- * trailing-update algorithm (MP_SIMPLE .. MP_WINOGRAD) and its cutoff. */
+ * trailing-update algorithm (MP_SIMPLE .. MP_WINOGRAD) and its cutoff
+ * (0: chosen by the library, as for mpgemm). */
 int mp_set_lu(int panel, int algo, int cutoff);
 
 /* Row exchanges in mplu: 1 (default) partial pivoting; 0 the paper's LU
@@ -157,6 +158,9 @@ size_t mpgemm_workspace_size(int64_t m, int64_t l, int64_t n, int32_t prec,
  *   algo   : MP_SIMPLE, MP_BLOCK, MP_STRASSEN, MP_WINOGRAD, MP_EXACT or MP_SPLIT;
  *   cutoff : Strassen/Winograd recurse while m, l and n all exceed it
  *            (n_min of Sec. 2, >= 1); below it the leaf product is Block.
+ *            0 lets the library choose (the cutoff measured fastest for the
+ *            precision class: 64 up to 1024 bits, 32 above); negative is
+ *            MP_ERR_ARG.
  * Every c_ij of Simple/Block is (((+0 + a_i1 b_1j) + a_i2 b_2j) + ...) with
  * each product and sum rounded; Strassen/Winograd evaluate the printed
  * formulas left to right with one rounding per matrix add/sub element.

@@ -575,6 +575,8 @@ static size_t lu_ws_bytes(int64_t n, int p, int panel, int algo, int cutoff, int
 }
 
 namespace mpg {
+int auto_cutoff(int p);
+
 // C := A B with the recursion's buffers carved from a caller-supplied device
 // block [base, base + bytes); nothing is allocated.  Returns MP_ERR_NOMEM if
 // the block is too small.  Used by the static-scratch entry point.
@@ -594,7 +596,7 @@ int gemm_in_block(int algo, int cutoff, int policy, int64_t m, int64_t l, int64_
 
 size_t gemm_scratch_bytes(int algo, int64_t m, int64_t l, int64_t n, int cutoff, int policy, int p)
 {
-    return gemm_ws_bytes(algo, m, l, n, cutoff, policy, limbs_of(p));
+    return gemm_ws_bytes(algo, m, l, n, cutoff == 0 ? auto_cutoff(p) : cutoff, policy, limbs_of(p));
 }
 
 bool gemm_args_ok(int64_t m, int64_t l, int64_t n, int32_t prec, int32_t algo, int32_t cutoff,
@@ -602,7 +604,7 @@ bool gemm_args_ok(int64_t m, int64_t l, int64_t n, int32_t prec, int32_t algo, i
 {
     if (!valid_prec(prec) || m < 0 || l < 0 || n < 0) return false;
     if (algo < MP_SIMPLE || algo > MP_WINOGRAD) return false;
-    if ((algo == MP_STRASSEN || algo == MP_WINOGRAD) && cutoff < 1) return false;
+    if ((algo == MP_STRASSEN || algo == MP_WINOGRAD) && cutoff < 0) return false;
     if (!valid_mat(A, m, l, prec) || !valid_mat(B, l, n, prec) || !valid_mat(C, m, n, prec))
         return false;
     return !(overlaps(C, A) || overlaps(C, B));
@@ -612,7 +614,7 @@ cudaStream_t current_stream() { return g_ts.stream; }
 
 size_t lu_scratch_bytes(int64_t n, int p, int panel, int algo, int cutoff, int policy)
 {
-    return lu_ws_bytes(n, p, panel, algo, cutoff, policy);
+    return lu_ws_bytes(n, p, panel, algo, cutoff == 0 ? auto_cutoff(p) : cutoff, policy);
 }
 
 // C_b = A_b B_b for a batch of equally shaped products by the Block kernel
@@ -644,6 +646,21 @@ int fill_zero_batched(BMat M, int64_t batch, int64_t rows, int64_t cols, int p, 
     return launch_status();
 }
 int current_odd_policy() { return g_ts.odd_policy; }
+
+// Strassen/Winograd cutoff for cutoff = 0: the value that was fastest for
+// Winograd on GB300 at n = 1024 and 2048 with cutoffs 16..256 (64 up to 1024
+// bits, 32 at 2048 bits, where a leaf product costs most against the
+// additions; the wide class takes 32 as well).  Leaves narrower than the
+// 32-column tile of the Block kernel waste lanes, so 16 was slowest always.
+int auto_cutoff(int p)
+{
+    return wclass(p) <= 32 ? 64 : 32;
+}
+
+int resolve_cutoff(int cutoff, int p)
+{
+    return cutoff == 0 ? auto_cutoff(p) : cutoff;
+}
 }  // namespace mpg
 
 // ======================================================================= ABI
@@ -673,7 +690,7 @@ int mp_set_odd_policy(int policy)
 
 int mp_set_lu(int panel, int algo, int cutoff)
 {
-    if (panel < 1 || algo < MP_SIMPLE || algo > MP_WINOGRAD || cutoff < 1) return MP_ERR_ARG;
+    if (panel < 1 || algo < MP_SIMPLE || algo > MP_WINOGRAD || cutoff < 0) return MP_ERR_ARG;
     g_ts.lu_panel = panel;
     g_ts.lu_algo = algo;
     g_ts.lu_cutoff = cutoff;
@@ -811,7 +828,8 @@ size_t mpgemm_workspace_size(int64_t m, int64_t l, int64_t n, int32_t prec, int3
     if (algo == MP_SPLIT)
         return (m > 0 && l > 0 && n > 0 && valid_prec(prec)) ? split_ws_bytes(m, l, n, prec) : 0;
     if (algo != MP_STRASSEN && algo != MP_WINOGRAD) return 0;
-    if (cutoff < 1 || m <= 0 || l <= 0 || n <= 0 || !valid_prec(prec)) return 0;
+    if (cutoff < 0 || m <= 0 || l <= 0 || n <= 0 || !valid_prec(prec)) return 0;
+    cutoff = resolve_cutoff(cutoff, prec);
     auto lv = plan(m, l, n, cutoff, g_ts.odd_policy);
     if (lv.size() <= 1) return 0;
     return recursion_bytes(lv, limbs_of(prec));
@@ -822,7 +840,8 @@ int mpgemm(int64_t m, int64_t l, int64_t n, int32_t prec, int32_t algo, int32_t 
 {
     if (!valid_prec(prec) || m < 0 || l < 0 || n < 0) return MP_ERR_ARG;
     if (algo < MP_SIMPLE || algo > MP_SPLIT) return MP_ERR_ARG;
-    if ((algo == MP_STRASSEN || algo == MP_WINOGRAD) && cutoff < 1) return MP_ERR_ARG;
+    if ((algo == MP_STRASSEN || algo == MP_WINOGRAD) && cutoff < 0) return MP_ERR_ARG;
+    cutoff = resolve_cutoff(cutoff, prec);
     if (!valid_mat(A, m, l, prec) || !valid_mat(B, l, n, prec) || !valid_mat(C, m, n, prec))
         return MP_ERR_ARG;
     if (overlaps(C, A) || overlaps(C, B)) return MP_ERR_ARG;
@@ -873,7 +892,8 @@ int mpgemm_batched(int64_t batch, int64_t m, int64_t l, int64_t n, int32_t prec,
 size_t mplu_workspace_size(int64_t n, int32_t prec)
 {
     if (n <= 0 || !valid_prec(prec)) return 0;
-    return lu_ws_bytes(n, prec, g_ts.lu_panel, g_ts.lu_algo, g_ts.lu_cutoff, g_ts.odd_policy);
+    return lu_ws_bytes(n, prec, g_ts.lu_panel, g_ts.lu_algo, resolve_cutoff(g_ts.lu_cutoff, prec),
+                       g_ts.odd_policy);
 }
 
 int mplu(int64_t n, int32_t prec, mpmat_t *A, int64_t *piv, const mpmat_t *b, mpmat_t *x)
@@ -888,7 +908,7 @@ int mplu(int64_t n, int32_t prec, mpmat_t *A, int64_t *piv, const mpmat_t *b, mp
     cudaStream_t s = g_ts.stream;
     DevStatus *st = status_ptr();
     if (!st) return MP_ERR_CUDA;
-    const int K = g_ts.lu_panel, algo = g_ts.lu_algo, cutoff = g_ts.lu_cutoff;
+    const int K = g_ts.lu_panel, algo = g_ts.lu_algo, cutoff = resolve_cutoff(g_ts.lu_cutoff, prec);
     const int policy = g_ts.odd_policy;
     const bool pivoting = g_ts.lu_pivoting;
     const int L = limbs_of(prec);

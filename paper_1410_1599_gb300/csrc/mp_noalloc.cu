@@ -20,6 +20,7 @@ int gemm_in_block(int algo, int cutoff, int policy, int64_t m, int64_t l, int64_
                   const mpmat_t *A, const mpmat_t *B, mpmat_t *C, void *base, size_t bytes,
                   cudaStream_t s);
 size_t gemm_scratch_bytes(int algo, int64_t m, int64_t l, int64_t n, int cutoff, int policy, int p);
+int resolve_cutoff(int cutoff, int p);
 bool gemm_args_ok(int64_t m, int64_t l, int64_t n, int32_t prec, int32_t algo, int32_t cutoff,
                   const mpmat_t *A, const mpmat_t *B, const mpmat_t *C);
 cudaStream_t current_stream();
@@ -64,6 +65,7 @@ extern "C" int mpgemm_noalloc(int64_t m, int64_t l, int64_t n, int32_t prec, int
 {
     using namespace mpg;
     if (!gemm_args_ok(m, l, n, prec, algo, cutoff, A, B, C)) return MP_ERR_ARG;
+    cutoff = resolve_cutoff(cutoff, prec);
     const int policy = current_odd_policy();
     const size_t need = gemm_scratch_bytes(algo, m, l, n, cutoff, policy, prec);
     if (need > (size_t)MP_NOALLOC_SCRATCH_BYTES) return MP_ERR_SCRATCH;

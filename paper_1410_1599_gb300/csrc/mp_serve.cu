@@ -141,8 +141,7 @@ struct mp_server {
                    gemm_scratch_bytes(r.algo, r.m, r.l, r.n, r.cutoff, MP_PEEL, p);
         const int64_t n = r.m;
         return mat_size(p, n, n) + 2 * mat_size(p, n, 1) + align256((size_t)n * 8) +
-               lu_scratch_bytes(n, p, r.lu_panel > 0 ? r.lu_panel : 128, r.algo,
-                                r.cutoff > 0 ? r.cutoff : 64, MP_PEEL);
+               lu_scratch_bytes(n, p, r.lu_panel > 0 ? r.lu_panel : 128, r.algo, r.cutoff, MP_PEEL);
     }
 
     static size_t batch_bytes(int p, int64_t b, int64_t count)
@@ -246,7 +245,7 @@ struct mp_server {
             mat_on(g->B, p, n, 1, g->mem + sa);
             mat_on(g->C, p, n, 1, g->mem + sa + sv);
             g->piv = (int64_t *)(g->mem + sa + 2 * sv);
-            mp_set_lu(r.lu_panel > 0 ? r.lu_panel : 128, r.algo, r.cutoff > 0 ? r.cutoff : 64);
+            mp_set_lu(r.lu_panel > 0 ? r.lu_panel : 128, r.algo, r.cutoff);
         }
         cudaGraph_t graph = nullptr;
         int rc = MP_ERR_CUDA;
@@ -360,7 +359,7 @@ struct mp_server {
             mat_on(b, p, n, 1, mem + sa);
             mat_on(x, p, n, 1, mem + sa + sv);
             int64_t *piv = (int64_t *)(mem + sa + 2 * sv);
-            mp_set_lu(r.lu_panel > 0 ? r.lu_panel : 128, r.algo, r.cutoff > 0 ? r.cutoff : 64);
+            mp_set_lu(r.lu_panel > 0 ? r.lu_panel : 128, r.algo, r.cutoff);
             rc = h2d(A, r.a_limb, r.a_exp, r.a_sign, st);
             if (rc == MP_OK) rc = h2d(b, r.b_limb, r.b_exp, r.b_sign, st);
             if (rc == MP_OK) rc = mplu(n, p, &A, piv, &b, &x);
@@ -560,7 +559,7 @@ int mp_server_submit(mp_server_t *s, const mp_request_t *req)
     if (r.prec < MP_PREC_MIN || r.prec > MP_PREC_MAX || r.m < 0 || r.l < 0 || r.n < 0) return MP_ERR_ARG;
     if (r.kind == MP_REQ_GEMM) {
         if (r.algo < MP_SIMPLE || r.algo > MP_WINOGRAD) return MP_ERR_ARG;
-        if ((r.algo >= MP_STRASSEN) && r.cutoff < 1) return MP_ERR_ARG;
+        if ((r.algo >= MP_STRASSEN) && r.cutoff < 0) return MP_ERR_ARG;
         if (r.m * r.l && (!r.a_limb || !r.a_exp || !r.a_sign)) return MP_ERR_ARG;
         if (r.l * r.n && (!r.b_limb || !r.b_exp || !r.b_sign)) return MP_ERR_ARG;
         if (r.m * r.n && (!r.c_limb || !r.c_exp || !r.c_sign)) return MP_ERR_ARG;

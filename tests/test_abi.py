@@ -36,6 +36,11 @@ def test_host_only_calls():
     assert lib.mp_strerror(-3) == b"zero pivot: matrix is singular"
     assert lib.mp_set_odd_policy(7) == -1
     assert lib.mp_set_lu(0, 0, 64) == -1
+    assert lib.mp_set_lu(128, 3, -1) == -1 and lib.mp_set_lu(128, 3, 0) == 0 and lib.mp_set_lu(128, 0, 64) == 0
+    # cutoff 0: the library's choice, 64 up to 1024 bits and 32 above
+    for p, c in ((512, 64), (1024, 64), (2048, 32)):
+        assert lib.mpgemm_workspace_size(1000, 1000, 1000, p, 3, 0) == \
+            lib.mpgemm_workspace_size(1000, 1000, 1000, p, 3, c) > 0
     assert lib.mp_set_lu_pivoting(2) == -1
     assert lib.mp_set_lu_pivoting(0) == 0 and lib.mp_set_lu_pivoting(1) == 0
     assert lib.mp_set_split_truncation(3) == -1

@@ -119,3 +119,14 @@ def test_exact_and_split_reject_wide_precision(algo):
     with pytest.raises(mp.MPError) as e:
         mp.mpgemm(dev(A), dev(A), dC, algo)
     assert e.value.code == -7
+
+
+@pytest.mark.parametrize("p,auto", [(512, 64), (2048, 32)])
+def test_automatic_cutoff(p, auto):
+    """cutoff 0: the library picks the cutoff (64 up to 1024 bits, 32 at
+    2048); the bits equal the oracle's Winograd at that cutoff."""
+    m = 133 if p == 512 else 70
+    A = gen.uniform_pm1(m, m, p, 61, -16, 16)
+    B = gen.uniform_pm1(m, m, p, 62, -16, 16)
+    want = orc.gemm(orc.WINOGRAD, A, B, cutoff=auto)
+    assert_bits_equal(gemm(A, B, mp.WINOGRAD, 0), want, "automatic cutoff p=%d" % p)
