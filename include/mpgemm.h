@@ -139,7 +139,9 @@ int mp_set_lu_pivoting(int on);
 
 /* R = X op Y elementwise on rows x cols views of equal shape and precision,
  * op 0 add, 1 subtract, 2 multiply, 3 divide (Sec. 1: one correct rounding
- * per operation).  R may alias X or Y exactly (same pointers and strides).
+ * per operation); ops 4..7 are the same four operations formed by one warp
+ * per element (the latency-bound form the LU solves use; same bits; up to
+ * 1024 bits, MP_ERR_UNSUPPORTED above).  R may alias X or Y exactly (same pointers and strides).
  * A division by zero leaves that entry untouched and makes mp_sync_status()
  * return MP_ERR_ARG. */
 int mp_elementwise(int op, const mpmat_t *X, const mpmat_t *Y, mpmat_t *R);

@@ -1,6 +1,7 @@
 // gemm_w32.cu -- elementwise and GEMM kernels, 32-word (1024-bit) capacity class.
-#include "mp_kernels.cuh"
+#include "mp_warp.cuh"
 
 namespace mpg {
 MPG_INSTANTIATE_GEMM(32)
+MPG_INSTANTIATE_WARP(32)
 }  // namespace mpg

@@ -781,9 +781,10 @@ int mp_profile_read(int cls, int64_t *launches, double *ms, double *units)
 
 int mp_elementwise(int op, const mpmat_t *X, const mpmat_t *Y, mpmat_t *R)
 {
-    if (op < 0 || op > 3 || !X || !Y || !R) return MP_ERR_ARG;
+    if (op < 0 || op > 7 || !X || !Y || !R) return MP_ERR_ARG;
     const int p = X->prec;
     if (!valid_prec(p)) return MP_ERR_ARG;
+    if (op >= 4 && wclass(p) > 32) return MP_ERR_UNSUPPORTED;
     const int64_t rows = X->rows, cols = X->cols;
     if (!valid_mat(X, rows, cols, p) || !valid_mat(Y, rows, cols, p) || !valid_mat(R, rows, cols, p))
         return MP_ERR_ARG;
@@ -798,8 +799,12 @@ int mp_elementwise(int op, const mpmat_t *X, const mpmat_t *Y, mpmat_t *R)
     if (!st) return MP_ERR_CUDA;
     Prof pr(MP_K_ELEMENTWISE, (double)rows * cols, g_ts.stream);
     dispatch(p, [&](auto w) {
-        launch_elementwise<decltype(w)::value>(op, bmat(X), bmat(Y), bmat(R), rows, cols, p, st,
-                                               g_ts.stream);
+        constexpr int WW = decltype(w)::value;
+        if (op < 4) {
+            launch_elementwise<WW>(op, bmat(X), bmat(Y), bmat(R), rows, cols, p, st, g_ts.stream);
+        } else if constexpr (WW <= 32) {
+            launch_elementwise_warp<WW>(op - 4, bmat(X), bmat(Y), bmat(R), rows, cols, p, st, g_ts.stream);
+        }
     });
     return launch_status();
 }

@@ -42,6 +42,11 @@ template <int W>
 void launch_elementwise(int op, BMat X, BMat Y, BMat R, int64_t rows, int64_t cols, int p,
                         DevStatus *st, cudaStream_t s);
 
+// the same operations with one warp per element (W <= 32; mp_warp.cuh)
+template <int W>
+void launch_elementwise_warp(int op, BMat X, BMat Y, BMat R, int64_t rows, int64_t cols, int p,
+                             DevStatus *st, cudaStream_t s);
+
 template <int W>
 void launch_convert(BMat X, int px, BMat R, int pr, int64_t rows, int64_t cols,
                     DevStatus *st, cudaStream_t s);

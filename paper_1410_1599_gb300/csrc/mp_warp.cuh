@@ -415,4 +415,55 @@ MP_DEV bool wst(uint32_t w, int64_t e, uint32_t s, const BMat &M, int64_t b, int
     return e != EXP_ZERO && (e > EXP_LIMIT || e < -EXP_LIMIT);
 }
 
+
+// R = X op Y elementwise with one warp per element (op 0 add, 1 subtract,
+// 2 multiply, 3 divide): the warp routines above, for call sites that want
+// the latency of one operation rather than throughput.  Same bits as the
+// one-thread operations.
+template <int W>
+__global__ void __launch_bounds__(128) elementwise_warp_kernel(int op, BMat X, BMat Y, BMat R, int64_t rows,
+                                                               int64_t cols, int p, DevStatus *status)
+{
+    const RoundSpec rs = make_spec<W>(p);
+    const int lane = (int)(threadIdx.x & 31u);
+    const int64_t total = rows * cols;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    bool bad = false, dz = false;
+    for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < total; t += nw) {
+        const int64_t r = t / cols, c = t % cols;
+        int64_t xe, ye, ze;
+        uint32_t xs, ys, zs;
+        const uint32_t xm = wld<W>(X, 0, r, c, rs.L, xe, xs);
+        const uint32_t ym = wld<W>(Y, 0, r, c, rs.L, ye, ys);
+        uint32_t zm;
+        if (op == 0 || op == 1) {
+            zm = warp_add<W>(xm, xe, xs, ym, ye, ys, (uint32_t)op, ze, zs, rs);
+        } else if (op == 2) {
+            zm = warp_mul<W>(xm, xe, xs, ym, ye, ys, ze, zs, rs);
+        } else {
+            if (ye == EXP_ZERO) {
+                dz = true;
+                continue;
+            }
+            zm = warp_div<W>(xm, xe, xs, ym, ye, ys, ze, zs, rs);
+        }
+        bad |= wst<W>(zm, ze, zs, R, 0, r, c, rs.L);
+    }
+    if (lane == 0 && bad) flag(status, ST_RANGE);
+    if (lane == 0 && dz) flag(status, ST_DIVZERO);
+}
+
+template <int W>
+void launch_elementwise_warp(int op, BMat X, BMat Y, BMat R, int64_t rows, int64_t cols, int p,
+                             DevStatus *st, cudaStream_t s)
+{
+    const int64_t total = rows * cols;
+    if (total <= 0) return;
+    elementwise_warp_kernel<W><<<grid_for(total * 32, 128), 128, 0, s>>>(op, X, Y, R, rows, cols, p, st);
+}
+
+#define MPG_INSTANTIATE_WARP(W)                                                                 \
+    template void launch_elementwise_warp<W>(int, BMat, BMat, BMat, int64_t, int64_t, int,      \
+                                             DevStatus *, cudaStream_t);
+
 }  // namespace mpg

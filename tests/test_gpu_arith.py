@@ -85,6 +85,41 @@ def test_elementwise_matches_oracle(op, p):
         assert_bits_equal(dR.to_host(), want, "%s p=%d" % (op, p))
 
 
+@pytest.mark.parametrize("p", [2, 53, 64, 127, 128, 200, 256, 300, 512, 1000, 1024])
+@pytest.mark.parametrize("op", ["add", "sub", "mul", "div"])
+def test_warp_elementwise_matches_oracle(op, p):
+    """ops 4..7: the warp-cooperative add, subtract, multiply and divide of
+    the LU solves (one warp per element, lane = word) on the same edge-case
+    pairs (ties, carries, cancellation, exponent gaps, zeros) and wide
+    exponent spreads; every bit equals the oracle's."""
+    X, Y = _edge_pairs(p, 700, p * 17 + len(op))
+    if op == "div":
+        z = Y.exp == gen.EXP_ZERO
+        Y.exp[z] = 1
+        Y.limb[0][z] = np.uint64(1 << 63)
+    U = gen.uniform_pm1(1, 300, p, 7, -40, 40)
+    V = gen.uniform_pm1(1, 300, p, 8, -40, 40)
+    if op == "div":
+        z = V.exp == gen.EXP_ZERO
+        V.exp[z] = 3
+        V.limb[0][z] = np.uint64(1 << 63)
+    for A, B in ((X, Y), (U, V)):
+        want, rc = orc.scalar(op, A, B)
+        assert rc == 0
+        dR = mp.DeviceMP.empty(1, A.shape[1], p)
+        mp.elementwise(OPS[op] + 4, dev(A), dev(B), dR)
+        mp.check_status(op)
+        assert_bits_equal(dR.to_host(), want, "warp %s p=%d" % (op, p))
+
+
+def test_warp_elementwise_rejects_wide():
+    A = gen.uniform_pm1(1, 4, 2048, 1)
+    dR = mp.DeviceMP.empty(1, 4, 2048)
+    with pytest.raises(mp.MPError) as e:
+        mp.elementwise(4, dev(A), dev(A), dR)
+    assert e.value.code == -7
+
+
 @pytest.mark.parametrize("op", ["add", "sub", "mul", "div"])
 def test_p53_matches_ieee_double(op):
     rng = np.random.default_rng(17)

@@ -56,7 +56,7 @@ def test_small_random_pivoting(panel, algo, cutoff):
     check(A, panel, algo, cutoff)
 
 
-@pytest.mark.parametrize("p", [128, 256, 1024])
+@pytest.mark.parametrize("p", [128, 256, 300, 512, 1024])
 @pytest.mark.parametrize("algo,cutoff", [(mp.SIMPLE, 64), (mp.WINOGRAD, 16)])
 def test_well_conditioned_ragged_panels(p, algo, cutoff):
     n = 75 if p == 1024 else 150
