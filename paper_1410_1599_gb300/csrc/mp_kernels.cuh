@@ -2,6 +2,8 @@
 // Sec. 2), instantiated once per word-capacity class W by gemm_w*.cu and
 // rec_w*.cu.
 #pragma once
+#include <mutex>
+
 #include "mp_arith.cuh"
 #include "mp_internal.h"
 
@@ -641,12 +643,11 @@ void launch_gemm_block(BMat A, BMat B, BMat C, int64_t batch, int64_t m, int64_t
     } else {
         using Cfg = BlockSmCfg<W>;
         const int64_t tm = (m + Cfg::BM - 1) / Cfg::BM, tn = (n + Cfg::BN - 1) / Cfg::BN;
-        static bool attr = false;
-        if (!attr) {
+        static std::once_flag once;                  // one GPU per process
+        std::call_once(once, [] {
             cudaFuncSetAttribute(gemm_block_sm_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Cfg::smem());
-            attr = true;
-        }
+        });
         gemm_block_sm_kernel<W><<<(unsigned)(batch * tm * tn), Cfg::THREADS, Cfg::smem(), s>>>(
             A, B, C, m, l, n, p, tm, tn, st);
     }

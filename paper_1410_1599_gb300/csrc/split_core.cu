@@ -27,6 +27,7 @@
 // unwinds (tensor memory is released on every path).
 #include <cstdio>
 #include <cstdlib>
+#include <mutex>
 
 #include "mpgemm.h"
 #include "mp_split.cuh"
@@ -362,16 +363,35 @@ int launch_split_slices(const __half *pa, const __half *pb, int64_t m, int64_t l
         if (std::getenv("MPGEMM_DEBUG")) std::fprintf(stderr, "split: tensor map encoding failed\n");
         return MP_ERR_UNSUPPORTED;
     }
-    static bool attr = false;
-    if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(split_slice_tc_kernel,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-        if (e != cudaSuccess) {
-            if (std::getenv("MPGEMM_DEBUG"))
-                std::fprintf(stderr, "split: shared memory attribute: %s\n", cudaGetErrorString(e));
-            return MP_ERR_CUDA;
+    // once per process (one GPU per process): the shared-memory opt-in and
+    // the number of clusters resident at once
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    static int resident = 0;
+    std::call_once(once, [] {
+        attr_err = cudaFuncSetAttribute(split_slice_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)SMEM_BYTES);
+        if (attr_err != cudaSuccess) return;
+        cudaLaunchConfig_t q = {};
+        q.blockDim = dim3(THREADS);
+        q.dynamicSmemBytes = SMEM_BYTES;
+        q.gridDim = dim3(CSIZE * (152 / CSIZE));
+        cudaLaunchAttribute qa[1];
+        qa[0].id = cudaLaunchAttributeClusterDimension;
+        qa[0].val.clusterDim.x = CSIZE;
+        qa[0].val.clusterDim.y = 1;
+        qa[0].val.clusterDim.z = 1;
+        q.attrs = qa;
+        q.numAttrs = 1;
+        if (cudaOccupancyMaxActiveClusters(&resident, split_slice_tc_kernel, &q) != cudaSuccess || resident <= 0) {
+            (void)cudaGetLastError();                   // clear a failed query
+            resident = 144 / CSIZE;
         }
-        attr = true;
+    });
+    if (attr_err != cudaSuccess) {
+        if (std::getenv("MPGEMM_DEBUG"))
+            std::fprintf(stderr, "split: shared memory attribute: %s\n", cudaGetErrorString(attr_err));
+        return MP_ERR_CUDA;
     }
     Sched sc;
     sc.S = S;
@@ -396,14 +416,6 @@ int launch_split_slices(const __half *pa, const __half *pb, int64_t m, int64_t l
     attr_cl[0].val.clusterDim.z = 1;
     cfg.attrs = attr_cl;
     cfg.numAttrs = 1;
-    static int resident = 0;
-    if (resident <= 0) {
-        cfg.gridDim = dim3(CSIZE * (152 / CSIZE));
-        if (cudaOccupancyMaxActiveClusters(&resident, split_slice_tc_kernel, &cfg) != cudaSuccess || resident <= 0) {
-            (void)cudaGetLastError();                   // clear a failed query
-            resident = 144 / CSIZE;
-        }
-    }
     const int64_t clusters = resident;
     int groups = 1;
     while (quads * groups < 8 * clusters && groups * 2 <= 2 * S - 1 - s0) groups *= 2;
