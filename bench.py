@@ -13,6 +13,7 @@ bounded sample of the same workload instead.
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -580,24 +581,26 @@ def lu_run(n, p, algo, panel=128, cutoff=64, kind="well"):
     mp.elementwise(mp.OP_SUB, wx, one, fe)
     mp.check_status("lu residual")
 
-    def dbl(M):
-        H = M.to_host()
-        f = H.limb[0].astype(np.float64) * 2.0 ** -64
-        e = np.where(H.exp == gen.EXP_ZERO, -10 ** 6, H.exp).clip(-1000, 1000)
-        v = f * np.exp2(e.astype(np.float64))
-        return np.where(H.sign == 1, -v, v)
-
-    a = np.abs(dbl(dA0)).sum(axis=1).max()
-    xn = np.abs(dbl(dx)).max()
-    bn = np.abs(dbl(db)).max()
-    back = float(np.abs(dbl(r)).max() / (a * xn + bn))
-    fwd = float(np.abs(dbl(fe)).max())
+    # norms in log2 space: the residual and the error of x sit near 2^-p,
+    # below the double range at 1024 bits and above
+    la = _log2abs(dA0)
+    rowmax = la.max(axis=1, keepdims=True)
+    rowmax = np.where(np.isfinite(rowmax), rowmax, 0.0)
+    l_anorm = float((rowmax[:, 0] + np.log2(np.exp2(la - rowmax).sum(axis=1))).max())
+    l_xn, l_bn = float(_log2abs(dx).max()), float(_log2abs(db).max())
+    hi = max(l_anorm + l_xn, l_bn)
+    l_den = hi + np.log2(np.exp2(l_anorm + l_xn - hi) + np.exp2(l_bn - hi))
+    l_back = float(_log2abs(r).max()) - l_den
+    l_fwd = float(_log2abs(fe).max())
+    back, fwd = float(2.0 ** l_back), float(2.0 ** l_fwd)
     return {"n": n, "prec": p, "algo": {0: "simple", 1: "block", 2: "strassen", 3: "winograd"}[algo],
             "panel": panel, "matrix": kind, "seconds": round(t, 4), "status": rc,
             "kernel_ms": {k: round(v[1], 2) for k, v in prof.items() if v[0]},
             "launches": int(sum(v[0] for v in prof.values())),
             "eff_gflops": round((2.0 / 3.0) * n ** 3 / t / 1e9, 4),
-            "backward_error": back, "forward_error": fwd}
+            "backward_error": back, "forward_error": fwd,
+            "backward_error_log10": round(l_back * math.log10(2.0), 2),
+            "forward_error_log10": round(l_fwd * math.log10(2.0), 2)}
 
 
 def lu_sweep_run(n=1024, precs=(256, 1024), algos=(0, 2, 3), alphas=range(1, 11), seed=21,
@@ -1027,33 +1030,38 @@ def paper_run(stream, precs=(128, 1024), square=True, rect=True):
 def cpu_baseline(A, B, seconds):
     """The oracle (plain C, all host threads) computing a sample of outputs of
     the same product by Simple dot products: eff GFLOP/s = 2 l outputs / t.
-    Only the sampled rows of A and the one column of B are handed over."""
+    The sample (rows x columns of C) grows until it takes about `seconds`;
+    only the sampled rows of A and columns of B are handed over."""
     import numpy as np
 
     from oracle import oracle as orc
 
     n, l = A.shape
+    ncols = B.shape[1]
     threads = orc.max_threads()
     rng = np.random.default_rng(0)
-    col = B.sub(np.arange(l), [int(rng.integers(0, B.shape[1]))])
 
     def run(count):
-        rows = np.sort(rng.choice(n, size=count, replace=False))
-        Asub = A.sub(rows, np.arange(l))
+        r = min(n, count)
+        c = min(ncols, max(1, -(-count // r)))
+        rows = np.sort(rng.choice(n, size=r, replace=False))
+        cols = np.sort(rng.choice(ncols, size=c, replace=False))
+        Asub, Bsub = A.sub(rows, np.arange(l)), B.sub(np.arange(l), cols)
         t0 = time.perf_counter()
-        orc.gemm(orc.SIMPLE, Asub, col)
-        return time.perf_counter() - t0
+        orc.gemm(orc.SIMPLE, Asub, Bsub)
+        return time.perf_counter() - t0, r, c
 
-    count, t = threads, run(threads)
-    while t < seconds / 8 and count < n:
-        count = min(n, count * 4)
-        t = run(count)
-    final = int(max(threads, min(n, count * seconds / max(t, 1e-9))))
-    t = run(final)
-    return {"value": round(2.0 * l * final / t / 1e9, 6), "unit": "GFLOP/s",
+    count = threads
+    t, r, c = run(count)
+    while t < seconds / 8 and r * c < n * ncols:
+        count = min(n * ncols, count * 4)
+        t, r, c = run(count)
+    count = int(max(threads, min(n * ncols, r * c * seconds / max(t, 1e-9))))
+    t, r, c = run(count)
+    return {"value": round(2.0 * l * r * c / t / 1e9, 6), "unit": "GFLOP/s",
             "cores": threads, "kind": "oracle",
-            "sample": "%d outputs of C by Simple dot products (l=%d), oracle C code, %d threads"
-                      % (final, l, threads), "seconds": round(t, 2)}
+            "sample": "%d x %d outputs of C by Simple dot products (l=%d), oracle C code, %d threads"
+                      % (r, c, l, threads), "seconds": round(t, 2)}
 
 
 # ----------------------------------------------------------- reference arm

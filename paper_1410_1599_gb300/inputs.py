@@ -202,9 +202,28 @@ def uniform_pm1(rows: int, cols: int, p: int, seed: int, exp_lo: int = 0,
                 exp_hi: int = 0) -> HostMP:
     """Entries v * 2^e, v uniform on the grid k / 2^(p-1), k in [-2^(p-1), 2^(p-1)),
     i.e. uniform in [-1, 1) and exact in p bits; e uniform in [exp_lo, exp_hi]."""
-    L = limbs_for(p)
+    M = HostMP.zeros(rows, cols, p)
     N = rows * cols
-    w = splitmix64(seed, N * (L + 1)).reshape(N, L + 1)
+    limb, exp, sign = M.limb.reshape(M.L, N), M.exp.reshape(N), M.sign.reshape(N)
+    # element t takes draws t(L+1)+1 .. t(L+1)+L+1; chunks keep the
+    # temporaries cache-sized and give the same values as one pass
+    for s0 in range(0, N, _CHUNK):
+        cnt = min(_CHUNK, N - s0)
+        mant, ex, neg = _uniform_pm1_flat(cnt, s0, p, seed, exp_lo, exp_hi)
+        limb[:, s0:s0 + cnt] = mant.T
+        exp[s0:s0 + cnt] = ex
+        sign[s0:s0 + cnt] = neg
+    return M
+
+
+_CHUNK = 1 << 12
+
+
+def _uniform_pm1_flat(N: int, first: int, p: int, seed: int, exp_lo: int, exp_hi: int):
+    """Entries first .. first+N-1 of uniform_pm1 in row-major order:
+    (N, L) mantissas, exponents (EXP_ZERO for zeros) and signs."""
+    L = limbs_for(p)
+    w = splitmix64(seed, N * (L + 1), first * (L + 1)).reshape(N, L + 1)
     neg = (w[:, 0] & np.uint64(1)).astype(np.int8)
     span = exp_hi - exp_lo + 1
     e = exp_lo + ((w[:, 0] >> np.uint64(1)) % np.uint64(span)).astype(np.int64)
@@ -231,11 +250,7 @@ def uniform_pm1(rows: int, cols: int, p: int, seed: int, exp_lo: int = 0,
         X[:, t] = s
     over = carry.astype(np.int64)
     mant, exp, zero = _normalize(X, over)
-    M = HostMP.zeros(rows, cols, p)
-    M.limb[:] = mant.T.reshape(L, rows, cols)
-    M.exp[:] = np.where(zero, EXP_ZERO, exp + e).reshape(rows, cols)
-    M.sign[:] = neg.reshape(rows, cols)
-    return M
+    return mant, np.where(zero, EXP_ZERO, exp + e), neg
 
 
 def rand_bits(seed: int, index: int, bits: int) -> int:
