@@ -115,3 +115,71 @@ def test_lotkin_wide_precision(p, pivoting):
     products, factors and solution bit for bit against the oracle."""
     A = gen.lotkin(32, p)
     check(A, 8, mp.WINOGRAD, 4, pivoting=pivoting)
+
+
+def _first_max_abs_row(A, col):
+    """Index of the first entry of largest magnitude in column col (exact)."""
+    mags = [abs(gen.entry_fraction(A, i, col)) for i in range(A.shape[0])]
+    best = max(mags)
+    return mags.index(best)
+
+
+def _log2abs(M):
+    """log2 |x| of every entry (-inf for zeros), from the top limb and the exponent."""
+    f = np.asarray(M.limb[0], dtype=np.float64) * 2.0 ** -64
+    with np.errstate(divide="ignore"):
+        out = np.log2(f) + np.asarray(M.exp, dtype=np.float64)
+    return np.where(np.asarray(M.exp) == gen.EXP_ZERO, -np.inf, out)
+
+
+@pytest.mark.parametrize("n,p,kind", [(1024, 256, "well"), (1024, 1024, "lotkin"),
+                                      (2048, 256, "lotkin"), (2048, 1024, "well")])
+def test_full_size_properties(n, p, kind):
+    """The LU workload at its full sizes (n = 1024 and 2048 at 256 and 1024
+    bits, U[-1,1) + nI and Lotkin, panel 128, Winograd trailing products,
+    cutoff 64: the launch configuration bench.py times), checked where the
+    oracle reaches one entry at a time and by properties that hold at any
+    size (Sec. 4 and partial pivoting):
+      - the first pivot is the first row of largest |a_i1|; row 1 of U is that
+        row of A, bit for bit; every multiplier of column 1 is the oracle's
+        RN(a_i1 / u_11) of the finally permuted row, bit for bit;
+      - piv is a sequence of exchanges (piv[k] >= k), the identity for the
+        diagonally dominant matrix; every multiplier has |l_ik| <= 1;
+      - sampled rows of the residual b - A x~, formed exactly by the
+        oracle, stay below n 2^-p (||A|| ||x~|| + ||b||)."""
+    A = gen.well_conditioned(n, p, 5) if kind == "well" else gen.lotkin(n, p)
+    b = gen.uniform_pm1(n, 1, p, 61)
+    F, piv, x, rc = gpu_lu(A, b, 128, mp.WINOGRAD, 64)
+    assert rc == 0
+    assert np.all(piv >= np.arange(n)) and np.all(piv < n)
+    if kind == "well":
+        assert np.array_equal(piv, np.arange(n))
+    sigma = np.arange(n)
+    for k in range(n):
+        sigma[[k, piv[k]]] = sigma[[piv[k], k]]
+    # column 1: pivot, first row of U, multipliers
+    assert sigma[0] == _first_max_abs_row(A, 0)
+    assert_bits_equal(F.sub([0], np.arange(n)), A.sub([sigma[0]], np.arange(n)), "first row of U")
+    q, _ = orc.scalar("div", A.sub(sigma[1:], [0]), A.sub(np.full(n - 1, sigma[0]), [0]))
+    assert_bits_equal(F.sub(np.arange(1, n), [0]), q, "multipliers of column 1")
+    # |l_ik| <= 1 below the diagonal: exponent <= 0, or exactly 1 (exponent 1, mantissa 1/2)
+    low = np.tril(np.ones((n, n), bool), -1)
+    e = np.asarray(F.exp)
+    zero = e == gen.EXP_ZERO
+    half = (np.asarray(F.limb[0]) == np.uint64(1 << 63)) & ~np.asarray(F.limb[1:]).any(axis=0)
+    assert np.all((zero | (e <= 0) | ((e == 1) & half))[low]), "a multiplier exceeds 1 in magnitude"
+    # residual of sampled rows, exact: [a_i, b_i] . [x~; -1] rounded once
+    rng = np.random.default_rng(n + p)
+    rows = np.unique(np.concatenate([[0, n - 1], rng.integers(0, n, 14)]))
+    Ar, br = A.sub(rows, np.arange(n)), b.sub(rows, [0])
+    Aaug = gen.HostMP(np.concatenate([Ar.limb, br.limb], axis=2), np.concatenate([Ar.exp, br.exp], axis=1),
+                      np.concatenate([Ar.sign, br.sign], axis=1), p)
+    m1 = gen.from_ints([[-1]], p)
+    Xaug = gen.HostMP(np.concatenate([x.limb, m1.limb], axis=1), np.concatenate([x.exp, m1.exp], axis=0),
+                      np.concatenate([x.sign, m1.sign], axis=0), p)
+    r = orc.dot_exact(Aaug, Xaug)
+    l_r = float(_log2abs(r).max())
+    l_a = float(np.log2(np.exp2(_log2abs(A)).sum(axis=1).max()))
+    l_x, l_b = float(_log2abs(x).max()), float(_log2abs(b).max())
+    l_den = max(l_a + l_x, l_b) + 1.0          # >= log2(||A|| ||x~|| + ||b||)
+    assert l_r <= l_den + np.log2(n) - p, "residual 2^%.1f above n 2^-p scale 2^%.1f" % (l_r, l_den + np.log2(n) - p)

@@ -138,3 +138,32 @@ def test_truncation_falls_back_on_cancellation(p):
     full, fb0 = _split(A, B, False)
     assert fb0 == 0
     assert_bits_equal(full, want, "full split with cancellation")
+
+
+def test_split_full_size_sampled():
+    """The split-form workload at its full size: 4096^3 at 1024 bits, entries
+    U[-1,1) * 2^e with e uniform in [-16, 16] (the inputs of bench.py --split),
+    truncated form (the default), the launch configuration that run times.
+    Sampled outputs, corners included, equal the oracle's correctly rounded
+    exact dot product computed one output at a time."""
+    import torch
+
+    p, n = 1024, 4096
+    A = gen.uniform_pm1(n, n, p, 13, -16, 16)
+    B = gen.uniform_pm1(n, n, p, 14, -16, 16)
+    dA, dB = mp.DeviceMP.from_host(A), mp.DeviceMP.from_host(B)
+    dC = mp.DeviceMP.empty(n, n, p)
+    mp.set_split_truncation(True)
+    mp.mpgemm(dA, dB, dC, mp.SPLIT, 64)
+    mp.check_status("split 4096")
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(4096)
+    rows = np.unique(np.concatenate([[0, n - 1], rng.integers(0, n, 10)]))
+    cols = np.unique(np.concatenate([[0, n - 1], rng.integers(0, n, 10)]))
+    r, c = torch.as_tensor(rows, device="cuda"), torch.as_tensor(cols, device="cuda")
+    got = gen.HostMP(dC.limb[:, r][:, :, c].cpu().numpy().view(np.uint64),
+                     dC.exp[r][:, c].cpu().numpy(), dC.sign[r][:, c].cpu().numpy(), p)
+    del dA, dB, dC
+    torch.cuda.empty_cache()
+    want = orc.dot_exact(A, B, rows=rows, cols=cols)
+    assert_bits_equal(got, want, "split 4096^3 sample")
