@@ -1077,12 +1077,16 @@ def run_reference(a, rank, world):
 
     from oracle import oracle as orc
     threads = orc.max_threads()
-    per_step = min(n, max(threads, int(256 * 512 / p)))
+    # a square block of outputs per step (the oracle spreads outputs over its
+    # threads; a block keeps each thread's A rows and B columns in cache)
+    side = min(n, max(4, int(round((max(threads, 256 * 512 // p)) ** 0.5))))
+    per_step = side * side
     rng = np.random.default_rng(1)
     subs = []
     for s in range(a.warmup + a.steps):
-        rows = np.sort(rng.choice(n, size=per_step, replace=False))
-        subs.append((A.sub(rows, np.arange(n)), B.sub(np.arange(n), [s % n])))
+        rows = np.sort(rng.choice(n, size=side, replace=False))
+        cols = np.sort(rng.choice(n, size=side, replace=False))
+        subs.append((A.sub(rows, np.arange(n)), B.sub(np.arange(n), cols)))
     for s in range(a.warmup):
         orc.gemm(orc.SIMPLE, *subs[s])
     t0 = time.perf_counter()
@@ -1097,7 +1101,7 @@ def run_reference(a, rank, world):
             "config": workload_config(a),
             "cpu_baseline": {"value": round(value, 6), "unit": "GFLOP/s", "cores": threads,
                              "kind": "oracle",
-                             "sample": "%d outputs per step by Simple dot products (l=%d)" % (per_step, n)},
+                             "sample": "%d x %d outputs per step by Simple dot products (l=%d)" % (side, side, n)},
             "e2e": {"value": round(value, 6), "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
