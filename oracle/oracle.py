@@ -42,9 +42,11 @@ class OMat:
 
 
 def lib():
+    """The oracle library: ORACLE_LIB names another build of the same sources
+    (the mutation tests load deliberately broken copies this way)."""
     global _lib
     if _lib is None:
-        _lib = C.CDLL(_build.build())
+        _lib = C.CDLL(os.environ.get("ORACLE_LIB") or _build.build())
         _lib.orc_api_sample_set.restype = C.c_int64
         _lib.orc_api_max_threads.restype = C.c_int
     return _lib

@@ -148,6 +148,24 @@ def test_replay_blocked_lu(panel):
             assert entry_mpf(F, i, j) == ref[i][j], (i, j)
 
 
+def test_replay_pivot_ties():
+    """Equal pivot magnitudes: the first row of largest |a_ik| is taken
+    (ties to the lowest index, the reading stated for partial pivoting).
+    The first two columns hold ties of opposite sign at every elimination
+    step, so taking the last maximum would exchange other rows."""
+    p, n = 128, 6
+    rows = [[2, 1, 3, -1, 5, 7], [-2, 3, 1, 4, -2, 1], [2, -3, 2, 1, 3, -4],
+            [1, 3, -5, 2, 1, 2], [-1, 2, 4, -3, 2, 6], [1, -1, 2, 5, -6, 3]]
+    A = gen.from_ints(rows, p)
+    F, piv, rc = orc.lu(A, panel=2, algo=orc.SIMPLE)
+    assert rc == 0
+    ref, rpiv = _replay_lu([[entry_mpf(A, i, j) for j in range(n)] for i in range(n)], p, 2)
+    assert list(piv) == rpiv and rpiv[0] == 0
+    for i in range(n):
+        for j in range(n):
+            assert entry_mpf(F, i, j) == ref[i][j], (i, j)
+
+
 @pytest.mark.parametrize("panel", [1, 3, 9])
 def test_replay_unpivoted_lu(panel):
     """The paper's LU (Sec. 4, no pivoting) replayed with mpmath scalar ops."""
