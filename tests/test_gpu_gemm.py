@@ -130,3 +130,29 @@ def test_automatic_cutoff(p, auto):
     B = gen.uniform_pm1(m, m, p, 62, -16, 16)
     want = orc.gemm(orc.WINOGRAD, A, B, cutoff=auto)
     assert_bits_equal(gemm(A, B, mp.WINOGRAD, 0), want, "automatic cutoff p=%d" % p)
+
+
+@pytest.mark.parametrize("algo", ["simple", "block", "strassen", "winograd", "exact", "split"])
+@pytest.mark.parametrize("p", [256, 1024])
+def test_strided_views(algo, p):
+    """A, B and C as sub-blocks of larger matrices (row stride ld > cols,
+    nonzero offsets): the product equals the oracle's on the extracted
+    blocks bit for bit, and C's parent keeps every entry outside the view."""
+    m, l, n = 70, 45, 53
+    BigA = gen.uniform_pm1(m + 9, l + 13, p, 91, -8, 8)
+    BigB = gen.uniform_pm1(l + 5, n + 7, p, 92, -8, 8)
+    BigC = gen.uniform_pm1(m + 6, n + 11, p, 93)
+    dC = dev(BigC)
+    code = {"exact": mp.EXACT, "split": mp.SPLIT}.get(algo, ALGOS.get(algo))
+    mp.mpgemm(dev(BigA).view(4, 7, m, l), dev(BigB).view(3, 2, l, n), dC.view(5, 3, m, n), code, 16)
+    mp.check_status("strided %s" % algo)
+    got = dC.to_host()
+    A = BigA.sub(np.arange(4, 4 + m), np.arange(7, 7 + l))
+    B = BigB.sub(np.arange(3, 3 + l), np.arange(2, 2 + n))
+    want = orc.dot_exact(A, B) if algo in ("exact", "split") else orc.gemm(code, A, B, cutoff=16)
+    assert_bits_equal(got.sub(np.arange(5, 5 + m), np.arange(3, 3 + n)), want, "strided %s" % algo)
+    outside = np.ones(BigC.shape, bool)
+    outside[5:5 + m, 3:3 + n] = False
+    assert np.array_equal(got.exp[outside], BigC.exp[outside])
+    assert np.array_equal(got.sign[outside], BigC.sign[outside])
+    assert np.array_equal(got.limb[:, outside], BigC.limb[:, outside])

@@ -67,6 +67,15 @@ def test_well_conditioned_ragged_panels(p, algo, cutoff):
     assert err < 1e-20
 
 
+def test_pivot_ties():
+    """Tied pivot magnitudes (opposite signs) at two elimination steps: the
+    first row of largest |a_ik| is taken, as in the oracle."""
+    rows = [[2, 1, 3, -1, 5, 7], [-2, 3, 1, 4, -2, 1], [2, -3, 2, 1, 3, -4],
+            [1, 3, -5, 2, 1, 2], [-1, 2, 4, -3, 2, 6], [1, -1, 2, 5, -6, 3]]
+    for p in (128, 1024):
+        check(gen.from_ints(rows, p), 2, mp.SIMPLE, 64)
+
+
 def test_lotkin_ill_conditioned():
     A = gen.lotkin(48, 256)
     check(A, 16, mp.WINOGRAD, 8)
@@ -183,3 +192,42 @@ def test_full_size_properties(n, p, kind):
     l_x, l_b = float(_log2abs(x).max()), float(_log2abs(b).max())
     l_den = max(l_a + l_x, l_b) + 1.0          # >= log2(||A|| ||x~|| + ||b||)
     assert l_r <= l_den + np.log2(n) - p, "residual 2^%.1f above n 2^-p scale 2^%.1f" % (l_r, l_den + np.log2(n) - p)
+
+
+@pytest.mark.parametrize("p", [256, 1024])
+def test_strided_views(p):
+    """A, b and x as sub-blocks of larger matrices (ld > cols, offsets):
+    factors, pivots and solution equal the oracle's, and the parents keep
+    every entry outside the views."""
+    n = 40
+    A = gen.uniform_pm1(n, n, p, 95)
+    Big = gen.uniform_pm1(n + 7, n + 10, p, 96)
+    Big.limb[:, 3:3 + n, 6:6 + n] = A.limb
+    Big.exp[3:3 + n, 6:6 + n] = A.exp
+    Big.sign[3:3 + n, 6:6 + n] = A.sign
+    b = b_of(A)
+    Bb = gen.uniform_pm1(n + 4, 3, p, 97)
+    Bb.limb[:, 2:2 + n, 1] = b.limb[:, :, 0]
+    Bb.exp[2:2 + n, 1] = b.exp[:, 0]
+    Bb.sign[2:2 + n, 1] = b.sign[:, 0]
+    Xb = gen.uniform_pm1(n + 2, 4, p, 98)
+    dBig, dBb, dXb = dev(Big), dev(Bb), dev(Xb)
+    piv = torch.zeros(n, dtype=torch.int64, device="cuda")
+    mp.set_lu(16, mp.WINOGRAD, 8)
+    try:
+        mp.mplu(dBig.view(3, 6, n, n), piv, dBb.view(2, 1, n, 1), dXb.view(1, 2, n, 1))
+        assert mp.sync_status() == 0
+    finally:
+        mp.set_lu(128, mp.SIMPLE, 64)
+    Fo, pivo, rco = orc.lu(A, panel=16, algo=mp.WINOGRAD, cutoff=8)
+    assert rco == 0 and list(piv.cpu().numpy()) == list(pivo)
+    got = dBig.to_host()
+    assert_bits_equal(got.sub(np.arange(3, 3 + n), np.arange(6, 6 + n)), Fo, "strided factors")
+    xo = orc.lu_solve(Fo, pivo, b)
+    gx = dXb.to_host()
+    assert_bits_equal(gx.sub(np.arange(1, 1 + n), [2]), xo, "strided solution")
+    for H, M, (r0, c0, r, c) in ((got, Big, (3, 6, n, n)), (gx, Xb, (1, 2, n, 1)),
+                                 (dBb.to_host(), Bb, (0, 0, 0, 0))):
+        keep = np.ones(M.shape, bool)
+        keep[r0:r0 + r, c0:c0 + c] = False
+        assert np.array_equal(H.exp[keep], M.exp[keep]) and np.array_equal(H.limb[:, keep], M.limb[:, keep])
