@@ -156,3 +156,17 @@ def test_strided_views(algo, p):
     assert np.array_equal(got.exp[outside], BigC.exp[outside])
     assert np.array_equal(got.sign[outside], BigC.sign[outside])
     assert np.array_equal(got.limb[:, outside], BigC.limb[:, outside])
+
+
+@pytest.mark.parametrize("algo", ["simple", "block", "strassen", "winograd", "exact", "split"])
+def test_empty_outputs(algo):
+    """m = 0 or n = 0: nothing to compute; the call succeeds and writes nothing."""
+    p = 256
+    code = {"exact": mp.EXACT, "split": mp.SPLIT}.get(algo, ALGOS.get(algo))
+    for m, l, n in ((0, 5, 4), (4, 5, 0), (0, 0, 0)):
+        A = dev(gen.uniform_pm1(m, l, p, 1))
+        B = dev(gen.uniform_pm1(l, n, p, 2))
+        C = mp.DeviceMP.empty(m, n, p)
+        mp.mpgemm(A, B, C, code, 8)
+        mp.check_status("empty %s %s" % (algo, (m, l, n)))
+        assert C.to_host().exp.shape == (m, n)

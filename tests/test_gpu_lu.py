@@ -231,3 +231,11 @@ def test_strided_views(p):
         keep = np.ones(M.shape, bool)
         keep[r0:r0 + r, c0:c0 + c] = False
         assert np.array_equal(H.exp[keep], M.exp[keep]) and np.array_equal(H.limb[:, keep], M.limb[:, keep])
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+@pytest.mark.parametrize("p", [128, 1024, 8650])
+def test_tiny_systems(n, p):
+    """n = 1, 2, 3 (one pivot, one exchange, a one-column trailing product)."""
+    A = gen.uniform_pm1(n, n, p, 60 + n)
+    check(A, 2, mp.WINOGRAD, 1)
