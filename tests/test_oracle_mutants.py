@@ -7,8 +7,10 @@ fix-up, a reordered sum, a pivot or elimination step of Sec. 4 done another
 way, a dropped term of the exact dot product -- builds that copy, and runs the
 pin tests against it (ORACLE_LIB points the oracle at the copy).  At least one
 pin must fail.  A control run of the same pins against an unmodified copy,
-built the same way, must pass.  The mistakes live only in the temporary
-copies; the oracle's sources are never changed.
+built the same way, must pass.  The Python part (the Section 4 benchmark's
+exact product and error routine) gets the same treatment in a swapped-in
+copy of one function.  The mistakes live only in the temporary copies; the
+oracle's sources are never changed.
 """
 import os
 import shutil
@@ -127,3 +129,51 @@ def test_planted_mistake_is_caught(tmp_path, name, file, old, new, pins):
     rc, out = _run_pins(lib, pins)
     # 1: a pin failed; a negative code: the broken copy crashed a pin run
     assert rc == 1 or rc < 0, "mutant %s survived the pins (pytest exit %d):\n%s" % (name, rc, out)
+
+
+# The Section 4 benchmark part of the oracle is Python: its mistakes are
+# planted in a copy of one function, swapped in for the duration of the test.
+def _pins_sqrt():
+    from tests import test_oracle_sqrt as ts
+    return [lambda: ts.test_product_S_closed_form(5, 7, 6), lambda: ts.test_product_S_closed_form(30, 65, 1024),
+            lambda: ts.test_product_rows_rounded_once(128), lambda: ts.test_product_rows_rounded_once(512),
+            ts.test_rel_errors_pinned]
+
+
+PY_MUTANTS = [
+    ("S_sum_stops_one_term_early", "sqrt_product_S", "for k in range(1, l + 1)", "for k in range(1, l)"),
+    ("S_second_factor_off_by_one", "sqrt_product_S", "* (n - k + 1)", "* (n - k)"),
+    ("sqrt15_truncated", "_rn_sqrt15", "keep += 1", "keep += 0"),
+    ("sqrt15_exponent_off_by_one", "_rn_sqrt15", "return (1 if S < 0 else 0, keep, s - d)",
+     "return (1 if S < 0 else 0, keep, s - d + 1)"),
+    ("rel_error_absolute", "sqrt_rel_errors", "/ ((float(x) + r15) * r15)", "/ (float(x) + r15)"),
+    ("rel_error_wrong_sign_branch", "sqrt_rel_errors", "out[i, j] = 1.0 + float(-x) / r15",
+     "out[i, j] = float(-x) / r15"),
+]
+
+
+@pytest.mark.parametrize("name,func,old,new", PY_MUTANTS, ids=[m[0] for m in PY_MUTANTS])
+def test_planted_mistake_in_python_part_is_caught(monkeypatch, name, func, old, new):
+    import inspect
+    import textwrap
+
+    from oracle import oracle as orc
+
+    fn = getattr(orc, func)
+    src = textwrap.dedent(inspect.getsource(fn))
+    assert src.count(old) == 1, "the planted text must occur once: %r" % old
+    ns = dict(fn.__globals__)
+    exec(compile(src.replace(old, new), "<planted %s>" % name, "exec"), ns)
+    monkeypatch.setattr(orc, func, ns[func])
+    caught = 0
+    for pin in _pins_sqrt():
+        try:
+            pin()
+        except AssertionError:
+            caught += 1
+    assert caught > 0, "mutant %s survived the pins" % name
+
+
+def test_python_pins_pass_unmutated():
+    for pin in _pins_sqrt():
+        pin()
