@@ -84,6 +84,24 @@ MUTANTS = [
      "orc_get(&T, i, c, &t);\n                orc_add(&y, &y, &t, p);", LU),
     ("solve_skips_row_exchanges", "orc_lu.c",
      "if (piv[k] != k) { orc_num s = v[k]; v[k] = v[piv[k]]; v[piv[k]] = s; }", "(void)piv;", LU),
+    # interchange format, conversion, Block, operation counts, the unpivoted
+    # LU and the forward substitution
+    ("limb_halves_swapped_on_import", "orc_mat.c",
+     "x.m[2 * (L - 1 - k)] = (uint32_t)v;\n                x.m[2 * (L - 1 - k) + 1] = (uint32_t)(v >> 32);",
+     "x.m[2 * (L - 1 - k) + 1] = (uint32_t)v;\n                x.m[2 * (L - 1 - k)] = (uint32_t)(v >> 32);",
+     SCALAR),
+    ("conversion_drops_sign", "orc_num.c",
+     "orc_round_int(r, p_to, x->m, nwf, x->exp - 32 * (int64_t)nwf, 0, x->sign);",
+     "orc_round_int(r, p_to, x->m, nwf, x->exp - 32 * (int64_t)nwf, 0, 0);", SCALAR),
+    ("block_k_blocks_descending", "orc_gemm.c", "for (int64_t K = 0; K < l; K += nb) {",
+     "for (int64_t K = ((l - 1) / nb) * nb; K >= 0; K -= nb) {", GEMM),
+    ("winograd_count_eight_combination_sums", "orc_gemm.c", "cc_ = algo == ORC_STRASSEN ? 8 : 7;",
+     "cc_ = algo == ORC_STRASSEN ? 8 : 8;", GEMM),
+    ("pivoting_flag_ignored", "orc_lu.c", "for (int64_t i = k + 1; pivoting && i < n; ++i) {",
+     "for (int64_t i = k + 1; i < n; ++i) {", LU),
+    ("forward_substitution_adds", "orc_lu.c",
+     "orc_sub(&v[i], &v[i], &t, p);\n        }\n    for (int64_t j = n - 1; j >= 0; --j) {",
+     "orc_add(&v[i], &v[i], &t, p);\n        }\n    for (int64_t j = n - 1; j >= 0; --j) {", LU),
     # correctly rounded exact dot product
     ("exact_dot_sign_of_a_only", "orc_num.c", "big_add_at((a[k].sign ^ b[k].sign) ? neg : pos",
      "big_add_at(a[k].sign ? neg : pos", LU),

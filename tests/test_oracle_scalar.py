@@ -152,7 +152,8 @@ def test_division_by_zero_reported():
 def test_convert_roundtrip_and_rounding():
     p = 256
     rnd = random.Random(5)
-    vals = [man_exp(rnd.getrandbits(256) | (1 << 255), -256 - rnd.randint(0, 9)) for _ in range(50)]
+    vals = [man_exp((rnd.getrandbits(256) | (1 << 255)) * rnd.choice((1, -1)), -256 - rnd.randint(0, 9))
+            for _ in range(50)]
     X = from_mpf_list(vals, p, (1, 50))
     W = orc.convert(X, 512)
     assert all(entry_mpf(W, 0, i) == vals[i] for i in range(50))
