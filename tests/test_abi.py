@@ -64,3 +64,24 @@ def test_argument_errors_without_gpu():
     Cm = binding.MPMat(128, 0, 2, 2, 2, 4, 4096, 8192, 12288)    # aliases A
     assert lib.mpgemm(2, 3, 2, 128, 0, 64, ctypes.byref(A), ctypes.byref(B), ctypes.byref(Cm)) == -1
     assert lib.mpgemm(2, 3, 2, 128, 9, 64, ctypes.byref(A), ctypes.byref(B), ctypes.byref(A)) == -1
+
+
+def test_noalloc_limit_checked_on_the_host():
+    """mpgemm_noalloc rejects a product whose recursion needs more than its
+    static scratch before any CUDA call, and an empty product returns at
+    once; the limit is the recursion's workspace size.  (Only paths that
+    never reach the device are taken here: the pointers are placeholders.)"""
+    lib = binding.load_library()
+    limit = binding.NOALLOC_SCRATCH_BYTES
+    p = 512
+    for n in (256, 300, 512):
+        assert lib.mpgemm_workspace_size(n, n, n, p, 3, 64) > limit
+        A = binding.MPMat(p, 0, n, n, n, n * n, 1 << 20, 1 << 30, 1 << 31)
+        B = binding.MPMat(p, 0, n, n, n, n * n, 1 << 32, 1 << 33, 1 << 34)
+        Cm = binding.MPMat(p, 0, n, n, n, n * n, 1 << 35, 1 << 36, 1 << 37)
+        assert lib.mpgemm_noalloc(n, n, n, p, 3, 64, ctypes.byref(A), ctypes.byref(B), ctypes.byref(Cm)) == -8
+    assert lib.mpgemm_workspace_size(200, 200, 200, p, 3, 64) <= limit
+    E = binding.MPMat(p, 0, 0, 5, 5, 0, 0, 0, 0)
+    F = binding.MPMat(p, 0, 5, 4, 4, 20, 1 << 20, 1 << 30, 1 << 31)
+    G = binding.MPMat(p, 0, 0, 4, 4, 0, 0, 0, 0)
+    assert lib.mpgemm_noalloc(0, 5, 4, p, 3, 64, ctypes.byref(E), ctypes.byref(F), ctypes.byref(G)) == 0
