@@ -326,7 +326,7 @@ def run_ours(a, rank, world, local):
 
     extras, extras_lu, serving, by_prec, split_small, other_configs = {}, None, None, {}, None, None
     serving_repeat = None
-    if not a.no_extras and rank == 0:
+    if not a.no_extras and rank == 0 and world == 1:      # the scaling runs report the headline only
         for name in ("simple", "block", "strassen", "winograd"):
             if name == a.algo:
                 extras[name] = round(value / world, 3)
