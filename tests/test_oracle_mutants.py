@@ -73,6 +73,10 @@ MUTANTS = [
     # sampled recursion: the closure must hold both halves' partner rows
     ("sampled_closure_partner_missing", "orc_sampled.c",
      "if (!rc && C.v[i] + half < x && iset_add(S, C.v[i] + half)) rc = -1;", "(void)half;", GEMM),
+    ("sampled_rank1_fixup_missing", "orc_sampled.c",
+     "if (Lr < l) {                                   /* peeled l: rank-1 */", "if (0) {", GEMM),
+    ("sampled_b_quadrant_rows_from_the_column_half", "orc_sampled.c", "int64_t rr = r + (q / 2) * k;",
+     "int64_t rr = r + (q % 2) * k;", GEMM),
     # LU (Sec. 4) with partial pivoting
     ("pivot_last_of_equal_magnitudes", "orc_lu.c", "if (orc_cmpabs(&x, &best, p) > 0) {",
      "if (orc_cmpabs(&x, &best, p) >= 0) {", LU),
