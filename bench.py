@@ -1079,7 +1079,7 @@ def run_reference(a, rank, world):
     threads = orc.max_threads()
     # a square block of outputs per step (the oracle spreads outputs over its
     # threads; a block keeps each thread's A rows and B columns in cache)
-    side = min(n, max(4, int(round((max(threads, 256 * 512 // p)) ** 0.5))))
+    side = min(n, max(4, int(round((16 * max(threads, 256 * 512 // p)) ** 0.5))))   # ~0.2 s per step
     per_step = side * side
     rng = np.random.default_rng(1)
     subs = []
