@@ -160,3 +160,28 @@ def test_convert_roundtrip_and_rounding():
     N = orc.convert(X, 128)
     for i in range(50):
         assert entry_mpf(N, 0, i) == rn(vals[i], 128)
+
+
+def test_search_for_disagreements_with_mpmath():
+    """A shrinking search (hypothesis) over precisions, mantissa lengths,
+    exponent gaps and signs for any disagreement with mpmath's correctly
+    rounded add, sub, mul and div."""
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=400, deadline=None, derandomize=True)
+    @hyp.given(st.integers(2, 700), st.integers(1, 700), st.integers(1, 700), st.integers(0, 2 ** 700),
+               st.integers(0, 2 ** 700), st.integers(-720, 720), st.booleans(), st.booleans(),
+               st.sampled_from(["add", "sub", "mul", "div"]))
+    def check(p, bx, by, mx, my, gap, nx, ny, op):
+        bx, by = min(bx, p), min(by, p)
+        mx = (mx % (1 << bx)) | (1 << (bx - 1))       # exactly bx significant bits
+        my = (my % (1 << by)) | (1 << (by - 1))
+        x = man_exp(-mx if nx else mx, -bx)
+        y = man_exp(-my if ny else my, gap - by)
+        X, Y = from_mpf_list([x], p, (1, 1)), from_mpf_list([y], p, (1, 1))
+        R, rc = orc.scalar(op, X, Y)
+        assert rc == 0
+        assert entry_mpf(R, 0, 0) == OPS[op](x, y, p), (p, x, y, op)
+
+    check()
