@@ -314,3 +314,28 @@ def test_error_bounds_and_ordering():
     assert errs[orc.STRASSEN] <= (12 ** d) * (cutoff ** 2 + 5 * cutoff)
     assert errs[orc.WINOGRAD] <= (18 ** d) * (cutoff ** 2 + 6 * cutoff)
     assert errs[orc.STRASSEN] > errs[orc.SIMPLE] and errs[orc.WINOGRAD] > errs[orc.SIMPLE]
+
+
+def test_search_shapes_against_the_replay():
+    """A shrinking search (hypothesis) over shapes 1..13, cutoffs 1..4, both
+    odd-size policies, both recursions and exponent ranges, for any
+    disagreement between the oracle and the mpmath replay of the printed
+    formulas."""
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=150, deadline=None, derandomize=True)
+    @hyp.given(st.integers(1, 13), st.integers(1, 13), st.integers(1, 13), st.integers(1, 4),
+               st.sampled_from([orc.PEEL, orc.MIXED]), st.sampled_from([orc.STRASSEN, orc.WINOGRAD]),
+               st.integers(0, 20), st.integers(0, 10 ** 6))
+    def check(m, l, n, cutoff, policy, algo, spread, seed):
+        p = 96
+        A = gen.uniform_pm1(m, l, p, seed, -spread, spread)
+        B = gen.uniform_pm1(l, n, p, seed + 1, -spread, spread)
+        R = orc.gemm(algo, A, B, cutoff=cutoff, policy=policy)
+        ref = _rec(_mat(A), _mat(B), p, algo, cutoff, policy, m, l, n)
+        for i in range(m):
+            for j in range(n):
+                assert entry_mpf(R, i, j) == ref[i][j], (m, l, n, cutoff, policy, algo, i, j)
+
+    check()
