@@ -254,3 +254,29 @@ def test_exact_dot_cancellation_and_single_term():
     B = gen.uniform_pm1(1, 1, p, 94)
     R = orc.dot_exact(A, B)
     assert entry_mpf(R, 0, 0) == mp_mul(entry_mpf(A, 0, 0), entry_mpf(B, 0, 0), p)
+
+
+def test_search_against_the_replay():
+    """A shrinking search (hypothesis) over sizes 1..10, panel widths,
+    pivoting on and off and exponent ranges, for any disagreement between
+    the oracle's blocked LU and the mpmath replay of Sec. 4."""
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=80, deadline=None, derandomize=True)
+    @hyp.given(st.integers(1, 10), st.integers(1, 10), st.booleans(), st.integers(0, 12),
+               st.integers(0, 10 ** 6))
+    def check(n, panel, pivoting, spread, seed):
+        p = 96
+        A = gen.uniform_pm1(n, n, p, seed, -spread, spread)
+        F, piv, rc = orc.lu(A, panel=panel, algo=orc.SIMPLE, pivoting=pivoting)
+        if rc != 0:                       # a zero pivot (unpivoted): nothing to compare
+            return
+        ref, rpiv = _replay_lu([[entry_mpf(A, i, j) for j in range(n)] for i in range(n)], p, panel,
+                               pivoting=pivoting)
+        assert list(piv) == rpiv
+        for i in range(n):
+            for j in range(n):
+                assert entry_mpf(F, i, j) == ref[i][j], (n, panel, pivoting, i, j)
+
+    check()
