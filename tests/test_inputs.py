@@ -65,3 +65,18 @@ def test_well_conditioned_and_lotkin():
         for j in range(n):
             exact = Fraction(1, i + j + 1)
             assert abs(fl[i][j] - exact) <= exact / 2 ** p
+
+
+@pytest.mark.parametrize("rows,cols,p", [(70, 130, 256), (3, 5000, 64), (41, 211, 1024), (9, 1000, 53)])
+def test_uniform_generator_is_independent_of_chunking(monkeypatch, rows, cols, p):
+    """The generator works through the entries in chunks; entry t always takes
+    the draws t(L+1)+1 .. t(L+1)+L+1, so the matrix is the same for any chunk
+    size (one pass, the default, and a tiny one)."""
+    ref = None
+    for chunk in (1 << 30, gen._CHUNK, 97):
+        monkeypatch.setattr(gen, "_CHUNK", chunk)
+        M = gen.uniform_pm1(rows, cols, p, 123, -16, 16)
+        if ref is None:
+            ref = M
+        else:
+            assert M.equal(ref), chunk
