@@ -239,3 +239,33 @@ def test_tiny_systems(n, p):
     """n = 1, 2, 3 (one pivot, one exchange, a one-column trailing product)."""
     A = gen.uniform_pm1(n, n, p, 60 + n)
     check(A, 2, mp.WINOGRAD, 1)
+
+
+@pytest.mark.parametrize("n", [256, 384])
+@pytest.mark.parametrize("p", [256, 1024])
+@pytest.mark.parametrize("kind", ["well", "lotkin", "uniform"])
+def test_config_lu_bit_exact(n, p, kind):
+    """The LU workload's own setup (Sec. 4 steps 1-3 with partial pivoting:
+    panel 128, trailing products by Winograd with cutoff 64) over two and
+    three panels, so that several trailing products recurse one level and
+    the multi-CTA column steps, U12 solves and row exchanges all run:
+    factors, piv and x bit for bit against the oracle.  U[-1,1) + nI
+    (no exchanges), the Lotkin matrix and plain U[-1,1) (exchanges at most
+    steps)."""
+    if kind == "well":
+        A = gen.well_conditioned(n, p, 5)
+    elif kind == "lotkin":
+        A = gen.lotkin(n, p)
+    else:
+        A = gen.uniform_pm1(n, n, p, 71)
+    check(A, 128, mp.WINOGRAD, 64)
+
+
+@pytest.mark.parametrize("kind", ["well", "lotkin"])
+def test_config_lu_bit_exact_n1024(kind):
+    """One full-size LU of the workload (n = 1024 at 256 bits, panel 128,
+    Winograd cutoff 64: eight panels, the configuration bench.py times):
+    every entry of the factors, the pivots and the solution bit for bit
+    against the oracle (about half a minute of oracle time on 16 cores)."""
+    A = gen.well_conditioned(1024, 256, 5) if kind == "well" else gen.lotkin(1024, 256)
+    check(A, 128, mp.WINOGRAD, 64)
