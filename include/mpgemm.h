@@ -112,7 +112,11 @@ enum {
 int mp_set_stream(void *stream);
 
 /* Caller-owned device buffer used as workspace by later calls of this
- * thread (NULL / 0 to let the library allocate).  Always MP_OK. */
+ * thread (NULL / 0 to let the library allocate).  Always MP_OK.  It must be
+ * device memory of the device the calls run on: MP_SPLIT refuses any other
+ * buffer (host, managed or another GPU's memory) with MP_ERR_ARG before it
+ * launches anything, because its tensor-core kernel reads the buffer with
+ * TMA loads multicast inside a thread-block cluster. */
 int mp_set_workspace(void *ptr, size_t bytes);
 
 /* Odd-dimension policy for Strassen / Winograd (MP_PEEL or MP_MIXED). */
@@ -189,31 +193,36 @@ int mpgemm_batched(int64_t batch, int64_t m, int64_t l, int64_t n, int32_t prec,
                    const mpmat_t *A, const mpmat_t *B, mpmat_t *C);
 
 /*
- * mpgemm_noalloc -- the same product as mpgemm, for callers that cannot
- * allocate device memory when they multiply (work issued while a stream is
- * being captured into a CUDA graph, serving loops that must not touch an
- * allocator, hosts whose device memory is owned elsewhere).  The paper has
- * no counterpart: it is a deployment variant, not part of the method.
+ * mpgemm_noalloc -- C := A B like mpgemm, for callers that cannot allocate
+ * device memory when they multiply: real-time or serving loops that must
+ * not touch an allocator (an allocation can synchronise the device and
+ * stall the loop), code that runs inside an allocator or memory-pool
+ * callback of a host framework (calling back into the allocator there can
+ * deadlock), and hosts whose device memory is all handed out in advance by
+ * another owner (a new allocation fails).  The paper has no counterpart: it
+ * is a deployment variant, not part of the method.
  *
  * It allocates nothing: Strassen/Winograd temporaries live in one
  * file-scope static device array of MP_NOALLOC_SCRATCH_BYTES (64 MiB), which
  * every GPU that loads the library holds until the process exits; Simple
- * and Block need none.  Arguments, results and the per-thread stream and
- * odd-dimension policy are those of mpgemm; the caller still provides A, B
- * and C.
+ * and Block need none.  The caller still provides A, B and C.
+ *   - algo: MP_SIMPLE, MP_BLOCK, MP_STRASSEN or MP_WINOGRAD, with the
+ *     arguments, results, per-thread stream and odd-dimension policy of
+ *     mpgemm (the same bits); MP_EXACT and MP_SPLIT return
+ *     MP_ERR_UNSUPPORTED; anything else MP_ERR_ARG.
  *   - A product whose recursion needs more than the array holds is rejected
  *     with MP_ERR_SCRATCH before anything is launched (Winograd with cutoff
  *     64 fits n = 200 at 512 bits and n = 256 at 256 bits, not n = 256 at
  *     512 bits).
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) once; make that first call before any stream
- *     capture.
+ *   - The first call on a device looks up the device addresses of the array
+ *     and of a static status word (cudaGetSymbolAddress) once; make that
+ *     first call before any stream capture.
  *   - Every call uses the same array and leaves its contents behind; the
  *     recursion writes every temporary before reading it.  Calls whose work
  *     overlaps on the GPU (other streams, other host threads) race on the
  *     array: serialise them.
- *   - Exponent-range overflow is not recorded for mp_sync_status() by this
- *     entry point (the status word would need allocated memory).
+ *   - Exponent-range overflow is recorded in the static status word and
+ *     reported by the next mp_sync_status() on that device (MP_ERR_RANGE).
  */
 #define MP_NOALLOC_SCRATCH_BYTES (64u << 20)
 int mpgemm_noalloc(int64_t m, int64_t l, int64_t n, int32_t prec, int32_t algo, int32_t cutoff,
@@ -331,11 +340,16 @@ enum {
     MP_K_COMBINE = 3,    /* Strassen/Winograd C combinations */
     MP_K_FIXUP = 4,      /* peel fix-ups (rank-1 update, last row / column) */
     MP_K_ELEMENTWISE = 5,/* mp_elementwise, mp_convert, fills */
-    MP_K_LU = 6,         /* LU panel, row exchange, TRSM, trailing subtract, solves */
+    MP_K_LU = 6,         /* LU panel: pivot searches, column steps, row exchanges */
     MP_K_SPLIT = 7,      /* split form: digit-product (tensor core) kernel */
     MP_K_SPLIT_AUX = 8,  /* split form: alignment, recombination, wide fallback */
     MP_K_EXACT = 9,      /* exact-dot GEMM kernel */
-    MP_K_COUNT = 10
+    MP_K_LU_TRSM = 10,   /* LU: U rows by the unit lower triangle (Sec. 4 step 2) */
+    MP_K_LU_UPDATE = 11, /* LU: subtractions of the earlier columns' updates (inside
+                            a panel by the subtracting Block kernel; A22 - T after a
+                            trailing product) */
+    MP_K_LU_SOLVE = 12,  /* LU: row permutation of b and the two substitutions */
+    MP_K_COUNT = 13
 };
 
 /* While enabled (on != 0), every kernel the library launches from the

@@ -39,9 +39,10 @@ EXPORTS = ["mp_set_stream", "mp_set_workspace", "mp_set_odd_policy", "mp_set_lu"
 REQ_GEMM, REQ_LU_SOLVE = 0, 1
 REQ_DONE, REQ_PENDING, REQ_RUNNING, REQ_CANCELLED, REQ_FAILED = 0, 1, 2, 3, 4
 
-K_LEAF, K_SIMPLE, K_OPERANDS, K_COMBINE, K_FIXUP, K_ELEMENTWISE, K_LU, K_SPLIT, K_SPLIT_AUX, K_EXACT = range(10)
-K_NAMES = ["leaf_gemm", "simple_gemm", "operands", "combine", "fixup", "elementwise", "lu",
-           "split_slices", "split_aux", "exact_gemm"]
+(K_LEAF, K_SIMPLE, K_OPERANDS, K_COMBINE, K_FIXUP, K_ELEMENTWISE, K_LU, K_SPLIT, K_SPLIT_AUX, K_EXACT,
+ K_LU_TRSM, K_LU_UPDATE, K_LU_SOLVE) = range(13)
+K_NAMES = ["leaf_gemm", "simple_gemm", "operands", "combine", "fixup", "elementwise", "lu_panel",
+           "split_slices", "split_aux", "exact_gemm", "lu_trsm", "lu_update", "lu_solve"]
 
 
 class MPError(RuntimeError):

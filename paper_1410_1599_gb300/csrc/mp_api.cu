@@ -440,6 +440,11 @@ size_t split_ws_bytes(int64_t m, int64_t l, int64_t n, int p)
 int run_split(int64_t m, int64_t l, int64_t n, int p, BMat A, BMat B, BMat C, Workspace &ws,
               DevStatus *st, cudaStream_t s)
 {
+    // The digit planes are read by TMA loads multicast across the CTAs of a
+    // cluster; they must be this GPU's own device memory (a caller's
+    // workspace on another device, or host / managed memory, is refused
+    // before anything is launched).
+    if (!on_current_device(ws.base)) return MP_ERR_ARG;
     const size_t mk = ws.mark();
     const size_t S = (size_t)split_digit_count(p), lp = (size_t)split_row_pad(l);
     __half *pa = (__half *)ws.take(S * m * lp * 2);
@@ -582,7 +587,7 @@ int auto_cutoff(int p);
 // the block is too small.  Used by the static-scratch entry point.
 int gemm_in_block(int algo, int cutoff, int policy, int64_t m, int64_t l, int64_t n, int p,
                   const mpmat_t *A, const mpmat_t *B, mpmat_t *C, void *base, size_t bytes,
-                  cudaStream_t s)
+                  DevStatus *st, cudaStream_t s)
 {
     const size_t need = gemm_ws_bytes(algo, m, l, n, cutoff, policy, limbs_of(p));
     if (need > bytes) return MP_ERR_NOMEM;
@@ -591,7 +596,7 @@ int gemm_in_block(int algo, int cutoff, int policy, int64_t m, int64_t l, int64_
     ws.size = bytes;
     ws.used = 0;
     ws.s = s;
-    return gemm_core(algo, cutoff, policy, m, l, n, p, bmat(A), bmat(B), bmat(C), ws, nullptr, s);
+    return gemm_core(algo, cutoff, policy, m, l, n, p, bmat(A), bmat(B), bmat(C), ws, st, s);
 }
 
 size_t gemm_scratch_bytes(int algo, int64_t m, int64_t l, int64_t n, int cutoff, int policy, int p)
@@ -732,6 +737,8 @@ int mp_sync_status(void)
         DevStatus init{0u, 0u, INT64_MAX, 0ull};
         cudaMemcpy(st, &init, sizeof init, cudaMemcpyHostToDevice);
     }
+    // conditions recorded by mpgemm_noalloc in its own static status word
+    h.flags |= noalloc_take_flags();
     g_ts.split_fallbacks = (long long)h.split_fallbacks;
     g_ts.singular_col = (h.singular_col == INT64_MAX) ? -1 : h.singular_col;
     if (h.flags & ST_TIMEOUT) return MP_ERR_TIMEOUT;
@@ -934,14 +941,55 @@ int mplu(int64_t n, int32_t prec, mpmat_t *A, int64_t *piv, const mpmat_t *b, mp
         for (int64_t j0 = 0; j0 < n && rc == MP_OK; j0 += K) {
             const int64_t je = std::min<int64_t>(j0 + K, n);
             {
-                Prof pr(MP_K_LU, (double)(je - j0) * (n - j0), s);
                 if (fused) {
-                    // exchanges on the panel's columns now, on the rest after the panel
-                    launch_lu_pivot<WW>(A0, n, j0, piv, prec, st, s, j0, je, pivoting);
-                    for (int64_t k = j0; k < je; ++k)
-                        launch_lu_column<WW>(A0, n, j0, k, je, piv, prec, st, cand, ticket, s, pivoting);
+                    // The panel in sub-panels of LU_SUB columns.  A sub-panel
+                    // [c0, c1) first takes the updates of the panel's earlier
+                    // columns k in [j0, c0) on its own columns from row c0
+                    // down (subtracting Block product, k ascending), then is
+                    // factored column by column over its own columns only,
+                    // so that all rows below the current column stay in one
+                    // state and the row exchanges move consistent rows.
+                    // Afterwards its rows take their updates on the panel's
+                    // later columns: k in [j0, c0) by the subtracting Block
+                    // product, then k in [c0, c1) by the triangular solve.
+                    // Every element receives a_ij = RN(a_ij - RN(l_ik u_kj))
+                    // for the same k in the same order as in the
+                    // right-looking panel, and each latency-bound column step
+                    // is one multiply-add deep.  Row exchanges: the panel's
+                    // columns at once, the rest after the panel.
+                    {
+                        Prof pr(MP_K_LU, (double)(n - j0), s);
+                        launch_lu_pivot<WW>(A0, n, j0, piv, prec, st, s, j0, je, pivoting);
+                    }
+                    for (int64_t c0 = j0; c0 < je; c0 += LU_SUB) {
+                        const int64_t c1 = std::min<int64_t>(c0 + LU_SUB, je);
+                        if (c0 > j0) {
+                            {
+                                Prof pr(MP_K_LU_UPDATE, (double)(n - c0) * (c0 - j0) * (c1 - c0), s);
+                                launch_gemm_sub<WW>(sub_view(A0, c0, j0), sub_view(A0, j0, c0), sub_view(A0, c0, c0),
+                                                    n - c0, c0 - j0, c1 - c0, prec, st, s);
+                            }
+                            Prof pr(MP_K_LU, (double)(n - c0), s);
+                            launch_lu_pivot<WW>(A0, n, c0, piv, prec, st, s, j0, je, pivoting);
+                        }
+                        for (int64_t k = c0; k < c1; ++k) {
+                            Prof pr(MP_K_LU, (double)(c1 - k) * (n - k), s);
+                            launch_lu_column<WW>(A0, n, j0, k, je, c1, piv, prec, st, cand, ticket, s, pivoting);
+                        }
+                        if (c1 < je) {
+                            if (c0 > j0) {
+                                Prof pr(MP_K_LU_UPDATE, (double)(c1 - c0) * (c0 - j0) * (je - c1), s);
+                                launch_gemm_sub<WW>(sub_view(A0, c0, j0), sub_view(A0, j0, c1), sub_view(A0, c0, c1),
+                                                    c1 - c0, c0 - j0, je - c1, prec, st, s);
+                            }
+                            Prof pr(MP_K_LU_TRSM, (double)(c1 - c0) * (c1 - c0 - 1) / 2 * (je - c1), s);
+                            launch_lu_u12<WW>(A0, je, c0, c1, prec, st, s);
+                        }
+                    }
+                    Prof pr(MP_K_LU, (double)(n - (je - j0)), s);
                     launch_lu_laswp<WW>(A0, n, j0, je, piv, prec, s);
                 } else {
+                    Prof pr(MP_K_LU, (double)(je - j0) * (n - j0), s);
                     for (int64_t k = j0; k < je; ++k) {
                         launch_lu_pivot<WW>(A0, n, k, piv, prec, st, s, 0, n, pivoting);
                         launch_lu_divide<WW>(A0, n, k, prec, s);
@@ -951,7 +999,7 @@ int mplu(int64_t n, int32_t prec, mpmat_t *A, int64_t *piv, const mpmat_t *b, mp
             }
             if (je >= n) break;
             {
-                Prof pr(MP_K_LU, (double)(je - j0) * (je - j0) * (n - je) / 2, s);
+                Prof pr(MP_K_LU_TRSM, (double)(je - j0) * (je - j0 - 1) / 2 * (n - je), s);
                 if (fused)                                     // U12 = L11^-1 A12
                     launch_lu_u12<WW>(A0, n, j0, je, prec, st, s);
                 else
@@ -965,13 +1013,13 @@ int mplu(int64_t n, int32_t prec, mpmat_t *A, int64_t *piv, const mpmat_t *b, mp
             rc = gemm_core(algo, cutoff, policy, nt, je - j0, nt, prec, sub_view(A0, je, j0),
                            sub_view(A0, j0, je), Tv, ws, st, s);
             {
-                Prof pr(MP_K_LU, (double)nt * nt, s);
+                Prof pr(MP_K_LU_UPDATE, (double)nt * nt, s);
                 const BMat A22 = sub_view(A0, je, je);
                 launch_elementwise<WW>(1, A22, Tv, A22, nt, nt, prec, st, s);
             }
         }
         if (rc == MP_OK && x) {
-            Prof pr(MP_K_LU, (double)n * n, s);
+            Prof pr(MP_K_LU_SOLVE, (double)n * n, s);
             launch_lu_solve<WW>(A0, n, piv, bmat(b), y, bmat(x), perm, prec, st, s);
         }
     });

@@ -58,6 +58,10 @@ void launch_gemm_simple(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n,
 template <int W>
 void launch_gemm_block(BMat A, BMat B, BMat C, int64_t batch, int64_t m, int64_t l, int64_t n,
                        int p, DevStatus *st, cudaStream_t s);
+// C := C - A B, each c_ij = RN(c_ij - RN(a_ik b_kj)) for k ascending
+template <int W>
+void launch_gemm_sub(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p,
+                     DevStatus *st, cudaStream_t s);
 
 // one level of the recursion on a batch of `nodes` parents
 //   parent A: m x l (real), even sizes M x K, halves h = M/2, k = K/2
@@ -101,6 +105,13 @@ void launch_gemm_exact_list(BMat A, BMat B, BMat C, int64_t n, int64_t l, int p,
 // outputs whose rounding that bound leaves open are listed for the exact
 // limb kernel (eb < 0: nothing skipped, nothing listed).
 int split_digit_count(int p);
+// true when ptr is device memory of the calling thread's current device
+// (not host, managed or another GPU's memory); the split form's tensor maps
+// may only cover such memory
+bool on_current_device(const void *ptr);
+// flags mpgemm_noalloc recorded on the current device since the last call
+// (then cleared); 0 when it has never run there
+unsigned noalloc_take_flags();
 int64_t split_row_pad(int64_t l);
 int split_first_diagonal(int p, int64_t l, int64_t *ebits);
 template <int W>
@@ -131,14 +142,24 @@ void launch_lu_solve(BMat LU, int64_t n, const int64_t *piv, BMat b, BMat y, BMa
 // cand holds LU_COL_MAX_CTAS row slots; *ticket starts at 0 and is returned
 // to 0 by every launch.
 constexpr int64_t LU_COL_MAX_CTAS = 152 * 8;
+// sub-panel width of the fused panel factorisation: one column per lane of
+// the column step's row warps
+#ifndef MPG_LU_SUB
+#define MPG_LU_SUB 32
+#endif
+constexpr int64_t LU_SUB = MPG_LU_SUB;
 template <int W>
 bool lu_fused_ok(int64_t panel);
+// column step k of the panel [j0, je): row updates over columns (k, ce)
+// with ce <= je, row exchanges over the panel's columns
 template <int W>
-void launch_lu_column(BMat A, int64_t n, int64_t j0, int64_t k, int64_t je, int64_t *piv, int p,
-                      DevStatus *st, int64_t *cand, unsigned *ticket, cudaStream_t s, bool pivoting);
+void launch_lu_column(BMat A, int64_t n, int64_t j0, int64_t k, int64_t je, int64_t ce, int64_t *piv,
+                      int p, DevStatus *st, int64_t *cand, unsigned *ticket, cudaStream_t s, bool pivoting);
 template <int W>
 void launch_lu_laswp(BMat A, int64_t n, int64_t j0, int64_t je, const int64_t *piv, int p, cudaStream_t s);
+// rows [j0, je) of the columns [je, cend): U = L^-1 A with the unit lower
+// triangle L of rows and columns [j0, je)
 template <int W>
-void launch_lu_u12(BMat A, int64_t n, int64_t j0, int64_t je, int p, DevStatus *st, cudaStream_t s);
+void launch_lu_u12(BMat A, int64_t cend, int64_t j0, int64_t je, int p, DevStatus *st, cudaStream_t s);
 
 }  // namespace mpg

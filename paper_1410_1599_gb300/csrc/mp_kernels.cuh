@@ -132,7 +132,9 @@ template <int W> struct SimpleCfg {
     static constexpr int MIN_CTAS = (W <= 16) ? 3 : (is_big<W>() ? 4 : 1);
 };
 
-template <int W, bool BATCHED = false>
+// SUB: c starts from C's own entry and each product is subtracted,
+// c = RN(c - RN(a_ik b_kj)) for k ascending (the LU's elimination sequence).
+template <int W, bool BATCHED = false, bool SUB = false>
 __global__ void __launch_bounds__(32 * SimpleCfg<W>::TY, SimpleCfg<W>::MIN_CTAS)
 gemm_simple_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p,
                    DevStatus *status)
@@ -143,12 +145,13 @@ gemm_simple_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int 
     const int64_t bt = BATCHED ? (int64_t)blockIdx.z : 0;
     if (i >= m || j >= n) return;
     Mp<W> c, a, b, t;
-    set_zero<W>(c, 0u);
+    if (SUB) ld_rw<W>(c, C, bt, i, j, rs.L);
+    else set_zero<W>(c, 0u);
     for (int64_t k = 0; k < l; ++k) {
         ld<W>(a, A, bt, i, k, rs.L);
         ld<W>(b, B, bt, k, j, rs.L);
         mul<W, true>(t, a, b, rs);
-        add<W, true>(c, c, t, 0u, rs);
+        add<W, true>(c, c, t, SUB ? 1u : 0u, rs);
     }
     if (st<W>(c, C, bt, i, j, rs.L)) flag(status, ST_RANGE);
 }
@@ -165,10 +168,10 @@ gemm_simple_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int 
 // (mantissa words little-endian; B records padded so that a warp's 16-byte
 // loads hit every bank once).
 
-// top words of the truncated product a * b, b read from shared memory:
-// acc[q] = word W-2+q of sum_{i+j >= W-2} a_i b_j 2^(32(i+j))
+// rows of b words streamed from shared memory (four per 16-byte load); each
+// partial product with the row carry as one 64-bit multiply-add
 template <int W>
-MP_DEV void mul_trunc_sm(uint32_t (&acc)[W + 2], const uint32_t (&a)[W], const uint32_t *b)
+MP_DEV void mul_trunc_rows_sm(uint32_t (&acc)[W + 2], const uint32_t (&a)[W], const uint32_t *b)
 {
 #pragma unroll
     for (int q = 0; q < W + 2; ++q) acc[q] = 0u;
@@ -191,6 +194,55 @@ MP_DEV void mul_trunc_sm(uint32_t (&acc)[W + 2], const uint32_t (&a)[W], const u
             }
             acc[j + 2] = (uint32_t)c;                   // not yet written by any row
         }
+    }
+}
+
+// top words of the truncated product a * b, b read from shared memory:
+// acc[q] = word W-2+q of sum_{i+j >= W-2} a_i b_j 2^(32(i+j))
+//
+// Up to 1024 bits the product is formed column by column (product
+// scanning): the partial products of word s = i + j are summed into a
+// three-word accumulator by one multiply-add chain with carry flags
+// (mad.lo.cc, madc.hi.cc, addc), the low word leaves as word s and the
+// other two move down.  Each partial product costs one wide multiply-add
+// and one carry add -- about 30 % fewer instructions than rows of 64-bit
+// multiply-adds, whose row carries need separate adds (the 512-bit leaf
+// measured 682 against 871 instructions per multiply-add, same bits).  At
+// 2048 bits b does not fit in registers beside a, c and the product, and
+// rows of b words streamed from shared memory are used instead.
+template <int W>
+MP_DEV void mul_trunc_sm(uint32_t (&acc)[W + 2], const uint32_t (&a)[W], const uint32_t *bp)
+{
+    if constexpr (W <= 32) {
+        uint32_t b[W];
+#pragma unroll
+        for (int j0 = 0; j0 < W; j0 += 4) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(bp + j0);
+            b[j0] = v.x;
+            b[j0 + 1] = v.y;
+            b[j0 + 2] = v.z;
+            b[j0 + 3] = v.w;
+        }
+        uint32_t c0 = 0u, c1 = 0u, c2 = 0u;
+#pragma unroll
+        for (int s = W - 2; s <= 2 * W - 2; ++s) {
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+                const int j = s - i;
+                if (j < 0 || j >= W) continue;
+                asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
+                    "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
+                    "addc.u32 %2, %2, 0;"
+                    : "+r"(c0), "+r"(c1), "+r"(c2) : "r"(a[i]), "r"(b[j]));
+            }
+            acc[s - (W - 2)] = c0;
+            c0 = c1;
+            c1 = c2;
+            c2 = 0u;
+        }
+        acc[W + 1] = c0;
+    } else {
+        mul_trunc_rows_sm<W>(acc, a, bp);
     }
 }
 
@@ -281,7 +333,9 @@ template <int W> struct BlockSmCfg {
     }
 };
 
-template <int W>
+// SUB: c starts from C's own entry and the products are subtracted (see
+// gemm_simple_kernel).
+template <int W, bool SUB = false>
 __global__ void __launch_bounds__(BlockSmCfg<W>::THREADS, BlockSmCfg<W>::MIN_CTAS)
 gemm_block_sm_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p,
                      int64_t tiles_m, int64_t tiles_n, DevStatus *status)
@@ -308,7 +362,8 @@ gemm_block_sm_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, in
     const bool valid = (i < m) && (j < n);
 
     Mp<W> c, t;
-    set_zero<W>(c, 0u);
+    if (SUB && valid) ld_rw<W>(c, C, b, i, j, L);
+    else set_zero<W>(c, 0u);
     for (int64_t k0 = 0; k0 < l; k0 += BK) {
         const int kc = (int)((l - k0) < BK ? (l - k0) : BK);
         // limb q of a record goes to words W-2-2q (low half) and W-1-2q
@@ -358,7 +413,7 @@ gemm_block_sm_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, in
                 mul_sm<W>(t, am, sAe[ty * BK + kk], (uint32_t)(sAs[ty * BK + kk] & 1),
                           sB + (kk * BN + tx) * RB, sBe[kk * BN + tx],
                           (uint32_t)(sBs[kk * BN + tx] & 1), rs);
-                add_impl<W>(c, c, t, 0u, rs);
+                add_impl<W>(c, c, t, SUB ? 1u : 0u, rs);
             }
         }
         __syncthreads();
@@ -653,6 +708,31 @@ void launch_gemm_block(BMat A, BMat B, BMat C, int64_t batch, int64_t m, int64_t
     }
 }
 
+// C := C - A B with every element's products subtracted one by one,
+// k ascending (one product, not batched)
+template <int W>
+void launch_gemm_sub(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p,
+                     DevStatus *st, cudaStream_t s)
+{
+    if (m <= 0 || n <= 0 || l <= 0) return;
+    if constexpr (is_big<W>()) {
+        constexpr int ty = SimpleCfg<W>::TY;
+        dim3 block(32, ty);
+        dim3 grid((unsigned)((n + 31) / 32), (unsigned)((m + ty - 1) / ty));
+        gemm_simple_kernel<W, false, true><<<grid, block, 0, s>>>(A, B, C, m, l, n, p, st);
+    } else {
+        using Cfg = BlockSmCfg<W>;
+        const int64_t tm = (m + Cfg::BM - 1) / Cfg::BM, tn = (n + Cfg::BN - 1) / Cfg::BN;
+        static std::once_flag once;                  // one GPU per process
+        std::call_once(once, [] {
+            cudaFuncSetAttribute(gemm_block_sm_kernel<W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Cfg::smem());
+        });
+        gemm_block_sm_kernel<W, true><<<(unsigned)(tm * tn), Cfg::THREADS, Cfg::smem(), s>>>(
+            A, B, C, m, l, n, p, tm, tn, st);
+    }
+}
+
 template <int W>
 void launch_operands_a(int algo, BMat P, BMat Ch, int64_t nodes, int64_t m, int64_t l,
                        int64_t h, int64_t k, int p, cudaStream_t s)
@@ -710,6 +790,8 @@ void launch_border(BMat A, BMat B, BMat C, int64_t nodes, int64_t m, int64_t l, 
                                         DevStatus *, cudaStream_t);                             \
     template void launch_gemm_block<W>(BMat, BMat, BMat, int64_t, int64_t, int64_t, int64_t,    \
                                        int, DevStatus *, cudaStream_t);                         \
+    template void launch_gemm_sub<W>(BMat, BMat, BMat, int64_t, int64_t, int64_t, int,          \
+                                     DevStatus *, cudaStream_t);                                \
     template void launch_rank1<W>(BMat, BMat, BMat, int64_t, int64_t, int64_t, int64_t, int,    \
                                   DevStatus *, cudaStream_t);                                   \
     template void launch_border<W>(BMat, BMat, BMat, int64_t, int64_t, int64_t, int64_t,        \

@@ -288,9 +288,15 @@ __device__ void cta_swap_rows(const BMat &A, int64_t c0, int64_t c1, int64_t r1,
     }
 }
 
+// The row updates cover the columns k+1 .. ce-1 only (ce <= je, the end of
+// the current sub-panel): every row below k is in the same state, so row
+// exchanges keep the later columns' pending updates consistent.  Those
+// columns take this step's update later, in the same order (the subtracting
+// Block product for rows below the sub-panel, lu_u12_kernel for the
+// sub-panel's own rows).  The next pivot is picked when k+1 < ce.
 template <int W>
 __global__ void __launch_bounds__(LU_COL_WARPS * 32)
-lu_column_kernel(BMat A, int64_t n, int64_t j0, int64_t k, int64_t je, int64_t *piv, int p,
+lu_column_kernel(BMat A, int64_t n, int64_t j0, int64_t k, int64_t je, int64_t ce, int64_t *piv, int p,
                  DevStatus *status, int64_t *cand, unsigned *ticket, int pivoting)
 {
     static_assert(W <= 32, "warp-per-row column step");
@@ -298,12 +304,13 @@ lu_column_kernel(BMat A, int64_t n, int64_t j0, int64_t k, int64_t je, int64_t *
     const RoundSpec rs = make_spec<W>(p);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t nw = (int64_t)gridDim.x * LU_COL_WARPS;
-    const bool next = k + 1 < je;
+    const bool next = k + 1 < ce;
     __shared__ int64_t s_list[NT];
     __shared__ int64_t s_we[LU_COL_WARPS];
     __shared__ uint64_t s_wm[LU_COL_WARPS];
     __shared__ int s_nc;
     __shared__ int s_last;
+    __shared__ int64_t s_wrow[LU_COL_WARPS];
     int64_t de;
     uint32_t ds;
     const uint32_t dm = wld<W>(A, 0, k, k, rs.L, de, ds);
@@ -326,7 +333,7 @@ lu_column_kernel(BMat A, int64_t n, int64_t j0, int64_t k, int64_t je, int64_t *
         for (int w = 0; w < W; ++w) l.m[w] = __shfl_sync(0xffffffffu, qm, w);
         l.e = qe;
         l.s = qs;
-        for (int64_t j = k + 1 + lane; j < je; j += 32) {
+        for (int64_t j = k + 1 + lane; j < ce; j += 32) {
             Mp<W> u, y, z;
             ld_rw<W>(u, A, 0, k, j, rs.L);
             ld_rw<W>(y, A, 0, i, j, rs.L);
@@ -343,7 +350,6 @@ lu_column_kernel(BMat A, int64_t n, int64_t j0, int64_t k, int64_t je, int64_t *
     if (bad) flag(status, ST_RANGE);
     if (!next) return;
     // this CTA's candidate for the pivot of column k+1
-    __shared__ int64_t s_wrow[LU_COL_WARPS];
     if (lane == 0) s_wrow[wid] = best;
     __syncthreads();
     const int64_t cb = cta_pick_row<W, NT>(A, k + 1, LU_COL_WARPS, [&](int c) { return s_wrow[c]; }, rs,
@@ -379,13 +385,13 @@ lu_column_kernel(BMat A, int64_t n, int64_t j0, int64_t k, int64_t je, int64_t *
 }
 
 // ------------------------------------------- U12 = L11^-1 A12, one launch
-// One CTA per column j of A12 (grid-stride), thread t <-> panel row j0 + t
-// (panels of at most 128 columns).  Row r is final after the steps s < r;
-// it is then shared, and every row below takes a_ij = RN(a_ij - RN(l_ir a_rj))
-// -- per element the steps s = j0 .. i-1 in ascending order, as the
-// row-step launches do.
+// One CTA per column j in [je, cend) (grid-stride), thread t <-> panel row
+// j0 + t (panels of at most 128 columns).  Row r is final after the steps
+// s < r; it is then shared, and every row below takes
+// a_ij = RN(a_ij - RN(l_ir a_rj)) -- per element the steps s = j0 .. i-1 in
+// ascending order, as the row-step launches do.
 template <int W>
-__global__ void __launch_bounds__(128) lu_u12_kernel(BMat A, int64_t n, int64_t j0, int64_t je, int p,
+__global__ void __launch_bounds__(128) lu_u12_kernel(BMat A, int64_t cend, int64_t j0, int64_t je, int p,
                                                      DevStatus *status)
 {
     const RoundSpec rs = make_spec<W>(p);
@@ -393,15 +399,18 @@ __global__ void __launch_bounds__(128) lu_u12_kernel(BMat A, int64_t n, int64_t 
     const int64_t i = j0 + threadIdx.x;
     const bool mine = i < je;
     bool bad = false;
-    for (int64_t j = je + blockIdx.x; j < n; j += gridDim.x) {
-        Mp<W> y, l, x, z;
+    for (int64_t j = je + blockIdx.x; j < cend; j += gridDim.x) {
+        Mp<W> y, l, ln, x, z;
         if (mine) ld_rw<W>(y, A, 0, i, j, rs.L);
         if (threadIdx.x == 0) s_x = y;
+        if (mine && i > j0) ld_rw<W>(ln, A, 0, i, j0, rs.L);
         for (int64_t r = j0; r + 1 < je; ++r) {
             __syncthreads();                 // s_x = a_rj, final
             if (mine && i > r) {
+                l = ln;
+                // the next step's multiplier loads while this one multiplies
+                if (i > r + 1) ld_rw<W>(ln, A, 0, i, r + 1, rs.L);
                 x = s_x;
-                ld_rw<W>(l, A, 0, i, r, rs.L);
                 mul<W, true>(z, l, x, rs);
                 add<W, true>(y, y, z, 1u, rs);
             }
@@ -809,7 +818,7 @@ bool lu_fused_ok(int64_t panel)
 }
 
 template <int W>
-void launch_lu_column(BMat A, int64_t n, int64_t j0, int64_t k, int64_t je, int64_t *piv, int p,
+void launch_lu_column(BMat A, int64_t n, int64_t j0, int64_t k, int64_t je, int64_t ce, int64_t *piv, int p,
                       DevStatus *st, int64_t *cand, unsigned *ticket, cudaStream_t s, bool pivoting)
 {
     if constexpr (W <= 32) {
@@ -817,7 +826,7 @@ void launch_lu_column(BMat A, int64_t n, int64_t j0, int64_t k, int64_t je, int6
         if (rows <= 0) return;
         int64_t g = (rows + LU_COL_WARPS - 1) / LU_COL_WARPS;
         if (g > LU_COL_MAX_CTAS) g = LU_COL_MAX_CTAS;
-        lu_column_kernel<W><<<(unsigned)g, LU_COL_WARPS * 32, 0, s>>>(A, n, j0, k, je, piv, p, st, cand,
+        lu_column_kernel<W><<<(unsigned)g, LU_COL_WARPS * 32, 0, s>>>(A, n, j0, k, je, ce, piv, p, st, cand,
                                                                      ticket, pivoting ? 1 : 0);
     }
 }
@@ -831,13 +840,13 @@ void launch_lu_laswp(BMat A, int64_t n, int64_t j0, int64_t je, const int64_t *p
 }
 
 template <int W>
-void launch_lu_u12(BMat A, int64_t n, int64_t j0, int64_t je, int p, DevStatus *st, cudaStream_t s)
+void launch_lu_u12(BMat A, int64_t cend, int64_t j0, int64_t je, int p, DevStatus *st, cudaStream_t s)
 {
     if constexpr (W <= 32) {
-        const int64_t cols = n - je;
+        const int64_t cols = cend - je;
         if (cols <= 0) return;
         const int64_t g = cols < 152 * 8 ? cols : 152 * 8;
-        lu_u12_kernel<W><<<(unsigned)g, 128, 0, s>>>(A, n, j0, je, p, st);
+        lu_u12_kernel<W><<<(unsigned)g, 128, 0, s>>>(A, cend, j0, je, p, st);
     }
 }
 
@@ -850,8 +859,8 @@ void launch_lu_u12(BMat A, int64_t n, int64_t j0, int64_t je, int p, DevStatus *
     template void launch_lu_solve<W>(BMat, int64_t, const int64_t *, BMat, BMat, BMat,          \
                                      int64_t *, int, DevStatus *, cudaStream_t);                \
     template bool lu_fused_ok<W>(int64_t);                                                      \
-    template void launch_lu_column<W>(BMat, int64_t, int64_t, int64_t, int64_t, int64_t *, int, \
-                                      DevStatus *, int64_t *, unsigned *, cudaStream_t, bool);  \
+    template void launch_lu_column<W>(BMat, int64_t, int64_t, int64_t, int64_t, int64_t, int64_t *, \
+                                      int, DevStatus *, int64_t *, unsigned *, cudaStream_t, bool); \
     template void launch_lu_laswp<W>(BMat, int64_t, int64_t, int64_t, const int64_t *, int,     \
                                      cudaStream_t);                                             \
     template void launch_lu_u12<W>(BMat, int64_t, int64_t, int64_t, int, DevStatus *, cudaStream_t);

@@ -36,6 +36,17 @@
 namespace mpg {
 
 int split_digit_count(int p) { return split_digits(p); }
+
+bool on_current_device(const void *ptr)
+{
+    int dev = -1;
+    cudaPointerAttributes a;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
 int64_t split_row_pad(int64_t l) { return split_lpad(l); }
 
 // Lowest diagonal kept by the truncated form and the bound 2^ebits on the
@@ -358,6 +369,9 @@ int launch_split_slices(const __half *pa, const __half *pb, int64_t m, int64_t l
     // TMA: 16-byte aligned bases and row strides (lp is a multiple of 32)
     if (((uintptr_t)pa & 15) || ((uintptr_t)pb & 15) || (lp * 2) % 16) return MP_ERR_ARG;
     if ((int64_t)S * m > 0x7fffffff || (int64_t)S * n > 0x7fffffff) return MP_ERR_ARG;
+    // the TMA loads below are multicast within a cluster: only this GPU's
+    // own device memory may sit under the tensor maps
+    if (!on_current_device(pa) || !on_current_device(pb)) return MP_ERR_ARG;
     CUtensorMap ma, mb;
     if (!make_map(&ma, pa, (int64_t)S * m, lp, BM / CC) || !make_map(&mb, pb, (int64_t)S * n, lp, BN / CR)) {
         if (std::getenv("MPGEMM_DEBUG")) std::fprintf(stderr, "split: tensor map encoding failed\n");
