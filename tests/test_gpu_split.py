@@ -167,3 +167,125 @@ def test_split_full_size_sampled():
     torch.cuda.empty_cache()
     want = orc.dot_exact(A, B, rows=rows, cols=cols)
     assert_bits_equal(got, want, "split 4096^3 sample")
+
+
+# ---------------------------------------------------------------------------
+# Worst-case digit magnitudes.  The exactness argument of the split form is
+# tight here: a digit product reaches 2^14 only when both digits are -128 or
+# both +128, an fp32 chunk of 512 such products reaches 2^23, and an int32
+# register of 255 chunks reaches 255 * 2^23 < 2^31.  Entries are built from
+# byte patterns whose balanced digits (byte + carry, minus 256 from 128 up)
+# are all -128: the lowest mantissa byte 0x80 (digit -128, carry 1), every
+# byte above it 0x7F (0x7F + 1 = 128: digit -128, carry 1), and the top byte
+# 0x80 so that the mantissa stays normalised.  "Small" entries keep the top
+# byte 0x80 and take their other bytes from {0x00, 0x01, 0xFF}, so their
+# digits are in {-1, 0, 1, 2}; one in every 16 consecutive k is small, so
+# each K = 16 tensor-core step adds a product of magnitude 1 to 4 to fifteen
+# products of 2^14 and an accumulator already near 2^23.
+# ---------------------------------------------------------------------------
+def _pattern_entries(rows, cols, p, seed, small_every, flip_from=None, axis=1):
+    """rows x cols entries of exponent 0 (so every row / column aligns to the
+    same e_max), mantissas built from the byte patterns above.  The entry at
+    position k along `axis` is small when k % small_every == small_every - 1
+    (never when small_every is 0); from k = flip_from on the entries are
+    negative (the chunk sums rise towards 2^22 and come back down)."""
+    assert p % 8 == 0
+    nb = p // 8
+    big = 0x80 | sum(0x7F << (8 * t) for t in range(1, nb - 1)) | (0x80 << (8 * (nb - 1)))
+    rng = np.random.default_rng(seed)
+    vals = []
+    for r in range(rows):
+        for c in range(cols):
+            k = c if axis == 1 else r
+            if small_every and k % small_every == small_every - 1:
+                low = rng.choice([0x00, 0x01, 0xFF], size=nb - 1)
+                M = sum(int(b) << (8 * t) for t, b in enumerate(low)) | (0x80 << (8 * (nb - 1)))
+            else:
+                M = big
+            sg = 1 if (flip_from is not None and k >= flip_from) else 0
+            vals.append((sg, M, p))
+    return gen.from_exact_ints(vals, p, (rows, cols))
+
+
+def _digits_of(M_int, p):
+    """Balanced base-256 digits of the aligned integer M 2^64 (exponent e_max,
+    F = p + 64), by the rule the split form documents: low digit first."""
+    S = (p + 64 + 7) // 8 + 1
+    x, out, carry = M_int << 64, [], 0
+    for u in range(S):
+        t = ((x >> (8 * u)) & 0xFF) + carry
+        d, carry = (t - 256, 1) if t >= 128 else (t, 0)
+        out.append(d)
+    return out
+
+
+def test_worst_case_patterns_have_extreme_digits():
+    """The construction does what the tests below rely on: a big entry's
+    digits are -128 everywhere inside its mantissa (one -127 and the carry
+    digit 1 at the top), a small entry's lie in [-1, 2] below its top byte,
+    and the maximal products exceed 2^22 per chunk."""
+    p = 512
+    A = _pattern_entries(1, 32, p, 5, 16)
+    big = _digits_of(gen.entry_int(A, 0, 0) >> (64 * A.L - p), p)
+    assert big[:8] == [0] * 8 and big[8:8 + p // 8 - 1] == [-128] * (p // 8 - 1)
+    assert big[8 + p // 8 - 1:] == [-127, 1]
+    small = _digits_of(gen.entry_int(A, 0, 15) >> (64 * A.L - p), p)
+    assert all(-1 <= d <= 2 for d in small[:8 + p // 8 - 1])
+    assert 480 * 128 * 128 + 32 > 1 << 22 and 512 * 128 * 128 <= 1 << 23
+
+
+@pytest.mark.parametrize("truncate", [False, True])
+@pytest.mark.parametrize("p,l,small_every,flip", [
+    (1024, 512, 16, None),     # chunk sums near 2^23 with their low bits set
+    (512, 1000, 16, None),     # ragged l: chunks cross pair boundaries
+    (1024, 2048, 0, None),     # every chunk exactly 2^23, 255 chunks per int32 sum
+    (1024, 1024, 16, 512),     # the sum rises to ~2^22, then cancels back down
+])
+def test_split_exact_at_worst_case_digits(p, l, small_every, flip, truncate):
+    """Digit products of 2^14 everywhere (the largest a balanced digit pair
+    gives), mixed inside each K = 16 tensor-core step with products of
+    magnitude 1 to 4: every output of the split form, full and truncated,
+    equals the oracle's correctly rounded exact dot product and the exact
+    limb kernel's result.  A tensor core that kept fewer than 24 significant
+    bits anywhere in its fp32 accumulation would drop the small products."""
+    m, n = 12, 20
+    A = _pattern_entries(m, l, p, 100 + l, small_every, flip, axis=1)
+    B = _pattern_entries(l, n, p, 200 + l, small_every, None, axis=0)
+    got, _ = _split(A, B, truncate)
+    assert_bits_equal(got, gemm(A, B, mp.EXACT), "split vs exact kernel at worst-case digits")
+    assert_bits_equal(got, orc.dot_exact(A, B), "split vs oracle at worst-case digits")
+
+
+def test_split_refuses_workspace_off_this_device():
+    """The split form's digit planes are read by TMA loads multicast inside a
+    cluster, so its tensor maps may only cover this GPU's own memory: a
+    caller workspace in page-locked host memory is refused with MP_ERR_ARG
+    on the host, before anything is launched, and C is left untouched; the
+    same product with a device workspace succeeds."""
+    import torch
+
+    p, m, l, n = 256, 16, 40, 24
+    A = gen.uniform_pm1(m, l, p, 83, -4, 4)
+    B = gen.uniform_pm1(l, n, p, 84, -4, 4)
+    dA, dB = mp.DeviceMP.from_host(A), mp.DeviceMP.from_host(B)
+    dC = mp.DeviceMP.empty(m, n, p)
+    before = dC.to_host()
+    need = mp.workspace_size(m, l, n, p, mp.SPLIT, 64)
+    host = torch.empty(need + 4096, dtype=torch.uint8, pin_memory=True)
+    mp.set_workspace(host)
+    try:
+        with pytest.raises(mp.MPError) as err:
+            mp.mpgemm(dA, dB, dC, mp.SPLIT, 64)
+        assert err.value.code == -1                     # MP_ERR_ARG
+    finally:
+        mp.set_workspace(None)
+    torch.cuda.synchronize()
+    assert_bits_equal(dC.to_host(), before, "C after a refused split call")
+    devws = torch.empty(need + 4096, dtype=torch.uint8, device="cuda")
+    mp.set_workspace(devws)
+    try:
+        mp.mpgemm(dA, dB, dC, mp.SPLIT, 64)
+        mp.check_status("split with a device workspace")
+    finally:
+        mp.set_workspace(None)
+    assert_bits_equal(dC.to_host(), orc.dot_exact(A, B), "split with a caller workspace")
