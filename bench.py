@@ -27,10 +27,10 @@ sys.path.insert(0, ROOT)
 ALGO_NAMES = {"simple": 0, "block": 1, "strassen": 2, "winograd": 3}
 # DRAM bytes (read + write) of one leaf launch of the 512-bit Winograd product
 # with cutoff 64, per 64^3 leaf: one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum) of the current leaf kernel at n = 1024 (2401 leaves,
-# 1.442 + 0.696 = 2.138 GB), scaled by the leaves of a launch.  Reset to None
-# whenever the leaf kernel changes.
-LEAF_TRAFFIC_PER_LEAF_P512_C64 = 2.138e9 / 2401
+# dram__bytes_write.sum) of the current leaf kernel (column-wise product) at
+# n = 1024 (2401 leaves, 1.439 + 0.696 = 2.135 GB), scaled by the leaves of a
+# launch.  Reset to None whenever the leaf kernel changes.
+LEAF_TRAFFIC_PER_LEAF_P512_C64 = 2.135e9 / 2401
 PEAK_IMAD_PER_CLK_PER_SM = 64      # 32-bit integer multiply-add lanes per SM per clock
 SM_COUNT_GB300 = 152
 
@@ -375,7 +375,7 @@ def run_ours(a, rank, world, local):
         mp.set_stream(stream)
         other_configs = configs_run(stream)
         mp.set_stream(stream)
-        split_small = split_run(1024, 1024, with_simple=False)
+        split_small = split_run(4096, 1024, with_simple=False, with_full=False)
         mp.set_stream(stream)
         serving = serve_run(a.serve_requests)
         mp.set_stream(stream)
@@ -384,7 +384,7 @@ def run_ours(a, rank, world, local):
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_extras:
-        cpu = cpu_baseline(A, B, a.cpu_seconds)
+        cpu = cpu_baseline(A, B, a.cpu_seconds, a.cutoff)
 
     if rank == 0:
         line = {
@@ -418,7 +418,7 @@ def run_ours(a, rank, world, local):
         if extras_lu:
             line["lu"] = extras_lu
         if split_small:
-            line["split_form_n1024_p1024"] = split_small
+            line["split_form_n4096_p1024"] = split_small
         if other_configs:
             line["configs"] = other_configs
         if serving:
@@ -558,13 +558,21 @@ def lu_run(n, p, algo, panel=128, cutoff=64, kind="well"):
     piv = torch.zeros(n, dtype=torch.int64, device="cuda")
     mp.set_lu(panel, algo, cutoff)
     torch.cuda.synchronize()
-    mp.profile_enable(True)
+    # timed without per-launch events; a second factorisation of a fresh copy
+    # of A, with the library's per-launch CUDA events, gives the kernel shares
     t0 = time.perf_counter()
     mp.mplu(dA, piv, db, dx)
     rc = mp.sync_status()
     t = time.perf_counter() - t0
+    dA2 = mp.DeviceMP.from_host(A)
+    dx2 = mp.DeviceMP.empty(n, 1, p)
+    torch.cuda.synchronize()
+    mp.profile_enable(True)
+    mp.mplu(dA2, piv, db, dx2)
+    mp.check_status("profiled LU")
     prof = mp.profile_read()
     mp.profile_enable(False)
+    del dA2, dx2
     mp.set_lu(128, mp.SIMPLE, 64)
     # residual r = b - A x at 2p (exact widening, Simple product, one subtraction)
     q = 2 * p
@@ -593,9 +601,22 @@ def lu_run(n, p, algo, panel=128, cutoff=64, kind="well"):
     l_back = float(_log2abs(r).max()) - l_den
     l_fwd = float(_log2abs(fe).max())
     back, fwd = float(2.0 ** l_back), float(2.0 ** l_fwd)
+    dev_ms = sum(v[1] for v in prof.values())
+    # the trailing products' leaves against the derived integer peak: one
+    # multiply-add is 2 ceil(p/32)^2 IMAD of schoolbook partial products
+    leaf_n, leaf_ms, leaf_madds = prof.get("leaf_gemm", (0, 0.0, 0.0))
+    leaf_roof = None
+    if leaf_n and leaf_ms > 0:
+        wds = -(-p // 32)
+        ach = leaf_madds * 2 * wds * wds / (leaf_ms * 1e-3) / 1e12
+        leaf_roof = {"bound": "alu", "achieved": round(ach, 3), "peak": 20.137, "unit": "T IMAD/s",
+                     "frac": round(ach / 20.137, 4), "work_per_madd_imad": 2 * wds * wds,
+                     "peak_note": "derived: 152 SMs x 64 IMAD/clk x 2070 MHz"}
     return {"n": n, "prec": p, "algo": {0: "simple", 1: "block", 2: "strassen", 3: "winograd"}[algo],
             "panel": panel, "matrix": kind, "seconds": round(t, 4), "status": rc,
             "kernel_ms": {k: round(v[1], 2) for k, v in prof.items() if v[0]},
+            "kernel_share": {k: round(v[1] / dev_ms, 4) for k, v in prof.items() if v[0] and dev_ms > 0},
+            "trailing_leaf_roofline": leaf_roof,
             "launches": int(sum(v[0] for v in prof.values())),
             "eff_gflops": round((2.0 / 3.0) * n ** 3 / t / 1e9, 4),
             "backward_error": back, "forward_error": fwd,
@@ -847,7 +868,7 @@ def serve_repeat_run(n_req=96, seed=12, slots=8, budget=150 << 30):
     return {"requests": n_req, "shapes": len(shapes), "offered_req_per_s": round(lam, 2), **res}
 
 
-def split_run(n=4096, p=1024, with_simple=True, exp_lo=-16, exp_hi=16, with_exact=True):
+def split_run(n=4096, p=1024, with_simple=True, exp_lo=-16, exp_hi=16, with_exact=True, with_full=True):
     """Split form vs the exact limb path (same correctly rounded result) on
     n^3 at p bits, entries U[-1,1)*2^e, e ~ U{-16..16}: the truncated split
     form (default), the full split form (every digit diagonal), the exact
@@ -863,7 +884,7 @@ def split_run(n=4096, p=1024, with_simple=True, exp_lo=-16, exp_hi=16, with_exac
     dA, dB = mp.DeviceMP.from_host(A), mp.DeviceMP.from_host(B)
     out = {}
     res = {}
-    runs = (("split", mp.SPLIT, True), ("split_full", mp.SPLIT, False)) + \
+    runs = (("split", mp.SPLIT, True),) + ((("split_full", mp.SPLIT, False),) if with_full else ()) + \
         ((("exact_limb", mp.EXACT, True),) if with_exact else ()) + \
         ((("simple_limb", mp.SIMPLE, True),) if with_simple else ())
     for name, algo, trunc in runs:
@@ -900,7 +921,7 @@ def split_run(n=4096, p=1024, with_simple=True, exp_lo=-16, exp_hi=16, with_exac
         return bool(torch.equal(X.limb, Y.limb) and torch.equal(X.exp, Y.exp) and torch.equal(X.sign, Y.sign))
 
     ref = res["exact_limb"] if with_exact else res["split_full"]
-    same = equal(res["split"], ref) and equal(res["split_full"], ref)
+    same = equal(res["split"], ref) and (not with_full or equal(res["split_full"], ref))
     wide_rows = int(sum(1 for i in range(n) if (A.exp[i][A.exp[i] != gen.EXP_ZERO]).min()
                         < (A.exp[i][A.exp[i] != gen.EXP_ZERO]).max() - 64))
     wide_cols = int(sum(1 for j in range(n) if (B.exp[:, j][B.exp[:, j] != gen.EXP_ZERO]).min()
@@ -1027,15 +1048,41 @@ def paper_run(stream, precs=(128, 1024), square=True, rect=True):
     return out
 
 
-def cpu_baseline(A, B, seconds):
-    """The oracle (plain C, all host threads) computing a sample of outputs of
-    the same product by Simple dot products: eff GFLOP/s = 2 l outputs / t.
-    The sample (rows x columns of C) grows until it takes about `seconds`;
-    only the sampled rows of A and columns of B are handed over."""
+def winograd_subproduct(A, B, cutoff, levels=2):
+    """The oracle (plain C, all host threads) running the same algorithm as
+    the GPU line on a bounded part of the same product: Winograd's recursion
+    on one node `levels` levels down, i.e. an (n/2^levels)^3 product with the
+    same cutoff, precision and odd-size policy (for n = 2048: a 512^3 product,
+    one of the 49 level-2 sub-products; the recursion below it is the one the
+    full product runs, and the additions of the two levels above it are about
+    1 % of the work).  Its operands are the corresponding blocks of A and B.
+    Returns (seconds, sub-product size, eff. GFLOP/s of the whole product at
+    7^levels sub-products of that time)."""
     import numpy as np
 
     from oracle import oracle as orc
 
+    n = A.shape[0]
+    h = n >> levels
+    Asub, Bsub = A.sub(np.arange(h), np.arange(h)), B.sub(np.arange(h), np.arange(h))
+    t0 = time.perf_counter()
+    orc.gemm(orc.WINOGRAD, Asub, Bsub, cutoff=cutoff)
+    t = time.perf_counter() - t0
+    return t, h, 2.0 * n ** 3 / (7 ** levels * t) / 1e9
+
+
+def cpu_baseline(A, B, seconds, cutoff=64):
+    """The oracle timed on the host cores, two ways.  value: the same
+    algorithm as the GPU line (Winograd, see winograd_subproduct).
+    simple_dot_sample: a sample of outputs of the same product by Simple dot
+    products, eff GFLOP/s = 2 l outputs / t; the sample (rows x columns of C)
+    grows until it takes about `seconds`; only the sampled rows of A and
+    columns of B are handed over."""
+    import numpy as np
+
+    from oracle import oracle as orc
+
+    tw, h, vw = winograd_subproduct(A, B, cutoff)
     n, l = A.shape
     ncols = B.shape[1]
     threads = orc.max_threads()
@@ -1058,14 +1105,22 @@ def cpu_baseline(A, B, seconds):
         t, r, c = run(count)
     count = int(max(threads, min(n * ncols, r * c * seconds / max(t, 1e-9))))
     t, r, c = run(count)
-    return {"value": round(2.0 * l * r * c / t / 1e9, 6), "unit": "GFLOP/s",
-            "cores": threads, "kind": "oracle",
-            "sample": "%d x %d outputs of C by Simple dot products (l=%d), oracle C code, %d threads"
-                      % (r, c, l, threads), "seconds": round(t, 2)}
+    return {"value": round(vw, 6), "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+            "sample": "Winograd (cutoff %d) on one of the 49 level-2 sub-products, a %d^3 product "
+                      "taking %.2f s on %d threads; whole-product rate = 2 n^3 / (49 t)"
+                      % (cutoff, h, tw, threads),
+            "seconds": round(tw, 2),
+            "simple_dot_sample": {"value": round(2.0 * l * r * c / t / 1e9, 6), "unit": "GFLOP/s",
+                                  "sample": "%d x %d outputs of C by Simple dot products (l=%d)" % (r, c, l),
+                                  "seconds": round(t, 2)}}
 
 
 # ----------------------------------------------------------- reference arm
 def run_reference(a, rank, world):
+    """The oracle as the reference arm: every step runs the same algorithm
+    as our arm (Winograd, cutoff and precision of the workload) on one of the
+    49 level-2 sub-products of the n^3 product (winograd_subproduct); the
+    whole-product rate is 2 n^3 / (49 t).  Rank 0 only."""
     if rank != 0:
         return
     from paper_1410_1599_gb300 import inputs as gen
@@ -1073,27 +1128,16 @@ def run_reference(a, rank, world):
     n, p = a.n, a.prec
     A = gen.uniform_pm1(n, n, p, 3, -16, 16)
     B = gen.uniform_pm1(n, n, p, 4, -16, 16)
-    import numpy as np
-
     from oracle import oracle as orc
     threads = orc.max_threads()
-    # a square block of outputs per step (the oracle spreads outputs over its
-    # threads; a block keeps each thread's A rows and B columns in cache)
-    side = min(n, max(4, int(round((16 * max(threads, 256 * 512 // p)) ** 0.5))))   # ~0.2 s per step
-    per_step = side * side
-    rng = np.random.default_rng(1)
-    subs = []
-    for s in range(a.warmup + a.steps):
-        rows = np.sort(rng.choice(n, size=side, replace=False))
-        cols = np.sort(rng.choice(n, size=side, replace=False))
-        subs.append((A.sub(rows, np.arange(n)), B.sub(np.arange(n), cols)))
     for s in range(a.warmup):
-        orc.gemm(orc.SIMPLE, *subs[s])
-    t0 = time.perf_counter()
+        winograd_subproduct(A, B, a.cutoff)
+    ts = []
     for s in range(a.steps):
-        orc.gemm(orc.SIMPLE, *subs[a.warmup + s])
-    t = (time.perf_counter() - t0) / a.steps
-    value = 2.0 * n * per_step / t / 1e9
+        t, h, _ = winograd_subproduct(A, B, a.cutoff)
+        ts.append(t)
+    t = sum(ts) / len(ts)
+    value = 2.0 * n ** 3 / (49 * t) / 1e9
     line = {"impl": "reference", "metric": "eff. MP GFLOP/s (2mln/t)", "value": round(value, 6),
             "unit": "GFLOP/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": round(t * 1e3, 3), "higher_is_better": True, "scaling": "weak",
@@ -1101,7 +1145,9 @@ def run_reference(a, rank, world):
             "config": workload_config(a),
             "cpu_baseline": {"value": round(value, 6), "unit": "GFLOP/s", "cores": threads,
                              "kind": "oracle",
-                             "sample": "%d x %d outputs per step by Simple dot products (l=%d)" % (side, side, n)},
+                             "sample": "per step: Winograd (cutoff %d) on one of the 49 level-2 "
+                                       "sub-products (a %d^3 product); whole-product rate = 2 n^3 / (49 t)"
+                                       % (a.cutoff, h)},
             "e2e": {"value": round(value, 6), "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
