@@ -60,6 +60,8 @@ def parse():
                     help="only the paper's LU experiment: no pivoting, K = 32 alpha, alpha = 1..10")
     ap.add_argument("--paper", action="store_true",
                     help="only the paper's Section 4 benchmark (sqrt matrices, Tables 2-5 shapes)")
+    ap.add_argument("--cond", action="store_true",
+                    help="only cond_1 of the 1024 x 1024 Lotkin matrix from its GPU inverse at 5376 bits")
     ap.add_argument("--split", action="store_true",
                     help="only the split-form comparison (4096^3 at 1024 bits by default)")
     return ap.parse_args()
@@ -265,6 +267,10 @@ def run_ours(a, rank, world, local):
     sm_mhz = clk.get("sm_mhz") or 2070.0
     peak = SM_COUNT_GB300 * PEAK_IMAD_PER_CLK_PER_SM * 2070e6 / 1e12      # T IMAD/s at max clock
     achieved = (lunits * imad_per_madd) / (lms * 1e-3) / 1e12 if lms > 0 else 0.0
+    # partial products the leaf actually forms: the truncated product keeps the
+    # columns i + j >= W - 2 of the W x W schoolbook (2W - 1 + W(W-1)/2 of W^2)
+    # when p = 32 W, the case of the configured precisions
+    formed = (2 * W32 - 1 + W32 * (W32 - 1) // 2) if 32 * W32 == p else W32 * W32
     kernels = {k: {"launches_per_step": v[0] / a.steps, "ms_per_step": v[1] / a.steps,
                    "share": v[1] / max(sum(x[1] for x in prof.values()), 1e-9)}
                for k, v in prof.items() if v[0]}
@@ -398,7 +404,12 @@ def run_ours(a, rank, world, local):
                          "peak": round(peak, 3), "unit": "T IMAD/s",
                          "frac": round(achieved / peak, 4),
                          "peak_note": "derived: 152 SMs x 64 IMAD/clk x 2070 MHz",
-                         "work_per_madd_imad": imad_per_madd, "traffic": leaf_traffic(a),
+                         "work_per_madd_imad": imad_per_madd,
+                         "achieved_formed": round(achieved * formed / (W32 * W32), 3),
+                         "frac_formed": round(achieved * formed / (W32 * W32) / peak, 4),
+                         "formed_note": "IMAD of the %d of %d partial products the truncated product forms"
+                                        % (formed, W32 * W32),
+                         "traffic": leaf_traffic(a),
                          "traffic_unit": "bytes per launch (ncu capture, scaled by leaves)"},
             "kernels": kernels,
             "gpu_launches": int(round(launches_per_step * a.steps)),
@@ -702,6 +713,58 @@ def lotkin_run(n=1024, alphas=(1, 2, 4, 8)):
     return lu_sweep_run(n, precs=(8192, 8650), kind="lotkin", runs_for=runs_for)
 
 
+def cond_run(n=1024, p=5376, panel=128):
+    """cond_1 = ||A||_1 ||A^-1||_1 of the n x n Lotkin matrix (Sec. 4 quotes
+    4.3e1576 for n = 1024): A^-1 on the GPU at p bits (mplu with partial
+    pivoting and Winograd trailing products, then mplu_solve with B = I, the
+    272-word wide class above 2048 bits), the 1-norms read in log2 space.
+    p must exceed log2 cond_1 (about 5237 bits) for A^-1 to carry correct
+    leading digits; 5376 leaves about 40 digits."""
+    import numpy as np
+    import torch
+
+    from paper_1410_1599_gb300 import binding as mp
+    from paper_1410_1599_gb300 import inputs as gen
+    from paper_1410_1599_gb300 import norms
+
+    t0 = time.perf_counter()
+    A = gen.lotkin(n, p)
+    t_gen = time.perf_counter() - t0
+    dA = mp.DeviceMP.from_host(A)
+    piv = torch.zeros(n, dtype=torch.int64, device="cuda")
+    mp.set_lu(panel, mp.WINOGRAD, 0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mp.mplu(dA, piv, None, None)
+    rc_lu = mp.sync_status()
+    t_lu = time.perf_counter() - t0
+    mp.set_lu(128, mp.SIMPLE, 64)
+    dI = mp.DeviceMP.from_host(gen.identity(n, p))
+    dX = mp.DeviceMP.empty(n, n, p)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mp.mplu_solve(dA, piv, dI, dX)
+    rc_inv = mp.sync_status()
+    t_inv = time.perf_counter() - t0
+    X = dX.to_host()
+    la, lx = norms.norm1_log2(A), norms.norm1_log2(X)
+    l10 = norms.log10_of_log2(la + lx)
+    mant = 10 ** (l10 - math.floor(l10))
+    exact = None                            # the oracle's exact value, stored by tests/golden/make_lotkin_cond1.py
+    gold = os.path.join(ROOT, "tests", "golden", "lotkin_cond1.txt")
+    if os.path.exists(gold):
+        for ln in open(gold):
+            f = ln.split()
+            if f and not ln.startswith("#") and int(f[0]) == n:
+                exact = float(f[3])
+    return {"n": n, "prec": p, "matrix": "lotkin", "panel": panel, "status_lu": rc_lu, "status_inverse": rc_inv,
+            "seconds_lu": round(t_lu, 2), "seconds_inverse": round(t_inv, 2), "seconds_host_generation": round(t_gen, 1),
+            "norm1_A": round(2.0 ** la, 6), "log10_norm1_inverse": round(norms.log10_of_log2(lx), 3),
+            "cond1": "%.3fe%d" % (mant, math.floor(l10)), "log10_cond1": round(l10, 4),
+            "log10_cond1_exact": exact,
+            "paper_cond1": "4.3e1576 (Sec. 4, n = 1024)"}
+
+
 def serve_run(n_req, seed=11, slots=8, budget=150 << 30):
     """Config-5 style request stream through the library's serving loop:
     70% GEMM (m, l, n ~ U{16..2048}), 30% LU solve (n ~ U{64..1024}),
@@ -751,37 +814,74 @@ def serve_run(n_req, seed=11, slots=8, budget=150 << 30):
             A.sign[j, j] = D.sign[0, j]
         return A, tile(p, n, 1, off + 11)
 
-    inputs = [make(s) for s in specs]
     flops = [2.0 * s[3][0] * s[3][1] * s[3][2] if s[0] == "gemm" else (2.0 / 3.0) * s[3][0] ** 3
              for s in specs]
 
-    def submit(srv, s, X, Y):
+    def prepare(srv, s):
         kind, i, p, dims, algo, off = s
+        X, Y = make(s)
         if kind == "gemm":
-            return srv.submit_gemm(i, X, Y, algo=algo, cutoff=64)
-        return srv.submit_lu(i, X, Y, algo=algo, cutoff=64, panel=128)
+            return srv.prepare_gemm(i, X, Y, algo=algo, cutoff=64)
+        return srv.prepare_lu(i, X, Y, algo=algo, cutoff=64, panel=128)
 
-    # phase 1: closed loop, all at once
-    srv = mp.Server(budget_bytes=budget, slots=slots)
+    # Requests are prepared (operands tiled and copied into page-locked host
+    # buffers) ahead of their submission by a helper thread, at most `window`
+    # of them at a time, so that submitting only queues a request; outputs of
+    # long runs are not kept (their status and latency are).
+    import queue as queue_mod
+    import threading
+
+    window = max(48, slots * 6) if n_req > 64 else n_req
+
+    def ahead(srv):
+        q = queue_mod.Queue(maxsize=window)
+
+        def work():
+            for s in specs:
+                q.put(prepare(srv, s))
+        th = threading.Thread(target=work, daemon=True)
+        th.start()
+        return q, th
+
+    keep = n_req <= 64
+    # phase 1: closed loop (the preparation window fills before the clock
+    # starts).  Up to `window` requests are outstanding at once: all of them
+    # for the default 32-request stream, a sliding window for long streams
+    # (whose pinned host buffers would not all fit in host memory).
+    srv = mp.Server(budget_bytes=budget, slots=slots, keep_outputs=keep)
+    q, th = ahead(srv)
+    while q.qsize() < min(window, n_req) and th.is_alive():
+        time.sleep(0.01)
     t0 = time.perf_counter()
-    for s, (X, Y) in zip(specs, inputs):
-        assert submit(srv, s, X, Y) == 0
+    submitted = finished = 0
+    while finished < n_req:
+        while submitted < n_req and submitted - finished < window:
+            assert srv.submit(q.get()) == 0
+            submitted += 1
+        finished += len(srv.poll())
+        if finished < n_req:
+            time.sleep(0.001)
     srv.drain()
     t_cap = time.perf_counter() - t0
+    th.join()
     st1 = srv.stats()
     srv.close()
     cap = n_req / t_cap
     # phase 2: Poisson arrivals at 0.7 x capacity
     lam = 0.7 * cap
     gaps = rng.exponential(1.0 / lam, n_req)
-    srv = mp.Server(budget_bytes=budget, slots=slots)
+    srv = mp.Server(budget_bytes=budget, slots=slots, keep_outputs=keep)
+    q, th = ahead(srv)
+    while q.qsize() < min(window, n_req) and th.is_alive():
+        time.sleep(0.01)
     t0 = time.perf_counter()
     due = t0
-    for s, (X, Y), g in zip(specs, inputs, gaps):
+    for g in gaps:
         due += g
         while time.perf_counter() < due:
             time.sleep(min(0.002, max(0.0, due - time.perf_counter())))
-        assert submit(srv, s, X, Y) == 0
+            srv.poll()                      # finished requests release their host buffers
+        assert srv.submit(q.get()) == 0
     srv.drain()
     t_run = time.perf_counter() - t0
     st2 = srv.stats()
@@ -796,6 +896,7 @@ def serve_run(n_req, seed=11, slots=8, budget=150 << 30):
             "p50_ms": round(float(np.percentile(lat, 50)), 2),
             "p99_ms": round(float(np.percentile(lat, 99)), 2),
             "batches": st1["batches"], "batched_requests": st1["batched_requests"],
+            "batches_poisson": st2["batches"], "batched_requests_poisson": st2["batched_requests"],
             "peak_gb": round(max(st1["peak_bytes"], st2["peak_bytes"]) / 2 ** 30, 3)}
 
 
@@ -1165,6 +1266,13 @@ def main():
         print(json.dumps({"split_form": split_run(n_s, p_s),
                           "split_form_u11": split_run(n_s, p_s, with_simple=False, exp_lo=0, exp_hi=0,
                                                       with_exact=False)}), flush=True)
+        return
+    if a.cond:
+        import torch
+        from paper_1410_1599_gb300 import build as libbuild
+        libbuild.build()
+        torch.cuda.set_device(local)
+        print(json.dumps({"cond1_lotkin": cond_run(a.lu_n)}), flush=True)
         return
     if a.lotkin:
         import torch

@@ -246,6 +246,21 @@ size_t mplu_workspace_size(int64_t n, int32_t prec);
  */
 int mplu(int64_t n, int32_t prec, mpmat_t *A, int64_t *piv, const mpmat_t *b, mpmat_t *x);
 
+/*
+ * X := A^-1 B for every column of B (n x nrhs), from the factors L\U and piv
+ * that mplu left in A (Sec. 4, the solve Ly = Pb, Ux = y, applied to each
+ * column).  Column c of X is bit for bit what mplu returns as x for
+ * b = column c of B: forward, y_i = RN(y_i - RN(l_ij y_j)) for j = 0..i-1
+ * ascending; backward, x_j = RN(y_j / u_jj) for j = n-1 down to 0, then
+ * y_i = RN(y_i - RN(u_ij x_j)) for every i < j.  With B = I, X = A^-1 (the
+ * condition number ||A||_1 ||A^-1||_1 of Sec. 4's ill-conditioned matrix).
+ * LU n x n, B and X n x nrhs, all of precision prec; piv device int64[n].
+ * X must not overlap LU or B (MP_ERR_ARG).  A zero u_jj gives x_j = +0 and
+ * mp_sync_status() returns MP_ERR_SINGULAR.  Uses n * nrhs numbers of
+ * workspace (mp_set_workspace or stream-ordered allocation).
+ */
+int mplu_solve(int64_t n, int32_t prec, const mpmat_t *LU, const int64_t *piv, const mpmat_t *B, mpmat_t *X);
+
 /* ---- serving: continuous batching of GEMM and LU-solve requests ---------- */
 
 /*
@@ -258,6 +273,13 @@ int mplu(int64_t n, int32_t prec, mpmat_t *A, int64_t *piv, const mpmat_t *b, mp
  * Block are batched into one grouped Block launch, zero-padded to the
  * bucket: the padding only appends exact zero products after each c_ij's
  * k-ascending sequence, so a request's result is the same alone or batched.
+ * Other GEMMs of the same precision and size class (largest dimension up to
+ * 256, 512, 1024 or 2048) that are queued together form a leaf group (up
+ * to 8): each runs its own Strassen/Winograd operand sums and combinations,
+ * and the leaf products of all of them (a Simple or Block request, also
+ * one that waits beside them in a bucket, is one leaf of its own shape)
+ * share grouped Block launches.  Requests whose shape was seen before are
+ * left to the graph cache instead.
  * Every request's result depends only on the request (never on the mix).
  *
  * Host buffers use the interchange layout, contiguous: limb[L][rows][cols]
@@ -306,8 +328,8 @@ int mp_server_poll(mp_server_t *srv, int64_t *ids, int32_t *status, double *late
 /* Block until every submitted request has finished. */
 int mp_server_drain(mp_server_t *srv);
 
-/* Counters: [0] submitted, [1] completed, [2] batches launched, [3] requests
- * that ran inside a multi-request batch, [4] peak device bytes in use,
+/* Counters: [0] submitted, [1] completed, [2] batches and leaf groups
+ * launched, [3] requests that ran inside one of them, [4] peak device bytes in use,
  * [5] budget, [6] currently running, [7] currently queued. */
 int mp_server_stats(mp_server_t *srv, int64_t out[8]);
 

@@ -315,3 +315,50 @@ def sqrt_rel_errors(Cm, m: int, l: int, n: int) -> np.ndarray:
                 continue
             out[i, j] = float(abs(x * x - 15)) / ((float(x) + r15) * r15)
     return out
+
+
+# ---------------------------------------------------------------------------
+# Sec. 4's ill-conditioned matrix: cond_1 of the Lotkin matrix, exactly
+# ---------------------------------------------------------------------------
+def lotkin_norm1_log2(n: int):
+    """(log2 ||A||_1, log2 ||A^-1||_1) of the n x n Lotkin matrix (first row
+    all ones, a_ij = 1/(i+j-1) below; Sec. 4), from exact integers.
+
+    The Hilbert matrix H (h_ij = 1/(i+j-1)) has the integer inverse
+    G_ij = (-1)^(i+j) a_i a_j / (i+j-1), a_i = (n+i-1)! / ((n-i)! ((i-1)!)^2)
+    (the binomial closed form of H^-1 regrouped).  The Lotkin matrix is
+    A = H + e_1 w^T with w_j = 1 - 1/j, so by Sherman and Morrison
+    A^-1 = G - c r^T / d with c = G e_1, r^T = w^T G = s^T - e_1^T (s the
+    column sums of G, since the first row of H times G is e_1^T) and
+    d = 1 + w^T G e_1 = s_1: every entry is the integer d G_ij - c_i r_j over
+    the common denominator d.  ||A||_1 is the first column's sum, the
+    harmonic number H_n."""
+    fact = [1] * (2 * n + 1)
+    for k in range(1, 2 * n + 1):
+        fact[k] = fact[k - 1] * k
+    a = [0] + [fact[n + i - 1] // (fact[n - i] * fact[i - 1] ** 2) for i in range(1, n + 1)]
+
+    def G(i, j):
+        v = a[i] * a[j] // (i + j - 1)
+        return -v if (i + j) & 1 else v
+
+    s = [0] * (n + 1)
+    for j in range(1, n + 1):
+        s[j] = sum(G(i, j) for i in range(1, n + 1))
+    d = s[1]
+    c = [0] + [G(i, 1) for i in range(1, n + 1)]
+    r = [0] + [s[j] - (1 if j == 1 else 0) for j in range(1, n + 1)]
+    best = 0
+    for j in range(1, n + 1):
+        tot = sum(abs(d * G(i, j) - c[i] * r[j]) for i in range(1, n + 1))
+        best = max(best, tot)
+
+    def log2_int(v):
+        shift = max(v.bit_length() - 60, 0)
+        return math.log2(v >> shift) + shift
+
+    def log2_ratio(num, den):
+        return log2_int(num) - log2_int(den)
+
+    hn = Fraction(1) + sum(Fraction(1, i) for i in range(2, n + 1))
+    return log2_ratio(hn.numerator, hn.denominator), log2_ratio(best, abs(d))

@@ -30,7 +30,7 @@ NOALLOC_SCRATCH_BYTES = 64 << 20
 EXPORTS = ["mp_set_stream", "mp_set_workspace", "mp_set_odd_policy", "mp_set_lu", "mp_set_lu_pivoting",
            "mp_set_split_truncation", "mp_split_fallbacks",
            "mp_elementwise", "mp_convert", "mpgemm_workspace_size", "mpgemm",
-           "mplu_workspace_size", "mplu", "mp_sync_status", "mp_singular_column",
+           "mplu_workspace_size", "mplu", "mplu_solve", "mp_sync_status", "mp_singular_column",
            "mp_strerror", "mp_version", "mp_profile_enable", "mp_profile_read",
            "mpgemm_noalloc", "mpgemm_batched", "mp_server_create", "mp_server_submit", "mp_server_cancel",
            "mp_server_poll", "mp_server_drain", "mp_server_stats", "mp_server_set_graphs",
@@ -277,6 +277,13 @@ def mpgemm_noalloc(A: DeviceMP, B: DeviceMP, C_: DeviceMP, algo: int = WINOGRAD,
                                          C.byref(b), C.byref(c)), "mpgemm_noalloc")
 
 
+def mplu_solve(LU: DeviceMP, piv, B: DeviceMP, X: DeviceMP) -> None:
+    """X = A^-1 B from the factors mplu left in LU (see include/mpgemm.h)."""
+    a, b, x = LU.struct(), B.struct(), X.struct()
+    _check(load_library().mplu_solve(LU.rows, LU.p, C.byref(a), C.c_void_p(piv.data_ptr()), C.byref(b),
+                                      C.byref(x)), "mplu_solve")
+
+
 def mplu(A: DeviceMP, piv, b: DeviceMP | None, x: DeviceMP | None) -> None:
     a = A.struct()
     bs = b.struct() if b is not None else None
@@ -309,16 +316,20 @@ def _host_arrays(M, pinned: bool):
 class Server:
     """Continuous-batching request loop of the library (mp_server_*)."""
 
-    def __init__(self, budget_bytes: int, slots: int = 8, pinned: bool = True):
+    def __init__(self, budget_bytes: int, slots: int = 8, pinned: bool = True, keep_outputs: bool = True):
         self.lib = load_library()
         self.h = self.lib.mp_server_create(C.c_size_t(budget_bytes), slots)
         if not self.h:
             raise MPError(-5, "mp_server_create")
         self.pinned = pinned
+        self.keep_outputs = keep_outputs     # False: results keep status and latency only
         self.live = {}            # id -> buffers kept alive until completion
         self.results = {}         # id -> (status, latency_ms, output HostMP)
 
-    def _req(self, rid, kind, prec, m, l, n, algo, cutoff, panel, A, B, out):
+    def _prepare(self, rid, kind, prec, m, l, n, algo, cutoff, panel, A, B, out):
+        """The request record and its host buffers (page-locked copies when
+        pinned), ready for submit(): preparing costs a copy of the operands,
+        submitting only queues the request."""
         a, ka = _host_arrays(A, self.pinned)
         b, kb = _host_arrays(B, self.pinned)
         o, ko = _host_arrays(out, self.pinned)
@@ -326,22 +337,32 @@ class Server:
         r = MPRequest(rid, kind, prec, m, l, n, algo, cutoff, panel, 0,
                       ptr(a[0]), ptr(a[1]), ptr(a[2]), ptr(b[0]), ptr(b[1]), ptr(b[2]),
                       ptr(o[0]), ptr(o[1]), ptr(o[2]))
-        self.live[rid] = (a, b, o, prec, (ka, kb, ko))
+        return (rid, r, (a, b, o, prec, (ka, kb, ko)))
+
+    def submit(self, prepared) -> int:
+        rid, r, bufs = prepared
+        self.live[rid] = bufs
         rc = self.lib.mp_server_submit(self.h, C.byref(r))
         if rc != MP_OK:
             del self.live[rid]
         return rc
 
-    def submit_gemm(self, rid, A, B, algo=BLOCK, cutoff=64):
+    def prepare_gemm(self, rid, A, B, algo=BLOCK, cutoff=64):
         m, l = A.shape
         n = B.shape[1]
         out = HostMP.zeros(m, n, A.p)
-        return self._req(rid, REQ_GEMM, A.p, m, l, n, algo, cutoff, 0, A, B, out)
+        return self._prepare(rid, REQ_GEMM, A.p, m, l, n, algo, cutoff, 0, A, B, out)
 
-    def submit_lu(self, rid, A, b, algo=SIMPLE, cutoff=64, panel=128):
+    def prepare_lu(self, rid, A, b, algo=SIMPLE, cutoff=64, panel=128):
         n = A.shape[0]
         out = HostMP.zeros(n, 1, A.p)
-        return self._req(rid, REQ_LU_SOLVE, A.p, n, n, 1, algo, cutoff, panel, A, b, out)
+        return self._prepare(rid, REQ_LU_SOLVE, A.p, n, n, 1, algo, cutoff, panel, A, b, out)
+
+    def submit_gemm(self, rid, A, B, algo=BLOCK, cutoff=64):
+        return self.submit(self.prepare_gemm(rid, A, B, algo, cutoff))
+
+    def submit_lu(self, rid, A, b, algo=SIMPLE, cutoff=64, panel=128):
+        return self.submit(self.prepare_lu(rid, A, b, algo, cutoff, panel))
 
     def cancel(self, rid) -> int:
         return self.lib.mp_server_cancel(self.h, rid)
@@ -357,7 +378,7 @@ class Server:
             rid = int(ids[i])
             bufs = self.live.pop(rid, None)
             out = None
-            if bufs is not None:
+            if bufs is not None and self.keep_outputs:
                 o, prec = bufs[2], bufs[3]
                 out = HostMP(o[0].copy(), o[1].copy(), o[2].copy(), prec)
             self.results[rid] = (int(st[i]), float(ms[i]), out)

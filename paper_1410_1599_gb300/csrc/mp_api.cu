@@ -337,81 +337,125 @@ __global__ void fill_zero_kernel(BMat C, int64_t rows, int64_t cols, int L)
     }
 }
 
+// The recursion's buffers and plan for one product (Sec. 2), split into
+// the phases a grouped run interleaves: operand sums top-down, the leaf
+// products, combinations bottom-up.
+struct RecState {
+    std::vector<LevelDims> lv;
+    std::vector<BMat> A, B, C;
+    int algo = 0;
+    int64_t leaves = 1;
+};
+
+// carve the level buffers and run the operand sums of every level (one
+// batched launch per side and level)
 template <int W>
-int run_recursion(int algo, const std::vector<LevelDims> &lv, int p, BMat A0, BMat B0, BMat C0,
-                  Workspace &ws, DevStatus *st, cudaStream_t s)
+void rec_down(RecState &r, int algo, const std::vector<LevelDims> &lv, int p, BMat A0, BMat B0, BMat C0,
+              Workspace &ws, cudaStream_t s)
 {
     const int L = limbs_of(p);
     const int D = (int)lv.size() - 1;
-    std::vector<BMat> A(D + 1), B(D + 1), C(D + 1);
-    A[0] = A0;
-    B[0] = B0;
-    C[0] = C0;
+    r.lv = lv;
+    r.algo = algo;
+    r.A.assign(D + 1, BMat{});
+    r.B.assign(D + 1, BMat{});
+    r.C.assign(D + 1, BMat{});
+    r.A[0] = A0;
+    r.B[0] = B0;
+    r.C[0] = C0;
     int64_t nodes = 1;
     for (int k = 1; k <= D; ++k) {
         nodes *= 7;
-        A[k] = carve(ws, nodes, lv[k].m, lv[k].l, L);
-        B[k] = carve(ws, nodes, lv[k].l, lv[k].n, L);
-        C[k] = carve(ws, nodes, lv[k].m, lv[k].n, L);
+        r.A[k] = carve(ws, nodes, lv[k].m, lv[k].l, L);
+        r.B[k] = carve(ws, nodes, lv[k].l, lv[k].n, L);
+        r.C[k] = carve(ws, nodes, lv[k].m, lv[k].n, L);
     }
-    // down: operand sums of every level (one batched launch per side)
+    r.leaves = nodes;
     nodes = 1;
     for (int k = 0; k < D; ++k) {
         const LevelDims &d = lv[k];
         {
             Prof pr(MP_K_OPERANDS, (double)nodes * 7 * (d.M / 2) * (d.K / 2), s);
-            launch_operands_a<W>(algo, A[k], A[k + 1], nodes, d.m, d.l, d.M / 2, d.K / 2, p, s);
+            launch_operands_a<W>(algo, r.A[k], r.A[k + 1], nodes, d.m, d.l, d.M / 2, d.K / 2, p, s);
         }
         {
             Prof pr(MP_K_OPERANDS, (double)nodes * 7 * (d.K / 2) * (d.N / 2), s);
-            launch_operands_b<W>(algo, B[k], B[k + 1], nodes, d.l, d.n, d.K / 2, d.N / 2, p, s);
+            launch_operands_b<W>(algo, r.B[k], r.B[k + 1], nodes, d.l, d.n, d.K / 2, d.N / 2, p, s);
         }
         nodes *= 7;
     }
-    // peeled borders (last row / column of a node with odd m / n, Simple over
-    // its whole l): they need only the node's operands, so they run on a
-    // second stream, overlapping the leaves, and join before the combinations
-    bool any_border = false;
-    for (int k = 0; k < D; ++k)
-        if (lv[k].M < lv[k].m || lv[k].N < lv[k].n) any_border = true;
+}
+
+// peeled borders (last row / column of a node with odd m / n, Simple over
+// its whole l); they need only the node's operands
+template <int W>
+bool rec_has_borders(const RecState &r)
+{
+    for (size_t k = 0; k + 1 < r.lv.size(); ++k)
+        if (r.lv[k].M < r.lv[k].m || r.lv[k].N < r.lv[k].n) return true;
+    return false;
+}
+template <int W>
+void rec_borders(const RecState &r, int p, DevStatus *st, cudaStream_t s)
+{
+    const int D = (int)r.lv.size() - 1;
+    int64_t nk = 1;
+    for (int k = 0; k < D; ++k, nk *= 7) {
+        const LevelDims &d = r.lv[k];
+        if (!(d.M < d.m || d.N < d.n)) continue;
+        const int64_t mr = std::min(d.M, d.m);
+        const int64_t cnt = (d.M < d.m ? d.n : 0) + (d.N < d.n ? mr : 0);
+        Prof pr(MP_K_FIXUP, (double)nk * cnt * d.l, s);
+        launch_border<W>(r.A[k], r.B[k], r.C[k], nk, d.m, d.l, d.n, mr, d.M < d.m, d.N < d.n, p, st, s);
+    }
+}
+
+// combinations bottom-up, then the rank-1 fix-up of an odd l
+template <int W>
+void rec_up(const RecState &r, int p, DevStatus *st, cudaStream_t s)
+{
+    const int D = (int)r.lv.size() - 1;
+    int64_t nodes = r.leaves;
+    for (int k = D - 1; k >= 0; --k) {
+        nodes /= 7;
+        const LevelDims &d = r.lv[k];
+        const int64_t mr = std::min(d.M, d.m), nr = std::min(d.N, d.n);
+        {
+            Prof pr(MP_K_COMBINE, (double)nodes * mr * nr, s);
+            launch_combine<W>(r.algo, r.C[k + 1], r.C[k], nodes, d.M / 2, d.N / 2, mr, nr, p, st, s);
+        }
+        if (d.K < d.l) {
+            Prof pr(MP_K_FIXUP, (double)nodes * mr * nr, s);
+            launch_rank1<W>(r.A[k], r.B[k], r.C[k], nodes, mr, nr, d.l, p, st, s);
+        }
+    }
+}
+
+template <int W>
+int run_recursion(int algo, const std::vector<LevelDims> &lv, int p, BMat A0, BMat B0, BMat C0,
+                  Workspace &ws, DevStatus *st, cudaStream_t s)
+{
+    RecState r;
+    rec_down<W>(r, algo, lv, p, A0, B0, C0, ws, s);
+    const int D = (int)lv.size() - 1;
+    // the borders run on a second stream, overlapping the leaves, and join
+    // before the combinations
+    const bool any_border = rec_has_borders<W>(r);
     SideStream *ss = any_border ? side_stream() : nullptr;
     const cudaStream_t bs = ss ? ss->s : s;
     if (ss) {
         cudaEventRecord(ss->fork, s);
         cudaStreamWaitEvent(bs, ss->fork, 0);
     }
-    if (any_border) {
-        int64_t nk = 1;
-        for (int k = 0; k < D; ++k, nk *= 7) {
-            const LevelDims &d = lv[k];
-            if (!(d.M < d.m || d.N < d.n)) continue;
-            const int64_t mr = std::min(d.M, d.m);
-            const int64_t cnt = (d.M < d.m ? d.n : 0) + (d.N < d.n ? mr : 0);
-            Prof pr(MP_K_FIXUP, (double)nk * cnt * d.l, bs);
-            launch_border<W>(A[k], B[k], C[k], nk, d.m, d.l, d.n, mr, d.M < d.m, d.N < d.n, p, st, bs);
-        }
-    }
+    if (any_border) rec_borders<W>(r, p, st, bs);
     if (ss) cudaEventRecord(ss->join, bs);
     // leaves: one grouped Block GEMM over all 7^D products
     {
-        Prof pr(MP_K_LEAF, (double)nodes * lv[D].m * lv[D].l * lv[D].n, s);
-        launch_gemm_block<W>(A[D], B[D], C[D], nodes, lv[D].m, lv[D].l, lv[D].n, p, st, s);
+        Prof pr(MP_K_LEAF, (double)r.leaves * lv[D].m * lv[D].l * lv[D].n, s);
+        launch_gemm_block<W>(r.A[D], r.B[D], r.C[D], r.leaves, lv[D].m, lv[D].l, lv[D].n, p, st, s);
     }
     if (ss) cudaStreamWaitEvent(s, ss->join, 0);
-    // up: combinations, then the rank-1 fix-up of an odd l
-    for (int k = D - 1; k >= 0; --k) {
-        nodes /= 7;
-        const LevelDims &d = lv[k];
-        const int64_t mr = std::min(d.M, d.m), nr = std::min(d.N, d.n);
-        {
-            Prof pr(MP_K_COMBINE, (double)nodes * mr * nr, s);
-            launch_combine<W>(algo, C[k + 1], C[k], nodes, d.M / 2, d.N / 2, mr, nr, p, st, s);
-        }
-        if (d.K < d.l) {
-            Prof pr(MP_K_FIXUP, (double)nodes * mr * nr, s);
-            launch_rank1<W>(A[k], B[k], C[k], nodes, mr, nr, d.l, p, st, s);
-        }
-    }
+    rec_up<W>(r, p, st, s);
     return launch_status();
 }
 
@@ -581,6 +625,7 @@ static size_t lu_ws_bytes(int64_t n, int p, int panel, int algo, int cutoff, int
 
 namespace mpg {
 int auto_cutoff(int p);
+int resolve_cutoff(int cutoff, int p);
 
 // C := A B with the recursion's buffers carved from a caller-supplied device
 // block [base, base + bytes); nothing is allocated.  Returns MP_ERR_NOMEM if
@@ -632,6 +677,70 @@ int gemm_block_batched(int p, BMat A, BMat B, BMat C, int64_t batch, int64_t m, 
     Prof pr(MP_K_LEAF, (double)batch * m * l * n, s);
     dispatch(p, [&](auto w) {
         launch_gemm_block<decltype(w)::value>(A, B, C, batch, m, l, n, p, st, s);
+    });
+    return launch_status();
+}
+
+// Several products C_i := A_i B_i of one precision on stream s (the serving
+// loop's groups), each computed exactly as mpgemm computes it with the odd
+// policy MP_PEEL: Strassen / Winograd products run their operand sums and
+// peel borders, then the leaves of every product in the group go to one
+// grouped Block launch (Simple and Block products, and recursions of depth
+// 0, as a single leaf of their own shape: Simple and Block give the same
+// bits), then each product's combinations and fix-ups.  it[i].ws holds
+// gemm_scratch_bytes(...) bytes of device memory for product i.
+int gemm_group(GroupGemm *it, int count, int p, cudaStream_t s)
+{
+    DevStatus *st = status_ptr();
+    if (!st) return MP_ERR_CUDA;
+    dispatch(p, [&](auto w) {
+        constexpr int WW = decltype(w)::value;
+        const int L = limbs_of(p);
+        std::vector<RecState> rs((size_t)count);
+        std::vector<char> rec((size_t)count, 0);
+        LeafGroup grp;
+        grp.count = 0;
+        double units = 0;
+        auto flush = [&]() {
+            if (!grp.count) return;
+            Prof pr(MP_K_LEAF, units, s);
+            launch_gemm_block_group<WW>(grp, p, st, s);
+            grp.count = 0;
+            units = 0;
+        };
+        for (int i = 0; i < count; ++i) {
+            GroupGemm &g = it[i];
+            if (g.m == 0 || g.n == 0) continue;
+            if (g.l == 0) {
+                Prof pr(MP_K_ELEMENTWISE, (double)g.m * g.n, s);
+                fill_zero_kernel<<<(unsigned)std::min<int64_t>((g.m * g.n + 127) / 128, 152 * 32), 128, 0, s>>>(
+                    g.C, g.m, g.n, L);
+                continue;
+            }
+            LeafBatch lb;
+            const int cutoff = resolve_cutoff(g.cutoff, p);
+            auto lv = plan(g.m, g.l, g.n, cutoff, MP_PEEL);
+            if ((g.algo == MP_STRASSEN || g.algo == MP_WINOGRAD) && lv.size() > 1) {
+                Workspace ws;
+                ws.base = (char *)g.ws;
+                ws.size = g.ws_bytes;
+                ws.used = 0;
+                ws.s = s;
+                rec_down<WW>(rs[i], g.algo, lv, p, g.A, g.B, g.C, ws, s);
+                if (rec_has_borders<WW>(rs[i])) rec_borders<WW>(rs[i], p, st, s);
+                rec[i] = 1;
+                const int D = (int)lv.size() - 1;
+                lb = LeafBatch{rs[i].A[D], rs[i].B[D], rs[i].C[D], rs[i].leaves, lv[D].m, lv[D].l, lv[D].n, 0, 0};
+            } else {
+                lb = LeafBatch{g.A, g.B, g.C, 1, g.m, g.l, g.n, 0, 0};
+            }
+            units += (double)lb.batch * lb.m * lb.l * lb.n;
+            grp.batch[grp.count++] = lb;
+            if (grp.count == LEAF_GROUP_MAX) flush();
+        }
+        flush();
+        for (int i = 0; i < count; ++i)
+            if (rec[i]) rec_up<WW>(rs[i], p, st, s);
     });
     return launch_status();
 }
@@ -942,7 +1051,7 @@ int mplu(int64_t n, int32_t prec, mpmat_t *A, int64_t *piv, const mpmat_t *b, mp
             const int64_t je = std::min<int64_t>(j0 + K, n);
             {
                 if (fused) {
-                    // The panel in sub-panels of LU_SUB columns.  A sub-panel
+                    // The panel in sub-panels of lu_sub_width<W>() columns.  A sub-panel
                     // [c0, c1) first takes the updates of the panel's earlier
                     // columns k in [j0, c0) on its own columns from row c0
                     // down (subtracting Block product, k ascending), then is
@@ -961,8 +1070,9 @@ int mplu(int64_t n, int32_t prec, mpmat_t *A, int64_t *piv, const mpmat_t *b, mp
                         Prof pr(MP_K_LU, (double)(n - j0), s);
                         launch_lu_pivot<WW>(A0, n, j0, piv, prec, st, s, j0, je, pivoting);
                     }
-                    for (int64_t c0 = j0; c0 < je; c0 += LU_SUB) {
-                        const int64_t c1 = std::min<int64_t>(c0 + LU_SUB, je);
+                    constexpr int64_t SW = lu_sub_width<WW>();
+                    for (int64_t c0 = j0; c0 < je; c0 += SW) {
+                        const int64_t c1 = std::min<int64_t>(c0 + SW, je);
                         if (c0 > j0) {
                             {
                                 Prof pr(MP_K_LU_UPDATE, (double)(n - c0) * (c0 - j0) * (c1 - c0), s);
@@ -1024,6 +1134,30 @@ int mplu(int64_t n, int32_t prec, mpmat_t *A, int64_t *piv, const mpmat_t *b, mp
         }
     });
     if (rc != MP_OK) return rc;
+    return launch_status();
+}
+
+int mplu_solve(int64_t n, int32_t prec, const mpmat_t *LU, const int64_t *piv, const mpmat_t *B, mpmat_t *X)
+{
+    if (!valid_prec(prec) || n < 0 || !valid_mat(LU, n, n, prec) || !B || !X) return MP_ERR_ARG;
+    const int64_t nrhs = B->cols;
+    if (!valid_mat(B, n, nrhs, prec) || !valid_mat(X, n, nrhs, prec)) return MP_ERR_ARG;
+    if (n > 0 && nrhs > 0 && !piv) return MP_ERR_ARG;
+    if (overlaps(X, LU) || overlaps(X, B)) return MP_ERR_ARG;
+    if (n == 0 || nrhs == 0) return MP_OK;
+    cudaStream_t s = g_ts.stream;
+    DevStatus *st = status_ptr();
+    if (!st) return MP_ERR_CUDA;
+    const int L = limbs_of(prec);
+    Workspace ws;
+    int rc = ws.acquire(mat_bytes(1, n, nrhs, L) + padded((size_t)n * 8) + 512, s);
+    if (rc != MP_OK) return rc;
+    BMat Y = carve(ws, 1, n, nrhs, L);
+    int64_t *perm = (int64_t *)ws.take((size_t)n * 8);
+    Prof pr(MP_K_LU_SOLVE, (double)n * n * nrhs, s);
+    dispatch(prec, [&](auto w) {
+        launch_lu_solve_multi<decltype(w)::value>(bmat(LU), n, piv, bmat(B), Y, bmat(X), nrhs, perm, prec, st, s);
+    });
     return launch_status();
 }
 

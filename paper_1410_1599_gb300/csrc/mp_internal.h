@@ -58,6 +58,31 @@ void launch_gemm_simple(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n,
 template <int W>
 void launch_gemm_block(BMat A, BMat B, BMat C, int64_t batch, int64_t m, int64_t l, int64_t n,
                        int p, DevStatus *st, cudaStream_t s);
+// Several batches of equally shaped products (all of one precision) in one
+// grouped Block launch: batch g is C_b = A_b B_b for b < batch (strides in
+// the BMat batch fields), m x l x n each.  tiles_m/n and first[] are filled
+// in by the launcher.
+constexpr int LEAF_GROUP_MAX = 32;
+struct LeafBatch {
+    BMat A, B, C;
+    int64_t batch, m, l, n, tiles_m, tiles_n;
+};
+struct LeafGroup {
+    LeafBatch batch[LEAF_GROUP_MAX];
+    int64_t first[LEAF_GROUP_MAX + 1];
+    int count;
+};
+template <int W>
+void launch_gemm_block_group(LeafGroup grp, int p, DevStatus *st, cudaStream_t s);
+// one product of a serving group (gemm_group in mp_api.cu): C = A B with
+// algorithm algo, device workspace ws of ws_bytes
+struct GroupGemm {
+    int algo, cutoff;
+    int64_t m, l, n;
+    BMat A, B, C;
+    void *ws;
+    size_t ws_bytes;
+};
 // C := C - A B, each c_ij = RN(c_ij - RN(a_ik b_kj)) for k ascending
 template <int W>
 void launch_gemm_sub(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p,
@@ -142,12 +167,17 @@ void launch_lu_solve(BMat LU, int64_t n, const int64_t *piv, BMat b, BMat y, BMa
 // cand holds LU_COL_MAX_CTAS row slots; *ticket starts at 0 and is returned
 // to 0 by every launch.
 constexpr int64_t LU_COL_MAX_CTAS = 152 * 8;
-// sub-panel width of the fused panel factorisation: one column per lane of
-// the column step's row warps
+// sub-panel width of the fused panel factorisation above 256 bits (two
+// columns per lane of the column step's row warps; 64 measured fastest
+// against 32 and 128 at n = 1024, 1024 bits).  Up to 256 bits a multiply-add
+// is cheap and the whole panel is one sub-panel: the sub-panel products and
+// solves would cost more launches than the column steps' extra rounds.
 #ifndef MPG_LU_SUB
-#define MPG_LU_SUB 32
+#define MPG_LU_SUB 64
 #endif
 constexpr int64_t LU_SUB = MPG_LU_SUB;
+template <int W>
+constexpr int64_t lu_sub_width() { return W <= 8 ? 128 : LU_SUB; }
 template <int W>
 bool lu_fused_ok(int64_t panel);
 // column step k of the panel [j0, je): row updates over columns (k, ce)
@@ -161,5 +191,10 @@ void launch_lu_laswp(BMat A, int64_t n, int64_t j0, int64_t je, const int64_t *p
 // triangle L of rows and columns [j0, je)
 template <int W>
 void launch_lu_u12(BMat A, int64_t cend, int64_t j0, int64_t je, int p, DevStatus *st, cudaStream_t s);
+// X = A^-1 B for the nrhs columns of B from the factors in LU and piv; Y is
+// n x nrhs workspace, perm n int64
+template <int W>
+void launch_lu_solve_multi(BMat LU, int64_t n, const int64_t *piv, BMat B, BMat Y, BMat X, int64_t nrhs,
+                           int64_t *perm, int p, DevStatus *st, cudaStream_t s);
 
 }  // namespace mpg

@@ -333,12 +333,12 @@ template <int W> struct BlockSmCfg {
     }
 };
 
-// SUB: c starts from C's own entry and the products are subtracted (see
-// gemm_simple_kernel).
-template <int W, bool SUB = false>
-__global__ void __launch_bounds__(BlockSmCfg<W>::THREADS, BlockSmCfg<W>::MIN_CTAS)
-gemm_block_sm_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p,
-                     int64_t tiles_m, int64_t tiles_n, DevStatus *status)
+// One BM x 32 tile of C_b = A_b B_b: tile = (b, tm, tn) in row-major order
+// over batch x tiles_m x tiles_n.  SUB: c starts from C's own entry and the
+// products are subtracted (see gemm_simple_kernel).
+template <int W, bool SUB>
+MP_DEV void block_sm_tile(const BMat &A, const BMat &B, const BMat &C, int64_t m, int64_t l, int64_t n,
+                          int p, int64_t tiles_m, int64_t tiles_n, int64_t tile, DevStatus *status)
 {
     using Cfg = BlockSmCfg<W>;
     static_assert(W == 4 || W == 8 || W == 16 || W == 32 || W == 64, "leaf class (the wide class takes the Simple kernel)");
@@ -354,7 +354,6 @@ gemm_block_sm_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, in
     int8_t *sAs = reinterpret_cast<int8_t *>(sBe + BK * BN);
     int8_t *sBs = sAs + BM * BK;
 
-    const int64_t tile = blockIdx.x;
     const int64_t b = tile / (tiles_m * tiles_n);
     const int64_t tm = (tile / tiles_n) % tiles_m, tn = tile % tiles_n;
     const int tx = threadIdx.x % BN, ty = threadIdx.x / BN;
@@ -419,6 +418,29 @@ gemm_block_sm_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, in
         __syncthreads();
     }
     if (valid && st<W>(c, C, b, i, j, L)) flag(status, ST_RANGE);
+}
+
+template <int W, bool SUB = false>
+__global__ void __launch_bounds__(BlockSmCfg<W>::THREADS, BlockSmCfg<W>::MIN_CTAS)
+gemm_block_sm_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p,
+                     int64_t tiles_m, int64_t tiles_n, DevStatus *status)
+{
+    block_sm_tile<W, SUB>(A, B, C, m, l, n, p, tiles_m, tiles_n, (int64_t)blockIdx.x, status);
+}
+
+// Several batches of products of one precision in one launch (the serving
+// loop's groups: the leaves of several requests' recursions).  Batch g owns
+// the CTAs [first[g], first[g + 1]); each runs one tile of its batch.
+template <int W>
+__global__ void __launch_bounds__(BlockSmCfg<W>::THREADS, BlockSmCfg<W>::MIN_CTAS)
+gemm_block_group_kernel(const __grid_constant__ LeafGroup grp, int p, DevStatus *status)
+{
+    const int64_t t = blockIdx.x;
+    int g = 0;
+    while (g + 1 < grp.count && t >= grp.first[g + 1]) ++g;
+    const LeafBatch &lb = grp.batch[g];
+    block_sm_tile<W, false>(lb.A, lb.B, lb.C, lb.m, lb.l, lb.n, p, lb.tiles_m, lb.tiles_n, t - grp.first[g],
+                            status);
 }
 
 // ------------------------------------------- recursion: operand sums (Sec. 2)
@@ -708,6 +730,37 @@ void launch_gemm_block(BMat A, BMat B, BMat C, int64_t batch, int64_t m, int64_t
     }
 }
 
+// The batches of grp (one precision, at most LEAF_GROUP_MAX) in one launch;
+// the tile counts and first[] are filled in here.  Narrow classes only.
+template <int W>
+void launch_gemm_block_group(LeafGroup grp, int p, DevStatus *st, cudaStream_t s)
+{
+    if constexpr (is_big<W>()) {
+        for (int g = 0; g < grp.count; ++g) {
+            const LeafBatch &lb = grp.batch[g];
+            launch_gemm_block<W>(lb.A, lb.B, lb.C, lb.batch, lb.m, lb.l, lb.n, p, st, s);
+        }
+    } else {
+        using Cfg = BlockSmCfg<W>;
+        int64_t total = 0;
+        for (int g = 0; g < grp.count; ++g) {
+            LeafBatch &lb = grp.batch[g];
+            lb.tiles_m = (lb.m + Cfg::BM - 1) / Cfg::BM;
+            lb.tiles_n = (lb.n + Cfg::BN - 1) / Cfg::BN;
+            grp.first[g] = total;
+            if (lb.m > 0 && lb.n > 0) total += lb.batch * lb.tiles_m * lb.tiles_n;
+        }
+        grp.first[grp.count] = total;
+        if (total <= 0) return;
+        static std::once_flag once;                  // one GPU per process
+        std::call_once(once, [] {
+            cudaFuncSetAttribute(gemm_block_group_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Cfg::smem());
+        });
+        gemm_block_group_kernel<W><<<(unsigned)total, Cfg::THREADS, Cfg::smem(), s>>>(grp, p, st);
+    }
+}
+
 // C := C - A B with every element's products subtracted one by one,
 // k ascending (one product, not batched)
 template <int W>
@@ -792,6 +845,7 @@ void launch_border(BMat A, BMat B, BMat C, int64_t nodes, int64_t m, int64_t l, 
                                        int, DevStatus *, cudaStream_t);                         \
     template void launch_gemm_sub<W>(BMat, BMat, BMat, int64_t, int64_t, int64_t, int,          \
                                      DevStatus *, cudaStream_t);                                \
+    template void launch_gemm_block_group<W>(LeafGroup, int, DevStatus *, cudaStream_t);        \
     template void launch_rank1<W>(BMat, BMat, BMat, int64_t, int64_t, int64_t, int64_t, int,    \
                                   DevStatus *, cudaStream_t);                                   \
     template void launch_border<W>(BMat, BMat, BMat, int64_t, int64_t, int64_t, int64_t,        \

@@ -810,6 +810,109 @@ void launch_lu_solve(BMat LU, int64_t n, const int64_t *piv, BMat b, BMat y, BMa
     }
 }
 
+// ------------------------------------ solves with several right-hand sides
+// X = U^-1 L^-1 P B column by column of B, every column with exactly the
+// update sequence of the one-column solve above: forward, y_i takes
+// RN(y_i - RN(l_ij y_j)) for j = 0, 1, .., i-1; backward, x_j = RN(y_j / u_jj)
+// for j = n-1 down to 0, then y_i takes RN(y_i - RN(u_ij x_j)) for i < j.
+// One launch per column step j, all rows and right-hand sides at once.
+
+// perm = the row exchanges of piv applied in order (one thread)
+template <int W>
+__global__ void lu_perm_kernel(int64_t n, const int64_t *piv, int64_t *perm)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int64_t i = 0; i < n; ++i) perm[i] = i;
+    for (int64_t k = 0; k < n; ++k) {
+        const int64_t q = piv[k];
+        const int64_t t = perm[k];
+        perm[k] = perm[q];
+        perm[q] = t;
+    }
+}
+
+// Y(i, c) = B(perm[i], c)
+template <int W>
+__global__ void lu_gather_rows_kernel(BMat B, BMat Y, const int64_t *perm, int64_t n, int64_t nrhs, int L)
+{
+    const int64_t total = n * nrhs;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / nrhs, c = t % nrhs, src = perm[i];
+        for (int q = 0; q < L; ++q)
+            Y.limb[(int64_t)q * Y.plane + i * Y.ld + c] = B.limb[(int64_t)q * B.plane + src * B.ld + c];
+        Y.exp[i * Y.ld + c] = B.exp[src * B.ld + c];
+        Y.sign[i * Y.ld + c] = B.sign[src * B.ld + c];
+    }
+}
+
+// Y(i, c) = RN(Y(i, c) - RN(M(i, j) S(j, c))) for i in [r0, r1), c < nrhs
+template <int W>
+__global__ void lu_multi_update_kernel(BMat M, BMat S, BMat Y, int64_t j, int64_t r0, int64_t r1, int64_t nrhs,
+                                       int p, DevStatus *status)
+{
+    const RoundSpec rs = make_spec<W>(p);
+    const int64_t total = (r1 - r0) * nrhs;
+    bool bad = false;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = r0 + t / nrhs, c = t % nrhs;
+        Mp<W> m, x, y, z;
+        ld<W>(m, M, 0, i, j, rs.L);
+        ld_rw<W>(x, S, 0, j, c, rs.L);
+        ld_rw<W>(y, Y, 0, i, c, rs.L);
+        mul<W>(z, m, x, rs);
+        add<W>(y, y, z, 1u, rs);
+        bad |= st<W>(y, Y, 0, i, c, rs.L);
+    }
+    if (bad) flag(status, ST_RANGE);
+}
+
+// X(j, c) = RN(Y(j, c) / u_jj) for c < nrhs; a zero u_jj gives +0 and
+// reports the matrix singular
+template <int W>
+__global__ void lu_multi_divide_kernel(BMat LU, BMat Y, BMat X, int64_t j, int64_t nrhs, int p, DevStatus *status)
+{
+    const RoundSpec rs = make_spec<W>(p);
+    bool bad = false, sing = false;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nrhs;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        Mp<W> u, y, x;
+        ld<W>(u, LU, 0, j, j, rs.L);
+        ld_rw<W>(y, Y, 0, j, c, rs.L);
+        if (u.e == EXP_ZERO) {
+            set_zero<W>(x, 0u);
+            sing = true;
+        } else {
+            div<W>(x, y, u, rs);
+        }
+        bad |= st<W>(x, X, 0, j, c, rs.L);
+    }
+    if (bad) flag(status, ST_RANGE);
+    if (sing && status) {
+        atomicOr(&status->flags, ST_SINGULAR);
+        atomicMin(&status->singular_col, (long long)j);
+    }
+}
+
+template <int W>
+void launch_lu_solve_multi(BMat LU, int64_t n, const int64_t *piv, BMat B, BMat Y, BMat X, int64_t nrhs,
+                           int64_t *perm, int p, DevStatus *st, cudaStream_t s)
+{
+    if (n <= 0 || nrhs <= 0) return;
+    constexpr int T = 128;
+    lu_perm_kernel<W><<<1, 32, 0, s>>>(n, piv, perm);
+    lu_gather_rows_kernel<W><<<grid_for(n * nrhs, T), T, 0, s>>>(B, Y, perm, n, nrhs, (p + 63) >> 6);
+    for (int64_t j = 0; j + 1 < n; ++j)
+        lu_multi_update_kernel<W><<<grid_for((n - j - 1) * nrhs, T), T, 0, s>>>(LU, Y, Y, j, j + 1, n, nrhs, p,
+                                                                               st);
+    for (int64_t j = n - 1; j >= 0; --j) {
+        lu_multi_divide_kernel<W><<<grid_for(nrhs, T), T, 0, s>>>(LU, Y, X, j, nrhs, p, st);
+        if (j > 0)
+            lu_multi_update_kernel<W><<<grid_for(j * nrhs, T), T, 0, s>>>(LU, X, Y, j, 0, j, nrhs, p, st);
+    }
+}
+
 // true when the fused column step and the one-launch U12 solve apply
 template <int W>
 bool lu_fused_ok(int64_t panel)
@@ -863,6 +966,8 @@ void launch_lu_u12(BMat A, int64_t cend, int64_t j0, int64_t je, int p, DevStatu
                                       int, DevStatus *, int64_t *, unsigned *, cudaStream_t, bool); \
     template void launch_lu_laswp<W>(BMat, int64_t, int64_t, int64_t, const int64_t *, int,     \
                                      cudaStream_t);                                             \
-    template void launch_lu_u12<W>(BMat, int64_t, int64_t, int64_t, int, DevStatus *, cudaStream_t);
+    template void launch_lu_u12<W>(BMat, int64_t, int64_t, int64_t, int, DevStatus *, cudaStream_t); \
+    template void launch_lu_solve_multi<W>(BMat, int64_t, const int64_t *, BMat, BMat, BMat, int64_t, \
+                                           int64_t *, int, DevStatus *, cudaStream_t);
 
 }  // namespace mpg

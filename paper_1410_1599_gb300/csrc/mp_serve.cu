@@ -6,7 +6,9 @@
 // slot (a CUDA stream) is free, looking past a request that does not fit
 // yet (bounded look-ahead) so that small requests keep flowing; it groups
 // queued Simple/Block GEMMs of one precision and size bucket into a single
-// grouped Block launch; and it retires finished work by polling events.
+// grouped Block launch, and other GEMMs of one precision and size class into
+// leaf groups (each request's own recursion, the leaves of all of them in
+// shared grouped launches); and it retires finished work by polling events.
 // Operands, results and factors stay in device memory from admission to
 // retirement; memory is taken and returned stream-ordered.
 //
@@ -38,6 +40,7 @@ int gemm_block_batched(int p, BMat A, BMat B, BMat C, int64_t batch, int64_t m, 
 int fill_zero_batched(BMat M, int64_t batch, int64_t rows, int64_t cols, int p, cudaStream_t s);
 size_t gemm_scratch_bytes(int algo, int64_t m, int64_t l, int64_t n, int cutoff, int policy, int p);
 size_t lu_scratch_bytes(int64_t n, int p, int panel, int algo, int cutoff, int policy);
+int gemm_group(GroupGemm *it, int count, int p, cudaStream_t s);
 }  // namespace mpg
 
 using namespace mpg;
@@ -48,7 +51,9 @@ using Clock = std::chrono::steady_clock;
 
 constexpr int kLookAhead = 32;     // queued requests scanned past a blocked head
 constexpr int kMaxBatch = 64;      // requests per grouped launch
+constexpr int kMaxGroup = 8;       // GEMMs per leaf group
 const int64_t kBuckets[] = {64, 128, 256, 512};
+const int64_t kClasses[] = {256, 512, 1024, 2048};
 
 int limbs(int p) { return (p + 63) / 64; }
 size_t elem_bytes(int p) { return (size_t)8 * limbs(p) + 9; }
@@ -66,6 +71,7 @@ struct GraphEntry;
 
 struct Unit {                     // admitted work on one slot
     std::vector<Req *> reqs;
+    bool group = false;           // GEMMs of one precision sharing their leaf launches
     GraphEntry *graph = nullptr;  // cached graph the unit ran from (busy until retired)
     int slot = -1;
     cudaEvent_t done = nullptr;
@@ -98,6 +104,17 @@ struct GraphEntry {
     bool busy = false;
     uint64_t last = 0;
 };
+
+// size class of a GEMM for leaf groups: the bound on its largest dimension
+// (0: too large, or not a GEMM)
+int64_t group_class(const mp_request_t &r)
+{
+    if (r.kind != MP_REQ_GEMM) return 0;
+    const int64_t mx = std::max(r.m, std::max(r.l, r.n));
+    for (int64_t c : kClasses)
+        if (mx <= c) return c;
+    return 0;
+}
 
 bool batchable(const mp_request_t &r, int64_t *bucket)
 {
@@ -422,6 +439,56 @@ struct mp_server {
         return rc;
     }
 
+    // GEMMs of one precision as one group: every request's own operands,
+    // result and workspace, its own recursion, and the leaves of all of
+    // them in shared grouped launches (gemm_group)
+    int run_group(const std::vector<Req *> &qs, cudaStream_t st)
+    {
+        const int p = qs[0]->r.prec;
+        const size_t k = qs.size();
+        std::vector<GroupGemm> items(k);
+        std::vector<char *> mems(k, nullptr);
+        int rc = MP_OK;
+        for (size_t i = 0; i < k && rc == MP_OK; ++i) {
+            const mp_request_t &r = qs[i]->r;
+            const size_t sa = mat_size(p, r.m, r.l), sb = mat_size(p, r.l, r.n), sc = mat_size(p, r.m, r.n);
+            const size_t sw = gemm_scratch_bytes(r.algo, r.m, r.l, r.n, r.cutoff, MP_PEEL, p);
+            if (cudaMallocAsync((void **)&mems[i], sa + sb + sc + sw + 256, st) != cudaSuccess) {
+                cudaGetLastError();
+                mems[i] = nullptr;
+                rc = MP_ERR_NOMEM;
+                break;
+            }
+            mpmat_t A, B, C;
+            mat_on(A, p, r.m, r.l, mems[i]);
+            mat_on(B, p, r.l, r.n, mems[i] + sa);
+            mat_on(C, p, r.m, r.n, mems[i] + sa + sb);
+            rc = h2d(A, r.a_limb, r.a_exp, r.a_sign, st);
+            if (rc == MP_OK) rc = h2d(B, r.b_limb, r.b_exp, r.b_sign, st);
+            GroupGemm &g = items[i];
+            g.algo = r.algo;
+            g.cutoff = r.cutoff;
+            g.m = r.m;
+            g.l = r.l;
+            g.n = r.n;
+            g.A = BMat{A.limb, A.exp, A.sign, A.ld, A.plane, 0, 0};
+            g.B = BMat{B.limb, B.exp, B.sign, B.ld, B.plane, 0, 0};
+            g.C = BMat{C.limb, C.exp, C.sign, C.ld, C.plane, 0, 0};
+            g.ws = (void *)(((uintptr_t)(mems[i] + sa + sb + sc) + 255) & ~(uintptr_t)255);
+            g.ws_bytes = sw;
+        }
+        if (rc == MP_OK) rc = gemm_group(items.data(), (int)k, p, st);
+        for (size_t i = 0; i < k && rc == MP_OK; ++i) {
+            const mp_request_t &r = qs[i]->r;
+            mpmat_t C;
+            mat_on(C, p, r.m, r.n, mems[i] + mat_size(p, r.m, r.l) + mat_size(p, r.l, r.n));
+            rc = d2h(C, r.c_limb, r.c_exp, r.c_sign, st);
+        }
+        for (char *m : mems)
+            if (m) cudaFreeAsync(m, st);
+        return rc;
+    }
+
     // ------------------------------------------------------------- scheduler
     void retire_locked()
     {
@@ -479,6 +546,36 @@ struct mp_server {
                 }
                 return u;
             }
+            // GEMMs of one precision and size class whose signatures have
+            // not been seen (seen ones are candidates for the graph cache)
+            // share their leaf launches; small Simple / Block requests that
+            // wait beside them join as one leaf of their own shape
+            const int64_t cls = group_class(h->r);
+            if (cls > 0 && (graph_slots <= 0 || !seen.count(signature(h->r)))) {
+                std::vector<size_t> idx;
+                size_t need = 0;
+                for (size_t j = i; j < queue.size() && j < i + kLookAhead && (int)idx.size() < kMaxGroup; ++j) {
+                    const Req *c = queue[j];
+                    if (c->r.prec != h->r.prec || group_class(c->r) != cls) continue;
+                    if (graph_slots > 0 && seen.count(signature(c->r))) continue;
+                    if (used + need + c->bytes > budget) continue;
+                    idx.push_back(j);
+                    need += c->bytes;
+                }
+                if (idx.size() >= 2) {
+                    Unit *u = new Unit;
+                    u->slot = slot;
+                    u->group = true;
+                    u->bytes = need;
+                    for (size_t t = idx.size(); t-- > 0;) {
+                        Req *q = queue[idx[t]];
+                        if (graph_slots > 0) seen[signature(q->r)] = 1;
+                        u->reqs.insert(u->reqs.begin(), q);
+                        queue.erase(queue.begin() + (long)idx[t]);
+                    }
+                    return u;
+                }
+            }
             while (used + h->bytes > budget) {           // cached graphs give way to requests
                 GraphEntry *v = lru_idle_locked();
                 if (!v) break;
@@ -512,7 +609,9 @@ struct mp_server {
                 running.push_back(u);
                 const cudaStream_t st = streams[u->slot];
                 lk.unlock();
-                if (u->reqs.size() > 1 || u->reqs[0]->bucket > 0)
+                if (u->group)
+                    u->rc = run_group(u->reqs, st);
+                else if (u->reqs.size() > 1 || u->reqs[0]->bucket > 0)
                     u->rc = run_batch(u->reqs, u->reqs[0]->bucket, st);
                 else
                     u->rc = run_request(u, st);

@@ -1,5 +1,7 @@
 """GPU blocked LU with partial pivoting and the solves (arXiv 1410.1599
 Sec. 4) against the CPU oracle: factors, pivots and solution bit for bit."""
+from fractions import Fraction
+
 import numpy as np
 import pytest
 import torch
@@ -269,3 +271,85 @@ def test_config_lu_bit_exact_n1024(kind):
     against the oracle (about half a minute of oracle time on 16 cores)."""
     A = gen.well_conditioned(1024, 256, 5) if kind == "well" else gen.lotkin(1024, 256)
     check(A, 128, mp.WINOGRAD, 64)
+
+
+@pytest.mark.parametrize("p,n,nrhs", [(256, 40, 7), (1024, 33, 5), (8650, 14, 3)])
+def test_multi_rhs_solve_matches_single(p, n, nrhs):
+    """mplu_solve on the factors mplu left: column c of X equals, bit for
+    bit, mplu's own solution for b = column c of B, and the oracle's solve
+    with its factors (Sec. 4; the wide class at 8650 bits)."""
+    A = gen.uniform_pm1(n, n, p, 110 + n)
+    B = gen.uniform_pm1(n, nrhs, p, 120 + n)
+    F, piv, x0, rc = gpu_lu(A, B.sub(np.arange(n), [0]), 8, mp.WINOGRAD, 4)
+    assert rc == 0
+    dF, dB = dev(F), dev(B)
+    dX = mp.DeviceMP.empty(n, nrhs, p)
+    dpiv = torch.as_tensor(piv, device="cuda")
+    mp.mplu_solve(dF, dpiv, dB, dX)
+    assert mp.sync_status() == 0
+    X = dX.to_host()
+    assert_bits_equal(X.sub(np.arange(n), [0]), x0, "column 0 vs mplu's own solve")
+    Fo, pivo, rco = orc.lu(A, panel=8, algo=mp.WINOGRAD, cutoff=4)
+    assert rco == 0 and list(piv) == list(pivo)
+    for c in range(nrhs):
+        xo = orc.lu_solve(Fo, pivo, B.sub(np.arange(n), [c]))
+        assert_bits_equal(X.sub(np.arange(n), [c]), xo, "column %d vs the oracle" % c)
+
+
+def _exact_inverse(M):
+    """Gauss-Jordan in exact rationals."""
+    n = len(M)
+    a = [row[:] + [Fraction(int(i == j)) for j in range(n)] for i, row in enumerate(M)]
+    for k in range(n):
+        piv = next(i for i in range(k, n) if a[i][k] != 0)
+        a[k], a[piv] = a[piv], a[k]
+        inv = 1 / a[k][k]
+        a[k] = [v * inv for v in a[k]]
+        for i in range(n):
+            if i != k and a[i][k] != 0:
+                f = a[i][k]
+                a[i] = [vi - f * vk for vi, vk in zip(a[i], a[k])]
+    return [row[n:] for row in a]
+
+
+def test_lotkin_condition_number_small():
+    """cond_1 = ||A||_1 ||A^-1||_1 of a small Lotkin matrix (Sec. 4's
+    ill-conditioned case) from the GPU inverse (mplu, then mplu_solve with
+    B = I) agrees with the exact rational value to 12 digits."""
+    from fractions import Fraction as Fr
+    from paper_1410_1599_gb300 import norms
+
+    n, p = 12, 256
+    A = gen.lotkin(n, p)
+    F, piv, _, rc = gpu_lu(A, gen.ones(n, 1, p), 4, mp.WINOGRAD, 2)
+    assert rc == 0
+    dX = mp.DeviceMP.empty(n, n, p)
+    mp.mplu_solve(dev(F), torch.as_tensor(piv, device="cuda"), dev(gen.identity(n, p)), dX)
+    assert mp.sync_status() == 0
+    X = dX.to_host()
+    got = norms.norm1_log2(A) + norms.norm1_log2(X)
+    exact_A = [[Fr(1)] * n] + [[Fr(1, i + j + 1) for j in range(n)] for i in range(1, n)]
+    Ai = _exact_inverse(exact_A)
+    n1 = lambda M: max(sum(abs(M[i][j]) for i in range(n)) for j in range(n))
+    import math
+    want = math.log2(n1(exact_A)) + math.log2(n1(Ai))
+    assert abs(got - want) < 1e-12 * want
+
+
+@pytest.mark.parametrize("n,p", [(64, 512), (256, 1536)])
+def test_lotkin_condition_number_exact(n, p):
+    """||A||_1 ||A^-1||_1 of the Lotkin matrix from the GPU inverse (mplu,
+    then mplu_solve with B = I) equals the oracle's exact value (the integer
+    Hilbert inverse and the Sherman-Morrison update) to 10 digits of its
+    logarithm: cond_1 = 10^96.04 at n = 64, 10^389.82 at n = 256."""
+    from paper_1410_1599_gb300 import norms
+
+    A = gen.lotkin(n, p)
+    F, piv, _, rc = gpu_lu(A, gen.ones(n, 1, p), 32, mp.WINOGRAD, 16)
+    assert rc == 0
+    dX = mp.DeviceMP.empty(n, n, p)
+    mp.mplu_solve(dev(F), torch.as_tensor(piv, device="cuda"), dev(gen.identity(n, p)), dX)
+    assert mp.sync_status() == 0
+    la, li = orc.lotkin_norm1_log2(n)
+    got_a, got_i = norms.norm1_log2(A), norms.norm1_log2(dX.to_host())
+    assert abs(got_a - la) < 1e-10 and abs(got_i - li) < 1e-10 * li

@@ -175,3 +175,38 @@ def test_graph_cache_replays_bit_exact(kind):
             assert gs["captured"] == 1 and gs["replays"] == len(reqs) - 1
     for rid, (plain, cached) in outs.items():
         assert_bits_equal(cached, plain, "request %d from the graph cache" % rid)
+
+
+def test_same_precision_gemms_share_leaf_launches():
+    """GEMMs of one precision and size class that wait behind a long request
+    run as one leaf group: each request's own operand sums and combinations,
+    the leaves of all of them in shared grouped launches.  Strassen,
+    Winograd (odd sizes: peeled borders and rank-1 fix-ups), Block and Simple
+    requests together; every result equals the oracle running the request's
+    own algorithm, bit for bit, and a request of another precision waiting
+    beside them is not grouped with them."""
+    p = 512
+    big_A = gen.well_conditioned(400, 1024, 79)
+    big_b = gen.uniform_pm1(400, 1, 1024, 80)
+    shapes = [(150, 131, 97, mp.WINOGRAD, 32), (140, 200, 120, mp.STRASSEN, 48), (130, 66, 140, mp.WINOGRAD, 64),
+              (96, 100, 90, mp.BLOCK, 64), (77, 180, 101, mp.SIMPLE, 64), (200, 160, 170, mp.WINOGRAD, 40)]
+    reqs = [(gen.uniform_pm1(m, l, p, 6300 + i, -16, 16), gen.uniform_pm1(l, n, p, 6400 + i, -16, 16), algo, cut)
+            for i, (m, l, n, algo, cut) in enumerate(shapes)]
+    other = (gen.uniform_pm1(90, 80, 256, 6500, -16, 16), gen.uniform_pm1(80, 70, 256, 6501, -16, 16))
+    srv = mp.Server(budget_bytes=8 << 30, slots=1)
+    assert srv.submit_lu(100, big_A, big_b, algo=mp.SIMPLE, cutoff=64, panel=128) == 0   # holds the slot
+    for i, (A, B, algo, cut) in enumerate(reqs):
+        assert srv.submit_gemm(i, A, B, algo=algo, cutoff=cut) == 0
+    assert srv.submit_gemm(50, *other, algo=mp.WINOGRAD, cutoff=32) == 0
+    srv.drain()
+    stats = srv.stats()
+    assert stats["completed"] == len(reqs) + 2
+    assert stats["batches"] >= 1 and stats["batched_requests"] >= len(reqs)
+    for i, (A, B, algo, cut) in enumerate(reqs):
+        st, ms, out = srv.results[i]
+        assert st == mp.REQ_DONE
+        assert_bits_equal(out, orc.gemm(algo, A, B, cutoff=cut), "grouped request %d" % i)
+    st, ms, out = srv.results[50]
+    assert st == mp.REQ_DONE
+    assert_bits_equal(out, orc.gemm(orc.WINOGRAD, *other, cutoff=32), "other precision")
+    srv.close()
