@@ -91,6 +91,8 @@ def load_library(path: str = LIB_PATH):
                                            C.POINTER(MPMat)]
             lib.mplu.argtypes = [C.c_int64, C.c_int32, C.POINTER(MPMat), C.c_void_p,
                                  C.POINTER(MPMat), C.POINTER(MPMat)]
+            lib.mplu_solve.argtypes = [C.c_int64, C.c_int32, C.POINTER(MPMat), C.c_void_p,
+                                       C.POINTER(MPMat), C.POINTER(MPMat)]
             lib.mpgemm_batched.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
                                            C.c_int32, C.POINTER(MPMat), C.POINTER(MPMat),
                                            C.POINTER(MPMat)]

@@ -833,13 +833,17 @@ MP_DEV void add_impl_reg(Mp<W> &r, const Mp<W> &x, const Mp<W> &y, uint32_t neg_
         }
         return;
     }
-    // |y| > |x| ?  exponents first, mantissas on a tie (borrow of x.m - y.m)
-    uint32_t t = sub_cc(x.m[0], y.m[0]);
+    // |y| > |x| ?  exponents first, mantissas on a tie (borrow of x.m - y.m);
+    // the mantissa comparison runs only when some lane of the warp has a tie
+    bool sw = y.e > x.e;
+    if (__any_sync(__activemask(), y.e == x.e)) {
+        uint32_t t = sub_cc(x.m[0], y.m[0]);
 #pragma unroll
-    for (int i = 1; i < W; ++i) t = subc_cc(x.m[i], y.m[i]);
-    const uint32_t mlt = subc(0u, 0u);           // all ones if x.m < y.m
-    (void)t;
-    const bool sw = (y.e > x.e) || (y.e == x.e && mlt != 0u);
+        for (int i = 1; i < W; ++i) t = subc_cc(x.m[i], y.m[i]);
+        const uint32_t mlt = subc(0u, 0u);       // all ones if x.m < y.m
+        (void)t;
+        sw = sw || (y.e == x.e && mlt != 0u);
+    }
     uint32_t X[W + 1], Y[W + 1];
     X[0] = 0u;
     Y[0] = 0u;

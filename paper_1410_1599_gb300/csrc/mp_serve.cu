@@ -144,7 +144,13 @@ struct mp_server {
     // graph cache (touched by the scheduler thread only; `used` under mu)
     int graph_slots = 8;
     std::vector<GraphEntry *> graphs;
-    std::map<Sig, int> seen;
+    std::map<Sig, int> seen;      // signatures seen once (graph-cache candidates), at most kSeenMax
+    static constexpr size_t kSeenMax = 1 << 16;
+    void mark_seen(const Sig &sig)
+    {
+        if (seen.size() >= kSeenMax) seen.clear();   // forget old shapes rather than grow without bound
+        seen[sig] = 1;
+    }
     uint64_t tick = 0;
     int64_t n_captures = 0, n_replays = 0;
     size_t graph_bytes = 0;
@@ -307,8 +313,10 @@ struct mp_server {
             if (e->sig == sig) { g = e; break; }
         if (g && g->busy) return run_single(q, st);     // one entry per signature
         if (!g) {
-            int &count = seen[sig];
-            if (count++ == 0) return run_single(q, st);            // first sighting
+            if (!seen.count(sig)) {                                 // first sighting
+                mark_seen(sig);
+                return run_single(q, st);
+            }
             // the cache holds the operand buffers and, in the graph's memory
             // pool, the captured work's temporaries: the whole footprint
             const size_t need = footprint(q->r);
@@ -569,7 +577,7 @@ struct mp_server {
                     u->bytes = need;
                     for (size_t t = idx.size(); t-- > 0;) {
                         Req *q = queue[idx[t]];
-                        if (graph_slots > 0) seen[signature(q->r)] = 1;
+                        if (graph_slots > 0) mark_seen(signature(q->r));
                         u->reqs.insert(u->reqs.begin(), q);
                         queue.erase(queue.begin() + (long)idx[t]);
                     }

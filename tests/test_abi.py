@@ -85,3 +85,26 @@ def test_noalloc_limit_checked_on_the_host():
     F = binding.MPMat(p, 0, 5, 4, 4, 20, 1 << 20, 1 << 30, 1 << 31)
     G = binding.MPMat(p, 0, 0, 4, 4, 0, 0, 0, 0)
     assert lib.mpgemm_noalloc(0, 5, 4, p, 3, 64, ctypes.byref(E), ctypes.byref(F), ctypes.byref(G)) == 0
+
+
+def test_multi_rhs_solve_argument_errors_without_gpu():
+    """mplu_solve checks its arguments on the host: precision, shapes (B and
+    X n x nrhs), a missing pivot vector, X overlapping the factors or B; an
+    empty system returns at once.  (Placeholder pointers: no path here
+    reaches the device.)"""
+    lib = binding.load_library()
+    p, n, r = 256, 3, 2
+    LU = binding.MPMat(p, 0, n, n, n, n * n, 4096, 8192, 12288)
+    B = binding.MPMat(p, 0, n, r, r, n * r, 16384, 20480, 24576)
+    X = binding.MPMat(p, 0, n, r, r, n * r, 32768, 36864, 40960)
+    piv = ctypes.c_void_p(65536)
+    ok = lambda *a: lib.mplu_solve(*a)
+    bad_p = binding.MPMat(9000, 0, n, n, n, n * n, 4096, 8192, 12288)
+    assert ok(n, 9000, ctypes.byref(bad_p), piv, ctypes.byref(B), ctypes.byref(X)) == -1
+    Xs = binding.MPMat(p, 0, n, r + 1, r + 1, n * (r + 1), 32768, 36864, 40960)   # nrhs differs from B
+    assert ok(n, p, ctypes.byref(LU), piv, ctypes.byref(B), ctypes.byref(Xs)) == -1
+    assert ok(n, p, ctypes.byref(LU), None, ctypes.byref(B), ctypes.byref(X)) == -1
+    Xa = binding.MPMat(p, 0, n, r, r, n * r, 16384, 20480, 24576)                  # X = B
+    assert ok(n, p, ctypes.byref(LU), piv, ctypes.byref(B), ctypes.byref(Xa)) == -1
+    E = binding.MPMat(p, 0, 0, 0, 0, 0, 0, 0, 0)
+    assert ok(0, p, ctypes.byref(E), None, ctypes.byref(E), ctypes.byref(E)) == 0

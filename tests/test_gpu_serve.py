@@ -210,3 +210,33 @@ def test_same_precision_gemms_share_leaf_launches():
     assert st == mp.REQ_DONE
     assert_bits_equal(out, orc.gemm(orc.WINOGRAD, *other, cutoff=32), "other precision")
     srv.close()
+
+
+def test_leaf_group_with_empty_products():
+    """A leaf group that holds degenerate products (m = 0, n = 0, l = 0) beside
+    recursive ones: the empty ones return empty or +0 results, the others
+    equal the oracle, bit for bit."""
+    p = 256
+    big_A = gen.well_conditioned(300, 1024, 81)
+    big_b = gen.uniform_pm1(300, 1, 1024, 82)
+    shapes = [(120, 130, 110, mp.WINOGRAD), (0, 90, 100, mp.WINOGRAD), (100, 0, 90, mp.STRASSEN),
+              (80, 100, 0, mp.WINOGRAD), (140, 100, 150, mp.STRASSEN)]
+    reqs = [(gen.uniform_pm1(m, l, p, 6600 + i, -16, 16), gen.uniform_pm1(l, n, p, 6700 + i, -16, 16), algo)
+            for i, (m, l, n, algo) in enumerate(shapes)]
+    srv = mp.Server(budget_bytes=8 << 30, slots=1)
+    assert srv.submit_lu(100, big_A, big_b, algo=mp.SIMPLE, cutoff=64, panel=128) == 0   # holds the slot
+    for i, (A, B, algo) in enumerate(reqs):
+        assert srv.submit_gemm(i, A, B, algo=algo, cutoff=32) == 0
+    srv.drain()
+    stats = srv.stats()
+    assert stats["completed"] == len(reqs) + 1 and stats["batches"] >= 1
+    for i, (A, B, algo) in enumerate(reqs):
+        st, ms, out = srv.results[i]
+        assert st == mp.REQ_DONE
+        m, n = A.shape[0], B.shape[1]
+        assert out.exp.shape == (m, n)
+        if A.shape[1] == 0:
+            assert np.all(out.exp == gen.EXP_ZERO) and not out.limb.any() and not out.sign.any()
+        elif m and n:
+            assert_bits_equal(out, orc.gemm(algo, A, B, cutoff=32), "grouped request %d" % i)
+    srv.close()
