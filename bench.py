@@ -275,13 +275,16 @@ def run_ours(a, rank, world, local):
                    "share": v[1] / max(sum(x[1] for x in prof.values()), 1e-9)}
                for k, v in prof.items() if v[0]}
     # HBM roofline of the recursion's elementwise kernels: algorithmic bytes
-    # operand sums read 4 quadrants and write 7 child operands (11 per 7 written),
-    # combinations read 7 child products and write 4 (11 per 4 written)
+    # = the numbers each launch reads and writes (the library's work units
+    # for these classes): operand sums read 4 quadrants and write the 7
+    # children, at the last level only the children that are not plain
+    # quadrants of the parent (the leaves read those in place);
+    # combinations read 7 child products and write 4
     be = 8 * ((p + 63) // 64) + 9
     hbm = measured_peaks().get("hbm_gbs", 6768.4)
-    for k, per in (("operands", 11.0 / 7.0), ("combine", 11.0 / 4.0)):
+    for k in ("operands", "combine"):
         if k in kernels and prof[k][1] > 0:
-            gbs = prof[k][2] * per * be / (prof[k][1] * 1e-3) / 1e9
+            gbs = prof[k][2] * be / (prof[k][1] * 1e-3) / 1e9
             kernels[k]["achieved_gbs"] = round(gbs, 1)
             kernels[k]["hbm_frac"] = round(gbs / hbm, 3)
 

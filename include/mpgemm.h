@@ -381,7 +381,9 @@ int mp_profile_enable(int on);
 
 /* Totals for one class since the last enable: launches, summed device time
  * in milliseconds, and work units (MP multiply-adds for the GEMM classes,
- * elements written for the others).  Synchronises the device. */
+ * numbers read and written for the recursion's operand sums and
+ * combinations, elements written or processed for the others).
+ * Synchronises the device. */
 int mp_profile_read(int cls, int64_t *launches, double *ms, double *units);
 
 /* ---- status ------------------------------------------------------------- */

@@ -351,7 +351,7 @@ struct RecState {
 // batched launch per side and level)
 template <int W>
 void rec_down(RecState &r, int algo, const std::vector<LevelDims> &lv, int p, BMat A0, BMat B0, BMat C0,
-              Workspace &ws, cudaStream_t s)
+              Workspace &ws, cudaStream_t s, bool leaf_views = false)
 {
     const int L = limbs_of(p);
     const int D = (int)lv.size() - 1;
@@ -374,13 +374,17 @@ void rec_down(RecState &r, int algo, const std::vector<LevelDims> &lv, int p, BM
     nodes = 1;
     for (int k = 0; k < D; ++k) {
         const LevelDims &d = lv[k];
+        const bool skip = leaf_views && k == D - 1;   // plain children stay in the parents
+        // work units: numbers read (4 quadrants) and written (7 children, or
+        // the ones that are not plain quadrants)
+        const double rw = 4.0 + (skip ? (algo == MP_WINOGRAD ? 4.0 : 5.0) : 7.0);
         {
-            Prof pr(MP_K_OPERANDS, (double)nodes * 7 * (d.M / 2) * (d.K / 2), s);
-            launch_operands_a<W>(algo, r.A[k], r.A[k + 1], nodes, d.m, d.l, d.M / 2, d.K / 2, p, s);
+            Prof pr(MP_K_OPERANDS, rw * nodes * (d.M / 2) * (d.K / 2), s);
+            launch_operands_a<W>(algo, r.A[k], r.A[k + 1], nodes, d.m, d.l, d.M / 2, d.K / 2, p, s, skip);
         }
         {
-            Prof pr(MP_K_OPERANDS, (double)nodes * 7 * (d.K / 2) * (d.N / 2), s);
-            launch_operands_b<W>(algo, r.B[k], r.B[k + 1], nodes, d.l, d.n, d.K / 2, d.N / 2, p, s);
+            Prof pr(MP_K_OPERANDS, rw * nodes * (d.K / 2) * (d.N / 2), s);
+            launch_operands_b<W>(algo, r.B[k], r.B[k + 1], nodes, d.l, d.n, d.K / 2, d.N / 2, p, s, skip);
         }
         nodes *= 7;
     }
@@ -421,7 +425,8 @@ void rec_up(const RecState &r, int p, DevStatus *st, cudaStream_t s)
         const LevelDims &d = r.lv[k];
         const int64_t mr = std::min(d.M, d.m), nr = std::min(d.N, d.n);
         {
-            Prof pr(MP_K_COMBINE, (double)nodes * mr * nr, s);
+            // work units: numbers read (7 child products) and written (4 quadrants)
+            Prof pr(MP_K_COMBINE, 11.0 * nodes * (d.M / 2) * (d.N / 2), s);
             launch_combine<W>(r.algo, r.C[k + 1], r.C[k], nodes, d.M / 2, d.N / 2, mr, nr, p, st, s);
         }
         if (d.K < d.l) {
@@ -431,12 +436,42 @@ void rec_up(const RecState &r, int p, DevStatus *st, cudaStream_t s)
     }
 }
 
+// Children of the last level that are plain quadrants of their parent are
+// read by the leaves from the parent (LeafViews) instead of being copied:
+// Winograd's M2, M3, M7 take A11, A12, A22 and M2, M3, M6 take B11, B21,
+// B22; Strassen's P3, P4 take A11, A22 and P2, P5 take B11, B22.  Only
+// where the parent's even part lies inside its real rows and columns (the
+// peel policy; a zero-padded quadrant has to be materialised).
+template <int W>
+bool leaf_views_apply(int algo, const std::vector<LevelDims> &lv, LeafViews &v)
+{
+    if constexpr (W > 64) {                           // the wide class materialises every child
+        return false;
+    } else {
+        const int D = (int)lv.size() - 1;
+        if (D < 1) return false;
+        const LevelDims &d = lv[D - 1];
+        if (d.M > d.m || d.K > d.l || d.N > d.n) return false;
+        for (int t = 0; t < 7; ++t) v.qa[t] = v.qb[t] = 0;
+        if (algo == MP_WINOGRAD) {
+            v.qa[1] = 1; v.qa[2] = 2; v.qa[6] = 4;     // A11, A12, A22
+            v.qb[1] = 1; v.qb[2] = 3; v.qb[5] = 4;     // B11, B21, B22
+        } else {
+            v.qa[2] = 1; v.qa[3] = 4;                  // A11, A22
+            v.qb[1] = 1; v.qb[4] = 4;                  // B11, B22
+        }
+        return true;
+    }
+}
+
 template <int W>
 int run_recursion(int algo, const std::vector<LevelDims> &lv, int p, BMat A0, BMat B0, BMat C0,
                   Workspace &ws, DevStatus *st, cudaStream_t s)
 {
     RecState r;
-    rec_down<W>(r, algo, lv, p, A0, B0, C0, ws, s);
+    LeafViews views;
+    const bool use_views = leaf_views_apply<W>(algo, lv, views);
+    rec_down<W>(r, algo, lv, p, A0, B0, C0, ws, s, use_views);
     const int D = (int)lv.size() - 1;
     // the borders run on a second stream, overlapping the leaves, and join
     // before the combinations
@@ -452,7 +487,13 @@ int run_recursion(int algo, const std::vector<LevelDims> &lv, int p, BMat A0, BM
     // leaves: one grouped Block GEMM over all 7^D products
     {
         Prof pr(MP_K_LEAF, (double)r.leaves * lv[D].m * lv[D].l * lv[D].n, s);
-        launch_gemm_block<W>(r.A[D], r.B[D], r.C[D], r.leaves, lv[D].m, lv[D].l, lv[D].n, p, st, s);
+        if (use_views) {
+            views.Ap = r.A[D - 1];
+            views.Bp = r.B[D - 1];
+            launch_gemm_leaf_views<W>(r.A[D], r.B[D], r.C[D], views, r.leaves, lv[D].m, lv[D].l, lv[D].n, p, st, s);
+        } else {
+            launch_gemm_block<W>(r.A[D], r.B[D], r.C[D], r.leaves, lv[D].m, lv[D].l, lv[D].n, p, st, s);
+        }
     }
     if (ss) cudaStreamWaitEvent(s, ss->join, 0);
     rec_up<W>(r, p, st, s);

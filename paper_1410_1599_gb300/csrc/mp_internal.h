@@ -74,6 +74,17 @@ struct LeafGroup {
 };
 template <int W>
 void launch_gemm_block_group(LeafGroup grp, int p, DevStatus *st, cudaStream_t s);
+// The last level of a Strassen / Winograd recursion with its plain-quadrant
+// children left in the parents: child t of node b takes quadrant qa[t] of
+// parent b of Ap (1..4 = 11, 12, 21, 22; 0 = the materialised child), and
+// likewise qb[t] of Bp.
+struct LeafViews {
+    BMat Ap, Bp;
+    uint8_t qa[7], qb[7];
+};
+template <int W>
+void launch_gemm_leaf_views(BMat A, BMat B, BMat C, const LeafViews &v, int64_t batch, int64_t m, int64_t l,
+                            int64_t n, int p, DevStatus *st, cudaStream_t s);
 // one product of a serving group (gemm_group in mp_api.cu): C = A B with
 // algorithm algo, device workspace ws of ws_bytes
 struct GroupGemm {
@@ -91,12 +102,14 @@ void launch_gemm_sub(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, in
 // one level of the recursion on a batch of `nodes` parents
 //   parent A: m x l (real), even sizes M x K, halves h = M/2, k = K/2
 //   children: 7 * nodes matrices of h x k, child t of node b at index 7b + t
+// skip_plain: the children that are plain quadrants of the parent are not
+// written (the leaves read them from the parent: LeafViews)
 template <int W>
 void launch_operands_a(int algo, BMat P, BMat Ch, int64_t nodes, int64_t m, int64_t l,
-                       int64_t h, int64_t k, int p, cudaStream_t s);
+                       int64_t h, int64_t k, int p, cudaStream_t s, bool skip_plain = false);
 template <int W>
 void launch_operands_b(int algo, BMat P, BMat Ch, int64_t nodes, int64_t l, int64_t n,
-                       int64_t k, int64_t w, int p, cudaStream_t s);
+                       int64_t k, int64_t w, int p, cudaStream_t s, bool skip_plain = false);
 // combine 7 child products (h x w) into the parent C (m x n real part mr x nr)
 template <int W>
 void launch_combine(int algo, BMat Ch, BMat C, int64_t nodes, int64_t h, int64_t w,

@@ -333,12 +333,28 @@ template <int W> struct BlockSmCfg {
     }
 };
 
-// One BM x 32 tile of C_b = A_b B_b: tile = (b, tm, tn) in row-major order
-// over batch x tiles_m x tiles_n.  SUB: c starts from C's own entry and the
-// products are subtracted (see gemm_simple_kernel).
+// product b's operand: M shifted to batch element b (a view with no batch
+// stride of its own)
+MP_DEV BMat batch_view(const BMat &M, int64_t b)
+{
+    return BMat{M.limb + b * M.bs_limb, M.exp + b * M.bs_es, M.sign + b * M.bs_es, M.ld, M.plane, 0, 0};
+}
+
+// quadrant q (1..4: 11, 12, 21, 22) of parent node `node` of P, quadrants of
+// hq x wq numbers
+MP_DEV BMat quadrant_view(const BMat &P, int64_t node, int q, int64_t hq, int64_t wq)
+{
+    const int64_t off = ((q - 1) >> 1) * hq * P.ld + ((q - 1) & 1) * wq;
+    return BMat{P.limb + node * P.bs_limb + off, P.exp + node * P.bs_es + off, P.sign + node * P.bs_es + off,
+                P.ld, P.plane, 0, 0};
+}
+
+// The tile with product b's operands given as views (Ab, Bb); C is indexed
+// by batch element b.
 template <int W, bool SUB>
-MP_DEV void block_sm_tile(const BMat &A, const BMat &B, const BMat &C, int64_t m, int64_t l, int64_t n,
-                          int p, int64_t tiles_m, int64_t tiles_n, int64_t tile, DevStatus *status)
+MP_DEV void block_sm_tile_views(const BMat &A, const BMat &B, const BMat &C, int64_t b, int64_t m, int64_t l,
+                                int64_t n, int p, int64_t tiles_m, int64_t tiles_n, int64_t tile,
+                                DevStatus *status)
 {
     using Cfg = BlockSmCfg<W>;
     static_assert(W == 4 || W == 8 || W == 16 || W == 32 || W == 64, "leaf class (the wide class takes the Simple kernel)");
@@ -354,7 +370,6 @@ MP_DEV void block_sm_tile(const BMat &A, const BMat &B, const BMat &C, int64_t m
     int8_t *sAs = reinterpret_cast<int8_t *>(sBe + BK * BN);
     int8_t *sBs = sAs + BM * BK;
 
-    const int64_t b = tile / (tiles_m * tiles_n);
     const int64_t tm = (tile / tiles_n) % tiles_m, tn = tile % tiles_n;
     const int tx = threadIdx.x % BN, ty = threadIdx.x / BN;
     const int64_t i = tm * BM + ty, j = tn * BN + tx;
@@ -370,7 +385,7 @@ MP_DEV void block_sm_tile(const BMat &A, const BMat &B, const BMat &C, int64_t m
             const int cc = e % BN, kk = (e / BN) % BK, q = e / (BN * BK);
             const int64_t gj = tn * BN + cc, gk = k0 + kk;
             const uint64_t v = (q < L && gj < n && kk < kc)
-                                   ? __ldg(B.limb + b * B.bs_limb + (int64_t)q * B.plane + gk * B.ld + gj)
+                                   ? __ldg(B.limb + (int64_t)q * B.plane + gk * B.ld + gj)
                                    : 0ull;
             *reinterpret_cast<uint64_t *>(sB + (kk * BN + cc) * RB + (W - 2 - 2 * q)) = v;
         }
@@ -378,7 +393,7 @@ MP_DEV void block_sm_tile(const BMat &A, const BMat &B, const BMat &C, int64_t m
             const int kk = e % BK, rr = (e / BK) % BM, q = e / (BK * BM);
             const int64_t gi = tm * BM + rr, gk = k0 + kk;
             const uint64_t v = (q < L && gi < m && kk < kc)
-                                   ? __ldg(A.limb + b * A.bs_limb + (int64_t)q * A.plane + gi * A.ld + gk)
+                                   ? __ldg(A.limb + (int64_t)q * A.plane + gi * A.ld + gk)
                                    : 0ull;
             *reinterpret_cast<uint64_t *>(sA + (rr * BK + kk) * W + (W - 2 - 2 * q)) = v;
         }
@@ -386,15 +401,15 @@ MP_DEV void block_sm_tile(const BMat &A, const BMat &B, const BMat &C, int64_t m
             const int kk = e % BK, rr = e / BK;
             const int64_t gi = tm * BM + rr, gk = k0 + kk;
             const bool ok = gi < m && kk < kc;
-            sAe[e] = ok ? __ldg(A.exp + b * A.bs_es + gi * A.ld + gk) : EXP_ZERO;
-            sAs[e] = ok ? __ldg(A.sign + b * A.bs_es + gi * A.ld + gk) : (int8_t)0;
+            sAe[e] = ok ? __ldg(A.exp + gi * A.ld + gk) : EXP_ZERO;
+            sAs[e] = ok ? __ldg(A.sign + gi * A.ld + gk) : (int8_t)0;
         }
         for (int e = threadIdx.x; e < BK * BN; e += blockDim.x) {
             const int cc = e % BN, kk = e / BN;
             const int64_t gj = tn * BN + cc, gk = k0 + kk;
             const bool ok = gj < n && kk < kc;
-            sBe[e] = ok ? __ldg(B.exp + b * B.bs_es + gk * B.ld + gj) : EXP_ZERO;
-            sBs[e] = ok ? __ldg(B.sign + b * B.bs_es + gk * B.ld + gj) : (int8_t)0;
+            sBe[e] = ok ? __ldg(B.exp + gk * B.ld + gj) : EXP_ZERO;
+            sBs[e] = ok ? __ldg(B.sign + gk * B.ld + gj) : (int8_t)0;
         }
         __syncthreads();
         if (valid) {
@@ -420,12 +435,43 @@ MP_DEV void block_sm_tile(const BMat &A, const BMat &B, const BMat &C, int64_t m
     if (valid && st<W>(c, C, b, i, j, L)) flag(status, ST_RANGE);
 }
 
+// One BM x 32 tile of C_b = A_b B_b: tile = (b, tm, tn) in row-major order
+// over batch x tiles_m x tiles_n.  SUB: c starts from C's own entry and the
+// products are subtracted (see gemm_simple_kernel).
+template <int W, bool SUB>
+MP_DEV void block_sm_tile(const BMat &A, const BMat &B, const BMat &C, int64_t m, int64_t l, int64_t n,
+                          int p, int64_t tiles_m, int64_t tiles_n, int64_t tile, DevStatus *status)
+{
+    const int64_t b = tile / (tiles_m * tiles_n);
+    block_sm_tile_views<W, SUB>(batch_view(A, b), batch_view(B, b), C, b, m, l, n, p, tiles_m, tiles_n, tile,
+                                status);
+}
+
 template <int W, bool SUB = false>
 __global__ void __launch_bounds__(BlockSmCfg<W>::THREADS, BlockSmCfg<W>::MIN_CTAS)
 gemm_block_sm_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p,
                      int64_t tiles_m, int64_t tiles_n, DevStatus *status)
 {
     block_sm_tile<W, SUB>(A, B, C, m, l, n, p, tiles_m, tiles_n, (int64_t)blockIdx.x, status);
+}
+
+// The leaves of a Strassen / Winograd recursion, where the children that
+// are plain quadrants of their parent node (Winograd's M2, M3, M7 on the A
+// side, M2, M3, M6 on the B side; Strassen's P3, P4 / P2, P5) were not
+// copied: leaf b = 7 node + t reads such an operand straight from the
+// parent's quadrant (LeafViews), the others from the children buffers.
+template <int W>
+__global__ void __launch_bounds__(BlockSmCfg<W>::THREADS, BlockSmCfg<W>::MIN_CTAS)
+gemm_block_leaf_views_kernel(BMat A, BMat B, BMat C, const __grid_constant__ LeafViews v, int64_t m, int64_t l,
+                             int64_t n, int p, int64_t tiles_m, int64_t tiles_n, DevStatus *status)
+{
+    const int64_t tile = blockIdx.x;
+    const int64_t b = tile / (tiles_m * tiles_n);
+    const int64_t node = b / 7;
+    const int t = (int)(b % 7);
+    const BMat Ab = v.qa[t] ? quadrant_view(v.Ap, node, v.qa[t], m, l) : batch_view(A, b);
+    const BMat Bb = v.qb[t] ? quadrant_view(v.Bp, node, v.qb[t], l, n) : batch_view(B, b);
+    block_sm_tile_views<W, false>(Ab, Bb, C, b, m, l, n, p, tiles_m, tiles_n, tile, status);
 }
 
 // Several batches of products of one precision in one launch (the serving
@@ -449,8 +495,9 @@ gemm_block_group_kernel(const __grid_constant__ LeafGroup grp, int p, DevStatus 
 // or column.  Children of node b are written at 7b + t, t = product index.
 template <int W>
 __global__ void operands_a_kernel(int algo, BMat P, BMat Ch, int64_t nodes, int64_t m,
-                                  int64_t l, int64_t h, int64_t k, int p)
+                                  int64_t l, int64_t h, int64_t k, int p, int skip_plain)
 {
+    const bool cp = !skip_plain;           // write the plain-quadrant children
     const RoundSpec rs = make_spec<W>(p);
     const int64_t total = nodes * h * k;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -465,8 +512,8 @@ __global__ void operands_a_kernel(int algo, BMat P, BMat Ch, int64_t nodes, int6
         if (algo == 2) {   // Strassen: left operands of P1..P7
             add<W>(x, a11, a22, 0u, rs); st<W>(x, Ch, cb + 0, r, c, rs.L);   // A11 + A22
             add<W>(x, a21, a22, 0u, rs); st<W>(x, Ch, cb + 1, r, c, rs.L);   // A21 + A22
-            st<W>(a11, Ch, cb + 2, r, c, rs.L);                              // A11
-            st<W>(a22, Ch, cb + 3, r, c, rs.L);                              // A22
+            if (cp) st<W>(a11, Ch, cb + 2, r, c, rs.L);                      // A11
+            if (cp) st<W>(a22, Ch, cb + 3, r, c, rs.L);                      // A22
             add<W>(x, a11, a12, 0u, rs); st<W>(x, Ch, cb + 4, r, c, rs.L);   // A11 + A12
             add<W>(x, a21, a11, 1u, rs); st<W>(x, Ch, cb + 5, r, c, rs.L);   // A21 - A11
             add<W>(x, a12, a22, 1u, rs); st<W>(x, Ch, cb + 6, r, c, rs.L);   // A12 - A22
@@ -474,22 +521,23 @@ __global__ void operands_a_kernel(int algo, BMat P, BMat Ch, int64_t nodes, int6
             add<W>(x, a21, a22, 0u, rs);                                     // S1 = A21 + A22
             add<W>(y, x, a11, 1u, rs);                                       // S2 = S1 - A11
             st<W>(y, Ch, cb + 0, r, c, rs.L);                                // M1: S2
-            st<W>(a11, Ch, cb + 1, r, c, rs.L);                              // M2: A11
-            st<W>(a12, Ch, cb + 2, r, c, rs.L);                              // M3: A12
+            if (cp) st<W>(a11, Ch, cb + 1, r, c, rs.L);                      // M2: A11
+            if (cp) st<W>(a12, Ch, cb + 2, r, c, rs.L);                      // M3: A12
             st<W>(x, Ch, cb + 4, r, c, rs.L);                                // M5: S1
             add<W>(x, a12, y, 1u, rs);                                       // S4 = A12 - S2
             st<W>(x, Ch, cb + 5, r, c, rs.L);                                // M6: S4
             add<W>(x, a11, a21, 1u, rs);                                     // S3 = A11 - A21
             st<W>(x, Ch, cb + 3, r, c, rs.L);                                // M4: S3
-            st<W>(a22, Ch, cb + 6, r, c, rs.L);                              // M7: A22
+            if (cp) st<W>(a22, Ch, cb + 6, r, c, rs.L);                      // M7: A22
         }
     }
 }
 
 template <int W>
 __global__ void operands_b_kernel(int algo, BMat P, BMat Ch, int64_t nodes, int64_t l,
-                                  int64_t n, int64_t k, int64_t w, int p)
+                                  int64_t n, int64_t k, int64_t w, int p, int skip_plain)
 {
+    const bool cp = !skip_plain;           // write the plain-quadrant children
     const RoundSpec rs = make_spec<W>(p);
     const int64_t total = nodes * k * w;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -503,10 +551,10 @@ __global__ void operands_b_kernel(int algo, BMat P, BMat Ch, int64_t nodes, int6
         const int64_t cb = 7 * b;
         if (algo == 2) {   // Strassen: right operands of P1..P7
             add<W>(x, b11, b22, 0u, rs); st<W>(x, Ch, cb + 0, r, c, rs.L);   // B11 + B22
-            st<W>(b11, Ch, cb + 1, r, c, rs.L);                              // B11
+            if (cp) st<W>(b11, Ch, cb + 1, r, c, rs.L);                      // B11
             add<W>(x, b12, b22, 1u, rs); st<W>(x, Ch, cb + 2, r, c, rs.L);   // B12 - B22
             add<W>(x, b21, b11, 1u, rs); st<W>(x, Ch, cb + 3, r, c, rs.L);   // B21 - B11
-            st<W>(b22, Ch, cb + 4, r, c, rs.L);                              // B22
+            if (cp) st<W>(b22, Ch, cb + 4, r, c, rs.L);                      // B22
             add<W>(x, b11, b12, 0u, rs); st<W>(x, Ch, cb + 5, r, c, rs.L);   // B11 + B12
             add<W>(x, b21, b22, 0u, rs); st<W>(x, Ch, cb + 6, r, c, rs.L);   // B21 + B22
         } else {           // Winograd: right operands of M1..M7
@@ -518,9 +566,9 @@ __global__ void operands_b_kernel(int algo, BMat P, BMat Ch, int64_t nodes, int6
             st<W>(x, Ch, cb + 6, r, c, rs.L);                                // M7: S8
             add<W>(x, b22, b12, 1u, rs);                                     // S7 = B22 - B12
             st<W>(x, Ch, cb + 3, r, c, rs.L);                                // M4: S7
-            st<W>(b11, Ch, cb + 1, r, c, rs.L);                              // M2: B11
-            st<W>(b21, Ch, cb + 2, r, c, rs.L);                              // M3: B21
-            st<W>(b22, Ch, cb + 5, r, c, rs.L);                              // M6: B22
+            if (cp) st<W>(b11, Ch, cb + 1, r, c, rs.L);                      // M2: B11
+            if (cp) st<W>(b21, Ch, cb + 2, r, c, rs.L);                      // M3: B21
+            if (cp) st<W>(b22, Ch, cb + 5, r, c, rs.L);                      // M6: B22
         }
     }
 }
@@ -788,20 +836,40 @@ void launch_gemm_sub(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, in
 
 template <int W>
 void launch_operands_a(int algo, BMat P, BMat Ch, int64_t nodes, int64_t m, int64_t l,
-                       int64_t h, int64_t k, int p, cudaStream_t s)
+                       int64_t h, int64_t k, int p, cudaStream_t s, bool skip_plain)
 {
     const int64_t total = nodes * h * k;
     if (total <= 0) return;
-    operands_a_kernel<W><<<grid_for(total, 128), 128, 0, s>>>(algo, P, Ch, nodes, m, l, h, k, p);
+    operands_a_kernel<W><<<grid_for(total, 128), 128, 0, s>>>(algo, P, Ch, nodes, m, l, h, k, p, skip_plain ? 1 : 0);
 }
 
 template <int W>
 void launch_operands_b(int algo, BMat P, BMat Ch, int64_t nodes, int64_t l, int64_t n,
-                       int64_t k, int64_t w, int p, cudaStream_t s)
+                       int64_t k, int64_t w, int p, cudaStream_t s, bool skip_plain)
 {
     const int64_t total = nodes * k * w;
     if (total <= 0) return;
-    operands_b_kernel<W><<<grid_for(total, 128), 128, 0, s>>>(algo, P, Ch, nodes, l, n, k, w, p);
+    operands_b_kernel<W><<<grid_for(total, 128), 128, 0, s>>>(algo, P, Ch, nodes, l, n, k, w, p, skip_plain ? 1 : 0);
+}
+
+template <int W>
+void launch_gemm_leaf_views(BMat A, BMat B, BMat C, const LeafViews &v, int64_t batch, int64_t m, int64_t l,
+                            int64_t n, int p, DevStatus *st, cudaStream_t s)
+{
+    if (batch <= 0 || m <= 0 || n <= 0) return;
+    if constexpr (is_big<W>()) {
+        return;                                      // not used: the wide class materialises its children
+    } else {
+        using Cfg = BlockSmCfg<W>;
+        const int64_t tm = (m + Cfg::BM - 1) / Cfg::BM, tn = (n + Cfg::BN - 1) / Cfg::BN;
+        static std::once_flag once;                  // one GPU per process
+        std::call_once(once, [] {
+            cudaFuncSetAttribute(gemm_block_leaf_views_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Cfg::smem());
+        });
+        gemm_block_leaf_views_kernel<W><<<(unsigned)(batch * tm * tn), Cfg::THREADS, Cfg::smem(), s>>>(
+            A, B, C, v, m, l, n, p, tm, tn, st);
+    }
 }
 
 template <int W>
@@ -853,9 +921,11 @@ void launch_border(BMat A, BMat B, BMat C, int64_t nodes, int64_t m, int64_t l, 
 
 #define MPG_INSTANTIATE_REC(W)                                                                  \
     template void launch_operands_a<W>(int, BMat, BMat, int64_t, int64_t, int64_t, int64_t,     \
-                                       int64_t, int, cudaStream_t);                             \
+                                       int64_t, int, cudaStream_t, bool);                       \
     template void launch_operands_b<W>(int, BMat, BMat, int64_t, int64_t, int64_t, int64_t,     \
-                                       int64_t, int, cudaStream_t);                             \
+                                       int64_t, int, cudaStream_t, bool);                       \
+    template void launch_gemm_leaf_views<W>(BMat, BMat, BMat, const LeafViews &, int64_t, int64_t, \
+                                            int64_t, int64_t, int, DevStatus *, cudaStream_t);  \
     template void launch_combine<W>(int, BMat, BMat, int64_t, int64_t, int64_t, int64_t,        \
                                     int64_t, int, DevStatus *, cudaStream_t);
 
