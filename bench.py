@@ -27,10 +27,10 @@ sys.path.insert(0, ROOT)
 ALGO_NAMES = {"simple": 0, "block": 1, "strassen": 2, "winograd": 3}
 # DRAM bytes (read + write) of one leaf launch of the 512-bit Winograd product
 # with cutoff 64, per 64^3 leaf: one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum) of the current leaf kernel (column-wise product) at
-# n = 1024 (2401 leaves, 1.439 + 0.696 = 2.135 GB), scaled by the leaves of a
-# launch.  Reset to None whenever the leaf kernel changes.
-LEAF_TRAFFIC_PER_LEAF_P512_C64 = 2.135e9 / 2401
+# dram__bytes_write.sum) of the current leaf kernel at n = 1024 (2401
+# leaves), scaled by the leaves of a launch.  None until the TMA-staged leaf
+# has been captured; reset to None whenever the leaf kernel changes.
+LEAF_TRAFFIC_PER_LEAF_P512_C64 = None
 PEAK_IMAD_PER_CLK_PER_SM = 64      # 32-bit integer multiply-add lanes per SM per clock
 SM_COUNT_GB300 = 152
 
@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--n", type=int, default=2048)
     ap.add_argument("--prec", type=int, default=512)
     ap.add_argument("--cutoff", type=int, default=64)
+    ap.add_argument("--leaf-tma", type=int, default=1, choices=[0, 1],
+                    help="stage the Block leaves' tiles with TMA (1, the library default) or thread loads (0)")
     ap.add_argument("--no-extras", action="store_true", help="skip the other algorithms and the CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--lu-n", type=int, default=1024)
@@ -145,6 +147,7 @@ def workload_config(a):
     return {"workload": "mp_gemm_%s_n%d_p%d_cutoff%d" % (a.algo, a.n, a.prec, a.cutoff),
             "m": a.n, "l": a.n, "n": a.n, "prec_bits": a.prec, "algo": a.algo,
             "cutoff": a.cutoff, "odd": "peel", "entries": "U[-1,1)*2^e, e~U{-16..16}",
+            "leaf_staging": "tma" if a.leaf_tma else "threads",
             "l2": "inputs larger than L2 (no flush)"}
 
 
@@ -224,6 +227,7 @@ def run_ours(a, rank, world, local):
     dC = mp.DeviceMP.empty(n, n, p)
     stream = torch.cuda.Stream()
     mp.set_stream(stream)
+    mp.set_leaf_tma(bool(a.leaf_tma))
     ws_bytes = mp.workspace_size(n, n, n, p, algo, cutoff)
     ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device="cuda")
     mp.set_workspace(ws)
@@ -262,8 +266,13 @@ def run_ours(a, rank, world, local):
     launches_per_step = sum(v[0] for v in prof.values()) / a.steps
     W32 = (p + 31) // 32
     imad_per_madd = 2 * W32 * W32            # schoolbook: ceil(p/32)^2 partial products, lo + hi
-    leaf_name = "leaf_gemm" if algo != 0 else "simple_gemm"
-    nl, lms, lunits = prof[leaf_name]
+    if algo != 0:
+        # the Block leaves: TMA-staged where the layout allows, else thread-staged
+        leaf_name = "leaf_tma" if prof["leaf_tma"][0] else "leaf_gemm"
+        nl, lms, lunits = (prof["leaf_gemm"][k] + prof["leaf_tma"][k] for k in range(3))
+    else:
+        leaf_name = "simple_gemm"
+        nl, lms, lunits = prof[leaf_name]
     sm_mhz = clk.get("sm_mhz") or 2070.0
     peak = SM_COUNT_GB300 * PEAK_IMAD_PER_CLK_PER_SM * 2070e6 / 1e12      # T IMAD/s at max clock
     achieved = (lunits * imad_per_madd) / (lms * 1e-3) / 1e12 if lms > 0 else 0.0
@@ -618,7 +627,7 @@ def lu_run(n, p, algo, panel=128, cutoff=64, kind="well"):
     dev_ms = sum(v[1] for v in prof.values())
     # the trailing products' leaves against the derived integer peak: one
     # multiply-add is 2 ceil(p/32)^2 IMAD of schoolbook partial products
-    leaf_n, leaf_ms, leaf_madds = prof.get("leaf_gemm", (0, 0.0, 0.0))
+    leaf_n, leaf_ms, leaf_madds = (prof["leaf_gemm"][k] + prof["leaf_tma"][k] for k in range(3))
     leaf_roof = None
     if leaf_n and leaf_ms > 0:
         wds = -(-p // 32)

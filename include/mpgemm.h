@@ -129,6 +129,17 @@ int mp_set_odd_policy(int policy);
  * MP_ERR_ARG for any other value. */
 int mp_set_split_truncation(int on);
 
+/* Staging of the Block kernel's operand tiles (MP_BLOCK and the Strassen /
+ * Winograd leaves, Sec. 2 Eq. 2; up to 1024 bits): 1 (default) brings each
+ * k-slab's A and B limb tiles into shared memory with the GPU's bulk tensor
+ * copies (TMA), double-buffered, wherever the operands' layout allows it --
+ * a 16-byte aligned limb base and even ld, plane and batch strides, and an
+ * even column offset for a leaf read in place from its parent's quadrant;
+ * 0, and every other layout, has the CTA's threads load the tiles.  Both
+ * give the same bits; launches of the first kind are counted under
+ * MP_K_LEAF_TMA by the profiler.  MP_ERR_ARG for any other value. */
+int mp_set_leaf_tma(int on);
+
 /* LU settings used by mplu: panel width K (Sec. 4 block size, >= 1), the
  * trailing-update algorithm (MP_SIMPLE .. MP_WINOGRAD) and its cutoff
  * (0: chosen by the library, as for mpgemm). */
@@ -371,7 +382,8 @@ enum {
                             a panel by the subtracting Block kernel; A22 - T after a
                             trailing product) */
     MP_K_LU_SOLVE = 12,  /* LU: row permutation of b and the two substitutions */
-    MP_K_COUNT = 13
+    MP_K_LEAF_TMA = 13,  /* Block GEMM kernel with TMA-staged tiles (mp_set_leaf_tma) */
+    MP_K_COUNT = 14
 };
 
 /* While enabled (on != 0), every kernel the library launches from the

@@ -28,7 +28,7 @@ NOALLOC_SCRATCH_BYTES = 64 << 20
 
 # every symbol include/mpgemm.h declares
 EXPORTS = ["mp_set_stream", "mp_set_workspace", "mp_set_odd_policy", "mp_set_lu", "mp_set_lu_pivoting",
-           "mp_set_split_truncation", "mp_split_fallbacks",
+           "mp_set_split_truncation", "mp_split_fallbacks", "mp_set_leaf_tma",
            "mp_elementwise", "mp_convert", "mpgemm_workspace_size", "mpgemm",
            "mplu_workspace_size", "mplu", "mplu_solve", "mp_sync_status", "mp_singular_column",
            "mp_strerror", "mp_version", "mp_profile_enable", "mp_profile_read",
@@ -40,9 +40,9 @@ REQ_GEMM, REQ_LU_SOLVE = 0, 1
 REQ_DONE, REQ_PENDING, REQ_RUNNING, REQ_CANCELLED, REQ_FAILED = 0, 1, 2, 3, 4
 
 (K_LEAF, K_SIMPLE, K_OPERANDS, K_COMBINE, K_FIXUP, K_ELEMENTWISE, K_LU, K_SPLIT, K_SPLIT_AUX, K_EXACT,
- K_LU_TRSM, K_LU_UPDATE, K_LU_SOLVE) = range(13)
+ K_LU_TRSM, K_LU_UPDATE, K_LU_SOLVE, K_LEAF_TMA) = range(14)
 K_NAMES = ["leaf_gemm", "simple_gemm", "operands", "combine", "fixup", "elementwise", "lu_panel",
-           "split_slices", "split_aux", "exact_gemm", "lu_trsm", "lu_update", "lu_solve"]
+           "split_slices", "split_aux", "exact_gemm", "lu_trsm", "lu_update", "lu_solve", "leaf_tma"]
 
 
 class MPError(RuntimeError):
@@ -206,6 +206,11 @@ def set_lu_pivoting(on: bool = True) -> None:
 
 def set_split_truncation(on: bool = True) -> None:
     _check(load_library().mp_set_split_truncation(1 if on else 0), "split truncation")
+
+
+def set_leaf_tma(on: bool = True) -> None:
+    """Stage the Block kernel's tiles with TMA where the layout allows (default)."""
+    _check(load_library().mp_set_leaf_tma(1 if on else 0), "leaf staging")
 
 
 def split_fallbacks() -> int:

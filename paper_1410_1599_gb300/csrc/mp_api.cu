@@ -22,6 +22,7 @@ struct ThreadState {
     int lu_panel = 128, lu_algo = MP_SIMPLE, lu_cutoff = 64;
     bool lu_pivoting = true;
     bool split_truncate = true;
+    bool leaf_tma = true;
     long long singular_col = -1;
     long long split_fallbacks = 0;
 };
@@ -205,6 +206,11 @@ struct Prof {
         if (g_prof.recs.size() > 4096) g_prof.drain();
         rec = ProfRec{cls, g_prof.ev(), g_prof.ev(), units};
         cudaEventRecord(rec.a, s);
+    }
+    // the launch turned out to belong to another class (the leaf's staging)
+    void reclass(int cls)
+    {
+        if (on) rec.cls = cls;
     }
     ~Prof()
     {
@@ -469,7 +475,7 @@ int run_recursion(int algo, const std::vector<LevelDims> &lv, int p, BMat A0, BM
                   Workspace &ws, DevStatus *st, cudaStream_t s)
 {
     RecState r;
-    LeafViews views;
+    LeafViews views{};
     const bool use_views = leaf_views_apply<W>(algo, lv, views);
     rec_down<W>(r, algo, lv, p, A0, B0, C0, ws, s, use_views);
     const int D = (int)lv.size() - 1;
@@ -487,13 +493,22 @@ int run_recursion(int algo, const std::vector<LevelDims> &lv, int p, BMat A0, BM
     // leaves: one grouped Block GEMM over all 7^D products
     {
         Prof pr(MP_K_LEAF, (double)r.leaves * lv[D].m * lv[D].l * lv[D].n, s);
+        bool tma;
         if (use_views) {
             views.Ap = r.A[D - 1];
             views.Bp = r.B[D - 1];
-            launch_gemm_leaf_views<W>(r.A[D], r.B[D], r.C[D], views, r.leaves, lv[D].m, lv[D].l, lv[D].n, p, st, s);
+            views.nodes = r.leaves / 7;
+            views.a_rows = lv[D - 1].m;
+            views.a_cols = lv[D - 1].l;
+            views.b_rows = lv[D - 1].l;
+            views.b_cols = lv[D - 1].n;
+            tma = launch_gemm_leaf_views<W>(r.A[D], r.B[D], r.C[D], views, r.leaves, lv[D].m, lv[D].l, lv[D].n,
+                                            p, st, s, g_ts.leaf_tma);
         } else {
-            launch_gemm_block<W>(r.A[D], r.B[D], r.C[D], r.leaves, lv[D].m, lv[D].l, lv[D].n, p, st, s);
+            tma = launch_gemm_block<W>(r.A[D], r.B[D], r.C[D], r.leaves, lv[D].m, lv[D].l, lv[D].n, p, st, s,
+                                       g_ts.leaf_tma);
         }
+        if (tma) pr.reclass(MP_K_LEAF_TMA);
     }
     if (ss) cudaStreamWaitEvent(s, ss->join, 0);
     rec_up<W>(r, p, st, s);
@@ -629,7 +644,8 @@ int gemm_core(int algo, int cutoff, int policy, int64_t m, int64_t l, int64_t n,
     if (algo == MP_BLOCK || lv.size() <= 1) {
         Prof pr(MP_K_LEAF, (double)m * l * n, s);
         dispatch(p, [&](auto w) {
-            launch_gemm_block<decltype(w)::value>(A, B, C, 1, m, l, n, p, st, s);
+            if (launch_gemm_block<decltype(w)::value>(A, B, C, 1, m, l, n, p, st, s, g_ts.leaf_tma))
+                pr.reclass(MP_K_LEAF_TMA);
         });
         return launch_status();
     }
@@ -717,7 +733,8 @@ int gemm_block_batched(int p, BMat A, BMat B, BMat C, int64_t batch, int64_t m, 
     if (!st) return MP_ERR_CUDA;
     Prof pr(MP_K_LEAF, (double)batch * m * l * n, s);
     dispatch(p, [&](auto w) {
-        launch_gemm_block<decltype(w)::value>(A, B, C, batch, m, l, n, p, st, s);
+        if (launch_gemm_block<decltype(w)::value>(A, B, C, batch, m, l, n, p, st, s, g_ts.leaf_tma))
+            pr.reclass(MP_K_LEAF_TMA);
     });
     return launch_status();
 }
@@ -910,6 +927,13 @@ int mp_set_split_truncation(int on)
     return MP_OK;
 }
 
+int mp_set_leaf_tma(int on)
+{
+    if (on != 0 && on != 1) return MP_ERR_ARG;
+    g_ts.leaf_tma = on == 1;
+    return MP_OK;
+}
+
 int mp_profile_enable(int on)
 {
     std::lock_guard<std::mutex> lk(g_prof.mu);
@@ -1046,7 +1070,8 @@ int mpgemm_batched(int64_t batch, int64_t m, int64_t l, int64_t n, int32_t prec,
     c.bs_limb = c.bs_es = m * C->ld;
     Prof pr(MP_K_LEAF, (double)batch * m * l * n, s);
     dispatch(prec, [&](auto w) {
-        launch_gemm_block<decltype(w)::value>(a, b, c, batch, m, l, n, prec, st, s);
+        if (launch_gemm_block<decltype(w)::value>(a, b, c, batch, m, l, n, prec, st, s, g_ts.leaf_tma))
+            pr.reclass(MP_K_LEAF_TMA);
     });
     return launch_status();
 }

@@ -586,9 +586,11 @@ MP_DEV void mul_trunc(uint32_t (&P)[2 * W], const uint32_t (&a)[W], const uint32
 // window words are final and leave the window.  Returns the top W words in
 // hi, the two words just below them (P[W-1], P[W-2]) and whether anything
 // below those is nonzero.
-template <int W>
+// b is anything indexable by word: an array, a pointer or a reader of
+// shared-memory limb planes.
+template <int W, class BW>
 MP_DEV void mul_top(uint32_t (&hi)[W], uint32_t &pw1, uint32_t &pw2, bool &low_nz,
-                    const uint32_t (&a)[W], const uint32_t *b)
+                    const uint32_t (&a)[W], const BW &b)
 {
     static_assert(W % 4 == 0, "W must be a multiple of 4");
     uint32_t acc[W + 4];

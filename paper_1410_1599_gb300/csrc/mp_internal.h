@@ -2,6 +2,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -55,9 +56,14 @@ template <int W>
 void launch_gemm_simple(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int p,
                         DevStatus *st, cudaStream_t s);
 
+// C_b = A_b B_b for b < batch by the Block kernel (A_b m x l, B_b l x n).
+// With tma set and a layout the bulk tensor copies can address (see
+// limb_map), the A/B limb tiles are staged in shared memory by TMA;
+// otherwise the CTA's threads load them.  Same bits either way.  Returns
+// true when the TMA-staged kernel ran.
 template <int W>
-void launch_gemm_block(BMat A, BMat B, BMat C, int64_t batch, int64_t m, int64_t l, int64_t n,
-                       int p, DevStatus *st, cudaStream_t s);
+bool launch_gemm_block(BMat A, BMat B, BMat C, int64_t batch, int64_t m, int64_t l, int64_t n,
+                       int p, DevStatus *st, cudaStream_t s, bool tma = false);
 // Several batches of equally shaped products (all of one precision) in one
 // grouped Block launch: batch g is C_b = A_b B_b for b < batch (strides in
 // the BMat batch fields), m x l x n each.  tiles_m/n and first[] are filled
@@ -78,13 +84,28 @@ void launch_gemm_block_group(LeafGroup grp, int p, DevStatus *st, cudaStream_t s
 // children left in the parents: child t of node b takes quadrant qa[t] of
 // parent b of Ap (1..4 = 11, 12, 21, 22; 0 = the materialised child), and
 // likewise qb[t] of Bp.
+// The parents are `nodes` matrices of a_rows x a_cols (A side) and
+// b_rows x b_cols (B side), their real sizes.
 struct LeafViews {
     BMat Ap, Bp;
+    int64_t nodes, a_rows, a_cols, b_rows, b_cols;
     uint8_t qa[7], qb[7];
 };
 template <int W>
-void launch_gemm_leaf_views(BMat A, BMat B, BMat C, const LeafViews &v, int64_t batch, int64_t m, int64_t l,
-                            int64_t n, int p, DevStatus *st, cudaStream_t s);
+bool launch_gemm_leaf_views(BMat A, BMat B, BMat C, const LeafViews &v, int64_t batch, int64_t m, int64_t l,
+                            int64_t n, int p, DevStatus *st, cudaStream_t s, bool tma = false);
+
+// Tensor map for TMA loads of the limb planes of a batch of `batch`
+// rows x cols matrices laid out as M (limb q of element (b, r, c) at
+// b * bs + q * plane + r * ld + c, bs = M.bs_limb, or one matrix when
+// batch == 1): a 4-D uint64 tensor {cols, rows, L, batch}, boxes of
+// box_x x box_y elements over all L planes, zeros past the edges.  False,
+// with *map untouched, when the layout is outside what the copies can
+// address: a limb base not 16-byte aligned, an odd ld, plane or batch
+// stride (byte strides must be multiples of 16), sizes beyond the copy
+// unit's limits, or no driver entry point.
+bool limb_map(CUtensorMap *map, const BMat &M, int64_t batch, int64_t rows, int64_t cols, int L,
+              uint32_t box_x, uint32_t box_y);
 // one product of a serving group (gemm_group in mp_api.cu): C = A B with
 // algorithm algo, device workspace ws of ws_bytes
 struct GroupGemm {

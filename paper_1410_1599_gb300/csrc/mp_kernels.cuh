@@ -2,10 +2,12 @@
 // Sec. 2), instantiated once per word-capacity class W by gemm_w*.cu and
 // rec_w*.cu.
 #pragma once
+#include <cstring>
 #include <mutex>
 
 #include "mp_arith.cuh"
 #include "mp_internal.h"
+#include "mp_tc.cuh"
 
 namespace mpg {
 
@@ -197,8 +199,8 @@ MP_DEV void mul_trunc_rows_sm(uint32_t (&acc)[W + 2], const uint32_t (&a)[W], co
     }
 }
 
-// top words of the truncated product a * b, b read from shared memory:
-// acc[q] = word W-2+q of sum_{i+j >= W-2} a_i b_j 2^(32(i+j))
+// top words of the truncated product a * b (b loaded into registers from
+// shared memory): acc[q] = word W-2+q of sum_{i+j >= W-2} a_i b_j 2^(32(i+j))
 //
 // Up to 1024 bits the product is formed column by column (product
 // scanning): the partial products of word s = i + j are summed into a
@@ -211,44 +213,74 @@ MP_DEV void mul_trunc_rows_sm(uint32_t (&acc)[W + 2], const uint32_t (&a)[W], co
 // 2048 bits b does not fit in registers beside a, c and the product, and
 // rows of b words streamed from shared memory are used instead.
 template <int W>
-MP_DEV void mul_trunc_sm(uint32_t (&acc)[W + 2], const uint32_t (&a)[W], const uint32_t *bp)
+MP_DEV void mul_trunc_cols(uint32_t (&acc)[W + 2], const uint32_t (&a)[W], const uint32_t (&b)[W])
 {
-    if constexpr (W <= 32) {
-        uint32_t b[W];
+    static_assert(W <= 32, "b in registers");
+    uint32_t c0 = 0u, c1 = 0u, c2 = 0u;
+#pragma unroll
+    for (int s = W - 2; s <= 2 * W - 2; ++s) {
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            const int j = s - i;
+            if (j < 0 || j >= W) continue;
+            asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
+                "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
+                "addc.u32 %2, %2, 0;"
+                : "+r"(c0), "+r"(c1), "+r"(c2) : "r"(a[i]), "r"(b[j]));
+        }
+        acc[s - (W - 2)] = c0;
+        c0 = c1;
+        c1 = c2;
+        c2 = 0u;
+    }
+    acc[W + 1] = c0;
+}
+
+// b's mantissa in shared memory, as one record of W words (little-endian,
+// 16-byte aligned: four words per load) ...
+template <int W>
+struct RecWords {
+    const uint32_t *p;
+    MP_DEV void load(uint32_t (&b)[W]) const
+    {
 #pragma unroll
         for (int j0 = 0; j0 < W; j0 += 4) {
-            const uint4 v = *reinterpret_cast<const uint4 *>(bp + j0);
+            const uint4 v = *reinterpret_cast<const uint4 *>(p + j0);
             b[j0] = v.x;
             b[j0 + 1] = v.y;
             b[j0 + 2] = v.z;
             b[j0 + 3] = v.w;
         }
-        uint32_t c0 = 0u, c1 = 0u, c2 = 0u;
-#pragma unroll
-        for (int s = W - 2; s <= 2 * W - 2; ++s) {
-#pragma unroll
-            for (int i = 0; i < W; ++i) {
-                const int j = s - i;
-                if (j < 0 || j >= W) continue;
-                asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
-                    "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
-                    "addc.u32 %2, %2, 0;"
-                    : "+r"(c0), "+r"(c1), "+r"(c2) : "r"(a[i]), "r"(b[j]));
-            }
-            acc[s - (W - 2)] = c0;
-            c0 = c1;
-            c1 = c2;
-            c2 = 0u;
-        }
-        acc[W + 1] = c0;
-    } else {
-        mul_trunc_rows_sm<W>(acc, a, bp);
     }
-}
+    MP_DEV uint32_t operator[](int j) const { return p[j]; }
+};
 
-// t = RN_p(a * b) with b's mantissa in shared memory (p = 32W or below)
+// ... or as limb planes (limb q, most significant first, at p[q * stride]:
+// words W-1-2q and W-2-2q), the layout the bulk tensor copies produce
 template <int W>
-MP_DEV void mul_sm(Mp<W> &t, const uint32_t (&am)[W], int64_t ae, uint32_t as, const uint32_t *bm,
+struct PlaneWords {
+    const uint64_t *p;
+    int stride;
+    MP_DEV void load(uint32_t (&b)[W]) const
+    {
+#pragma unroll
+        for (int q = 0; q < W / 2; ++q) {
+            const uint64_t v = p[q * stride];
+            b[W - 2 - 2 * q] = (uint32_t)v;
+            b[W - 1 - 2 * q] = (uint32_t)(v >> 32);
+        }
+    }
+    MP_DEV uint32_t operator[](int j) const
+    {
+        const uint64_t v = p[((W - 1 - j) >> 1) * stride];
+        return (j & 1) ? (uint32_t)(v >> 32) : (uint32_t)v;
+    }
+};
+
+// t = RN_p(a * b) with b's mantissa in shared memory (p = 32W or below),
+// read through bm (RecWords or PlaneWords; PlaneWords for W <= 32 only)
+template <int W, class BR>
+MP_DEV void mul_sm(Mp<W> &t, const uint32_t (&am)[W], int64_t ae, uint32_t as, const BR &bm,
                    int64_t be, uint32_t bs, const RoundSpec &rs)
 {
     t.s = as ^ bs;
@@ -261,7 +293,13 @@ MP_DEV void mul_sm(Mp<W> &t, const uint32_t (&am)[W], int64_t ae, uint32_t as, c
         // the truncation test of mul_impl: decide from the truncated product
         // unless its error bound reaches the rounding boundary
         uint32_t acc[W + 2];
-        mul_trunc_sm<W>(acc, am, bm);
+        if constexpr (W <= 32) {
+            uint32_t b[W];
+            bm.load(b);
+            mul_trunc_cols<W>(acc, am, b);
+        } else {
+            mul_trunc_rows_sm<W>(acc, am, bm.p);
+        }
         const uint32_t w = acc[1];
         const uint32_t top = acc[W + 1] >> 31;
         const int rpos = top ? 31 : 30;
@@ -425,7 +463,7 @@ MP_DEV void block_sm_tile_views(const BMat &A, const BMat &B, const BMat &C, int
                     am[q + 3] = v.w;
                 }
                 mul_sm<W>(t, am, sAe[ty * BK + kk], (uint32_t)(sAs[ty * BK + kk] & 1),
-                          sB + (kk * BN + tx) * RB, sBe[kk * BN + tx],
+                          RecWords<W>{sB + (kk * BN + tx) * RB}, sBe[kk * BN + tx],
                           (uint32_t)(sBs[kk * BN + tx] & 1), rs);
                 add_impl<W>(c, c, t, SUB ? 1u : 0u, rs);
             }
@@ -487,6 +525,175 @@ gemm_block_group_kernel(const __grid_constant__ LeafGroup grp, int p, DevStatus 
     const LeafBatch &lb = grp.batch[g];
     block_sm_tile<W, false>(lb.A, lb.B, lb.C, lb.m, lb.l, lb.n, p, lb.tiles_m, lb.tiles_n, t - grp.first[g],
                             status);
+}
+
+// ------------------------------------------- Block leaf with TMA staging
+// The same tile as block_sm_tile_views -- one output per thread, c and a_ik
+// in registers, k ascending, so the same bits -- with the A and B limb tiles
+// of each k-chunk brought into shared memory by bulk tensor copies (TMA)
+// instead of the threads' loads.  Two stages: while the CTA works on chunk
+// c, the copy engine fetches chunk c + 1 into the other stage, and one
+// barrier per chunk separates the stages' reuse.  The copies land as limb
+// planes ([L][BK][BN] for B, [L][BM][BK] for A), which the product reads
+// through PlaneWords; planes L .. W/2-1 are zeroed once and never written.
+// Exponents and signs (9 bytes an element against 8L of limbs) are loaded by
+// the threads, with zero exponents outside the product, so the copies may
+// read past a ragged tile's edge without effect.
+#ifndef MPG_TMA16_BK
+#define MPG_TMA16_BK 12
+#endif
+template <int W> struct BlockTmaCfg {
+    using S = BlockSmCfg<W>;
+    static constexpr int BN = S::BN, BM = S::BM, THREADS = S::THREADS, MIN_CTAS = S::MIN_CTAS;
+    static constexpr int LM = W / 2;                                  // limb planes a stage holds
+    static constexpr int BK = (W <= 8) ? 16 : (W == 16 ? MPG_TMA16_BK : 6);
+    static constexpr int NB = BK * BN, NA = BM * BK;                 // elements of a B / A chunk
+    static constexpr size_t B_ST = (size_t)NB * LM * 8, A_ST = (size_t)NA * LM * 8;
+    static_assert(B_ST % 128 == 0 && A_ST % 128 == 0, "stages keep 128-byte alignment");
+    static_assert((BK * 8) % 16 == 0, "A box rows of whole 16-byte units");
+    static constexpr size_t smem()
+    {
+        return 128 + 2 * (B_ST + A_ST) + 2 * (size_t)(NB + NA) * 9 + 16;
+    }
+};
+
+// the tensor maps of one launch: the operands' batches and, for the leaves
+// with in-place quadrants, the parents (LeafViews)
+struct TmaOps {
+    CUtensorMap a, b, ap, bp;
+};
+
+constexpr long long TMA_WAIT_LIMIT = 1ll << 31;   // clock cycles, about a second
+
+template <int W, bool VIEWS>
+__global__ void __launch_bounds__(BlockTmaCfg<W>::THREADS, BlockTmaCfg<W>::MIN_CTAS)
+gemm_block_tma_kernel(const __grid_constant__ TmaOps ops, BMat A, BMat B, BMat C, const __grid_constant__ LeafViews v,
+                      int64_t m, int64_t l, int64_t n, int p, int64_t tiles_m, int64_t tiles_n, DevStatus *status)
+{
+    using Cfg = BlockTmaCfg<W>;
+    static_assert(W <= 32, "b in registers");
+    constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK, LM = Cfg::LM, NB = Cfg::NB, NA = Cfg::NA;
+    constexpr int NT = Cfg::THREADS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *sm = smem_raw + ((128u - (tc::saddr(smem_raw) & 127u)) & 127u);
+    uint64_t *sB = reinterpret_cast<uint64_t *>(sm);                 // [2][LM][BK][BN]
+    uint64_t *sA = sB + 2 * LM * NB;                                 // [2][LM][BM][BK]
+    int64_t *sBe = reinterpret_cast<int64_t *>(sA + 2 * LM * NA);   // [2][BK * BN]
+    int64_t *sAe = sBe + 2 * NB;                                     // [2][BM * BK]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sAe + 2 * NA);      // [2]
+    int8_t *sBs = reinterpret_cast<int8_t *>(bar + 2);               // [2][BK * BN]
+    int8_t *sAs = sBs + 2 * NB;                                      // [2][BM * BK]
+
+    const RoundSpec rs = make_spec<W>(p);
+    const int L = rs.L;
+    const int64_t tile = blockIdx.x;
+    const int64_t b = tile / (tiles_m * tiles_n);
+    const int64_t tm = (tile / tiles_n) % tiles_m, tn = tile % tiles_n;
+    // product b's operands: views for the exponents and signs, tensor map
+    // and box origin (x = column, y = row, w = batch element) for the limbs
+    const CUtensorMap *ma = &ops.a, *mb = &ops.b;
+    int32_t ax = 0, ay = 0, aw = (int32_t)b, bx = 0, by = 0, bw = (int32_t)b;
+    BMat Ab = batch_view(A, b), Bb = batch_view(B, b);
+    if constexpr (VIEWS) {
+        const int64_t node = b / 7;
+        const int t = (int)(b % 7);
+        if (v.qa[t]) {
+            Ab = quadrant_view(v.Ap, node, v.qa[t], m, l);
+            ma = &ops.ap;
+            ax = (int32_t)(((v.qa[t] - 1) & 1) * l);
+            ay = (int32_t)(((v.qa[t] - 1) >> 1) * m);
+            aw = (int32_t)node;
+        }
+        if (v.qb[t]) {
+            Bb = quadrant_view(v.Bp, node, v.qb[t], l, n);
+            mb = &ops.bp;
+            bx = (int32_t)(((v.qb[t] - 1) & 1) * n);
+            by = (int32_t)(((v.qb[t] - 1) >> 1) * l);
+            bw = (int32_t)node;
+        }
+    }
+    const int tx = threadIdx.x % BN, ty = threadIdx.x / BN;
+    const int64_t i = tm * BM + ty, j = tn * BN + tx;
+    const bool valid = (i < m) && (j < n);
+    const int nch = (int)((l + BK - 1) / BK);
+    const uint32_t bytes = (uint32_t)((NB + NA) * L * 8);
+
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar[0], 1);
+        tc::mbar_init(&bar[1], 1);
+        tc::mbar_fence_init();
+    }
+    // limb planes the copies do not write stay zero
+    const int zb = (LM - L) * NB, za = (LM - L) * NA;
+    for (int e = threadIdx.x; e < 2 * zb; e += NT) sB[(e / zb) * LM * NB + L * NB + e % zb] = 0ull;
+    for (int e = threadIdx.x; e < 2 * za; e += NT) sA[(e / za) * LM * NA + L * NA + e % za] = 0ull;
+    // exponents and signs of chunk ch into stage sg (zero exponent outside)
+    auto stage_es = [&](int ch, int sg) {
+        const int64_t k0 = (int64_t)ch * BK;
+        for (int e = threadIdx.x; e < NB + NA; e += NT) {
+            if (e < NB) {
+                const int kk = e / BN, cc = e % BN;
+                const int64_t gk = k0 + kk, gj = tn * BN + cc;
+                const bool ok = gk < l && gj < n;
+                sBe[sg * NB + e] = ok ? __ldg(Bb.exp + gk * Bb.ld + gj) : EXP_ZERO;
+                sBs[sg * NB + e] = ok ? __ldg(Bb.sign + gk * Bb.ld + gj) : (int8_t)0;
+            } else {
+                const int f = e - NB, rr = f / BK, kk = f % BK;
+                const int64_t gi = tm * BM + rr, gk = k0 + kk;
+                const bool ok = gi < m && gk < l;
+                sAe[sg * NA + f] = ok ? __ldg(Ab.exp + gi * Ab.ld + gk) : EXP_ZERO;
+                sAs[sg * NA + f] = ok ? __ldg(Ab.sign + gi * Ab.ld + gk) : (int8_t)0;
+            }
+        }
+    };
+    // limb tiles of chunk ch into stage sg (one thread)
+    auto issue = [&](int ch, int sg) {
+        const int32_t k0 = ch * BK;
+        tc::mbar_expect_tx(&bar[sg], bytes);
+        tc::tma_load_4d(sB + sg * LM * NB, mb, bx + (int32_t)(tn * BN), by + k0, 0, bw, &bar[sg]);
+        tc::tma_load_4d(sA + sg * LM * NA, ma, ax + k0, ay + (int32_t)(tm * BM), 0, aw, &bar[sg]);
+    };
+    stage_es(0, 0);
+    __syncthreads();
+    if (nch > 0 && threadIdx.x == 0) issue(0, 0);
+
+    Mp<W> c, t;
+    set_zero<W>(c, 0u);
+    for (int ch = 0; ch < nch; ++ch) {
+        const int sg = ch & 1;
+        const bool more = ch + 1 < nch;
+        if (more) {
+            if (threadIdx.x == 0) issue(ch + 1, sg ^ 1);   // that stage was released by the last barrier
+            stage_es(ch + 1, sg ^ 1);
+        }
+        const bool got = tc::mbar_wait(&bar[sg], (uint32_t)(ch >> 1) & 1u, nullptr, TMA_WAIT_LIMIT);
+        if (got && valid) {
+            const int kc = (int)((l - (int64_t)ch * BK) < BK ? (l - (int64_t)ch * BK) : BK);
+            const uint64_t *pa = sA + sg * LM * NA + ty * BK;
+            const uint64_t *pb = sB + sg * LM * NB + tx;
+            const int64_t *ae = sAe + sg * NA + ty * BK, *be = sBe + sg * NB + tx;
+            const int8_t *as = sAs + sg * NA + ty * BK, *bs = sBs + sg * NB + tx;
+            for (int kk = 0; kk < kc; ++kk) {
+                uint32_t am[W];
+                PlaneWords<W>{pa + kk, NA}.load(am);
+                mul_sm<W>(t, am, ae[kk], (uint32_t)(as[kk] & 1), PlaneWords<W>{pb + kk * BN, NB}, be[kk * BN],
+                          (uint32_t)(bs[kk * BN] & 1), rs);
+                add_impl<W>(c, c, t, 0u, rs);
+            }
+        }
+        if (__syncthreads_or(!got)) {
+            // a copy that did not complete in time: report it, give the
+            // copies still in flight their chance to land, and stop
+            if (threadIdx.x == 0) {
+                flag(status, ST_TIMEOUT);
+                tc::mbar_wait(&bar[sg], (uint32_t)(ch >> 1) & 1u, nullptr, TMA_WAIT_LIMIT);
+                if (more) tc::mbar_wait(&bar[sg ^ 1], (uint32_t)((ch + 1) >> 1) & 1u, nullptr, TMA_WAIT_LIMIT);
+            }
+            __syncthreads();
+            return;
+        }
+    }
+    if (valid && st<W>(c, C, b, i, j, L)) flag(status, ST_RANGE);
 }
 
 // ------------------------------------------- recursion: operand sums (Sec. 2)
@@ -747,11 +954,45 @@ void launch_gemm_simple(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n,
     gemm_simple_kernel<W><<<grid, block, 0, s>>>(A, B, C, m, l, n, p, st);
 }
 
-template <int W>
-void launch_gemm_block(BMat A, BMat B, BMat C, int64_t batch, int64_t m, int64_t l, int64_t n,
-                       int p, DevStatus *st, cudaStream_t s)
+// the TMA-staged leaf over a batch (VIEWS: with in-place quadrants)
+template <int W, bool VIEWS>
+bool launch_block_tma(const TmaOps &ops, BMat A, BMat B, BMat C, const LeafViews &v, int64_t batch, int64_t m,
+                      int64_t l, int64_t n, int p, DevStatus *st, cudaStream_t s)
 {
-    if (batch <= 0 || m <= 0 || n <= 0) return;
+    using Cfg = BlockTmaCfg<W>;
+    static std::once_flag once;                      // one GPU per process
+    static bool ready = false;
+    std::call_once(once, [] {
+        ready = cudaFuncSetAttribute(gemm_block_tma_kernel<W, VIEWS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)Cfg::smem()) == cudaSuccess;
+        if (!ready) cudaGetLastError();
+    });
+    if (!ready) return false;
+    const int64_t tm = (m + Cfg::BM - 1) / Cfg::BM, tn = (n + Cfg::BN - 1) / Cfg::BN;
+    gemm_block_tma_kernel<W, VIEWS><<<(unsigned)(batch * tm * tn), Cfg::THREADS, Cfg::smem(), s>>>(
+        ops, A, B, C, v, m, l, n, p, tm, tn, st);
+    return true;
+}
+
+template <int W>
+bool launch_gemm_block(BMat A, BMat B, BMat C, int64_t batch, int64_t m, int64_t l, int64_t n,
+                       int p, DevStatus *st, cudaStream_t s, bool tma)
+{
+    if (batch <= 0 || m <= 0 || n <= 0) return false;
+    if constexpr (W <= 32) {
+        if (tma) {
+            using Cfg = BlockTmaCfg<W>;
+            const int L = (p + 63) / 64;
+            TmaOps ops;
+            memset(&ops, 0, sizeof(ops));
+            LeafViews none;
+            memset(&none, 0, sizeof(none));
+            if (limb_map(&ops.a, A, batch, m, l, L, Cfg::BK, Cfg::BM) &&
+                limb_map(&ops.b, B, batch, l, n, L, Cfg::BN, Cfg::BK) &&
+                launch_block_tma<W, false>(ops, A, B, C, none, batch, m, l, n, p, st, s))
+                return true;
+        }
+    }
     if constexpr (is_big<W>()) {
         // wide class: the batched Simple kernel, up to 65535 products a launch
         constexpr int ty = SimpleCfg<W>::TY;
@@ -776,6 +1017,7 @@ void launch_gemm_block(BMat A, BMat B, BMat C, int64_t batch, int64_t m, int64_t
         gemm_block_sm_kernel<W><<<(unsigned)(batch * tm * tn), Cfg::THREADS, Cfg::smem(), s>>>(
             A, B, C, m, l, n, p, tm, tn, st);
     }
+    return false;
 }
 
 // The batches of grp (one precision, at most LEAF_GROUP_MAX) in one launch;
@@ -853,12 +1095,33 @@ void launch_operands_b(int algo, BMat P, BMat Ch, int64_t nodes, int64_t l, int6
 }
 
 template <int W>
-void launch_gemm_leaf_views(BMat A, BMat B, BMat C, const LeafViews &v, int64_t batch, int64_t m, int64_t l,
-                            int64_t n, int p, DevStatus *st, cudaStream_t s)
+bool launch_gemm_leaf_views(BMat A, BMat B, BMat C, const LeafViews &v, int64_t batch, int64_t m, int64_t l,
+                            int64_t n, int p, DevStatus *st, cudaStream_t s, bool tma)
 {
-    if (batch <= 0 || m <= 0 || n <= 0) return;
+    if (batch <= 0 || m <= 0 || n <= 0) return false;
+    if constexpr (W <= 32) {
+        if (tma) {
+            // a quadrant in the right half starts l (A) or n (B) columns in:
+            // the copies need that offset a whole number of 16-byte units
+            bool odd_x = false;
+            for (int t = 0; t < 7; ++t) {
+                if ((v.qa[t] == 2 || v.qa[t] == 4) && (l & 1)) odd_x = true;
+                if ((v.qb[t] == 2 || v.qb[t] == 4) && (n & 1)) odd_x = true;
+            }
+            using Cfg = BlockTmaCfg<W>;
+            const int L = (p + 63) / 64;
+            TmaOps ops;
+            memset(&ops, 0, sizeof(ops));
+            if (!odd_x && limb_map(&ops.a, A, batch, m, l, L, Cfg::BK, Cfg::BM) &&
+                limb_map(&ops.b, B, batch, l, n, L, Cfg::BN, Cfg::BK) &&
+                limb_map(&ops.ap, v.Ap, v.nodes, v.a_rows, v.a_cols, L, Cfg::BK, Cfg::BM) &&
+                limb_map(&ops.bp, v.Bp, v.nodes, v.b_rows, v.b_cols, L, Cfg::BN, Cfg::BK) &&
+                launch_block_tma<W, true>(ops, A, B, C, v, batch, m, l, n, p, st, s))
+                return true;
+        }
+    }
     if constexpr (is_big<W>()) {
-        return;                                      // not used: the wide class materialises its children
+        return false;                                // not used: the wide class materialises its children
     } else {
         using Cfg = BlockSmCfg<W>;
         const int64_t tm = (m + Cfg::BM - 1) / Cfg::BM, tn = (n + Cfg::BN - 1) / Cfg::BN;
@@ -870,6 +1133,7 @@ void launch_gemm_leaf_views(BMat A, BMat B, BMat C, const LeafViews &v, int64_t 
         gemm_block_leaf_views_kernel<W><<<(unsigned)(batch * tm * tn), Cfg::THREADS, Cfg::smem(), s>>>(
             A, B, C, v, m, l, n, p, tm, tn, st);
     }
+    return false;
 }
 
 template <int W>
@@ -909,8 +1173,8 @@ void launch_border(BMat A, BMat B, BMat C, int64_t nodes, int64_t m, int64_t l, 
                                     cudaStream_t);                                              \
     template void launch_gemm_simple<W>(BMat, BMat, BMat, int64_t, int64_t, int64_t, int,       \
                                         DevStatus *, cudaStream_t);                             \
-    template void launch_gemm_block<W>(BMat, BMat, BMat, int64_t, int64_t, int64_t, int64_t,    \
-                                       int, DevStatus *, cudaStream_t);                         \
+    template bool launch_gemm_block<W>(BMat, BMat, BMat, int64_t, int64_t, int64_t, int64_t,    \
+                                       int, DevStatus *, cudaStream_t, bool);                   \
     template void launch_gemm_sub<W>(BMat, BMat, BMat, int64_t, int64_t, int64_t, int,          \
                                      DevStatus *, cudaStream_t);                                \
     template void launch_gemm_block_group<W>(LeafGroup, int, DevStatus *, cudaStream_t);        \
@@ -924,8 +1188,9 @@ void launch_border(BMat A, BMat B, BMat C, int64_t nodes, int64_t m, int64_t l, 
                                        int64_t, int, cudaStream_t, bool);                       \
     template void launch_operands_b<W>(int, BMat, BMat, int64_t, int64_t, int64_t, int64_t,     \
                                        int64_t, int, cudaStream_t, bool);                       \
-    template void launch_gemm_leaf_views<W>(BMat, BMat, BMat, const LeafViews &, int64_t, int64_t, \
-                                            int64_t, int64_t, int, DevStatus *, cudaStream_t);  \
+    template bool launch_gemm_leaf_views<W>(BMat, BMat, BMat, const LeafViews &, int64_t, int64_t, \
+                                            int64_t, int64_t, int, DevStatus *, cudaStream_t,   \
+                                            bool);                                              \
     template void launch_combine<W>(int, BMat, BMat, int64_t, int64_t, int64_t, int64_t,        \
                                     int64_t, int, DevStatus *, cudaStream_t);
 

@@ -76,6 +76,17 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+// a 4-D box (x innermost) of this CTA's tensor map into shared memory
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int32_t x, int32_t y, int32_t z,
+                                            int32_t w, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(saddr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(saddr(bar))
+        : "memory");
+}
+
 // the same tile into the same shared-memory offset of every CTA in `mask`
 // (cluster ranks); each destination's mbarrier at `bar`'s offset receives
 // the byte count

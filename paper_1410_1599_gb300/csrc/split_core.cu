@@ -360,6 +360,32 @@ bool make_map(CUtensorMap *map, const __half *base, int64_t rows, int64_t lp, ui
 
 }  // namespace
 
+bool limb_map(CUtensorMap *map, const BMat &M, int64_t batch, int64_t rows, int64_t cols, int L,
+              uint32_t box_x, uint32_t box_y)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc || batch < 1 || rows < 1 || cols < 1 || L < 1 || L > 256) return false;
+    if (((uintptr_t)M.limb & 15) || (M.ld & 1) || (M.plane & 1)) return false;
+    if (batch > 1 && M.bs_limb <= 0) return false;
+    const int64_t bs = batch > 1 ? M.bs_limb : M.plane * L;
+    if (bs & 1) return false;
+    const int64_t lim = (int64_t)1 << 37;               // byte strides below 2^40
+    if (M.ld >= lim || M.plane >= lim || bs >= lim) return false;
+    if (cols > 0xffffffffll || rows > 0xffffffffll || batch > 0xffffffffll) return false;
+    if (box_x == 0 || box_y == 0 || box_x > 256 || box_y > 256 || (box_x * 8) % 16) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)L, (cuuint64_t)batch};
+    const cuuint64_t strides[3] = {(cuuint64_t)M.ld * 8, (cuuint64_t)M.plane * 8, (cuuint64_t)bs * 8};
+    const cuuint32_t box[4] = {box_x, box_y, (cuuint32_t)L, 1};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    CUtensorMap tmp;
+    if (enc(&tmp, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, M.limb, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    *map = tmp;
+    return true;
+}
+
 int launch_split_slices(const __half *pa, const __half *pb, int64_t m, int64_t l, int64_t n, int p,
                         int s0, long long *D, DevStatus *st, cudaStream_t s)
 {
