@@ -27,10 +27,10 @@ sys.path.insert(0, ROOT)
 ALGO_NAMES = {"simple": 0, "block": 1, "strassen": 2, "winograd": 3}
 # DRAM bytes (read + write) of one leaf launch of the 512-bit Winograd product
 # with cutoff 64, per 64^3 leaf: one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum) of the current leaf kernel at n = 1024 (2401
-# leaves), scaled by the leaves of a launch.  None until the TMA-staged leaf
-# has been captured; reset to None whenever the leaf kernel changes.
-LEAF_TRAFFIC_PER_LEAF_P512_C64 = None
+# dram__bytes_write.sum) of the current leaf kernel (TMA-staged, slabs of 8)
+# at n = 1024 (2401 leaves, 1.443 + 0.694 = 2.137 GB), scaled by the leaves of
+# a launch.  Reset to None whenever the leaf kernel changes.
+LEAF_TRAFFIC_PER_LEAF_P512_C64 = 2.137e9 / 2401
 PEAK_IMAD_PER_CLK_PER_SM = 64      # 32-bit integer multiply-add lanes per SM per clock
 SM_COUNT_GB300 = 152
 

@@ -539,14 +539,20 @@ gemm_block_group_kernel(const __grid_constant__ LeafGroup grp, int p, DevStatus 
 // Exponents and signs (9 bytes an element against 8L of limbs) are loaded by
 // the threads, with zero exponents outside the product, so the copies may
 // read past a ragged tile's edge without effect.
+#ifndef MPG_TMA8_BK
+#define MPG_TMA8_BK 16
+#endif
 #ifndef MPG_TMA16_BK
-#define MPG_TMA16_BK 12
+#define MPG_TMA16_BK 8
+#endif
+#ifndef MPG_TMA32_BK
+#define MPG_TMA32_BK 6
 #endif
 template <int W> struct BlockTmaCfg {
     using S = BlockSmCfg<W>;
     static constexpr int BN = S::BN, BM = S::BM, THREADS = S::THREADS, MIN_CTAS = S::MIN_CTAS;
     static constexpr int LM = W / 2;                                  // limb planes a stage holds
-    static constexpr int BK = (W <= 8) ? 16 : (W == 16 ? MPG_TMA16_BK : 6);
+    static constexpr int BK = (W == 4) ? 16 : (W == 8) ? MPG_TMA8_BK : (W == 16) ? MPG_TMA16_BK : MPG_TMA32_BK;
     static constexpr int NB = BK * BN, NA = BM * BK;                 // elements of a B / A chunk
     static constexpr size_t B_ST = (size_t)NB * LM * 8, A_ST = (size_t)NA * LM * 8;
     static_assert(B_ST % 128 == 0 && A_ST % 128 == 0, "stages keep 128-byte alignment");
