@@ -147,7 +147,6 @@ def workload_config(a):
     return {"workload": "mp_gemm_%s_n%d_p%d_cutoff%d" % (a.algo, a.n, a.prec, a.cutoff),
             "m": a.n, "l": a.n, "n": a.n, "prec_bits": a.prec, "algo": a.algo,
             "cutoff": a.cutoff, "odd": "peel", "entries": "U[-1,1)*2^e, e~U{-16..16}",
-            "leaf_staging": "tma" if a.leaf_tma else "threads",
             "l2": "inputs larger than L2 (no flush)"}
 
 
@@ -410,7 +409,8 @@ def run_ours(a, rank, world, local):
             "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "mp%d (u32-limb integer)" % p,
-            "data": "synthetic", "config": workload_config(a),
+            "data": "synthetic", "config": dict(workload_config(a),
+                                                leaf_staging="tma" if a.leaf_tma else "threads"),
             "parallelism": "replicas" if world > 1 else "single",
             "roofline": {"bound": "alu", "kernel": leaf_name, "achieved": round(achieved, 3),
                          "peak": round(peak, 3), "unit": "T IMAD/s",

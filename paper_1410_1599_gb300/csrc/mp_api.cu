@@ -298,6 +298,11 @@ std::vector<LevelDims> plan(int64_t m, int64_t l, int64_t n, int cutoff, int pol
     return lv;   // lv.size() - 1 recursion levels; the last entry is the leaf
 }
 
+// The recursion's buffers keep an even row stride (a padding column after
+// an odd one), so that the bulk tensor copies of the leaves can address
+// them (byte strides in 16-byte units).
+int64_t rec_ld(int64_t cols) { return cols + (cols & 1); }
+
 size_t mat_bytes(int64_t count, int64_t rows, int64_t cols, int L)
 {
     const size_t e = (size_t)count * (size_t)rows * (size_t)cols;
@@ -310,24 +315,26 @@ size_t recursion_bytes(const std::vector<LevelDims> &lv, int L)
     int64_t nodes = 1;
     for (size_t k = 1; k < lv.size(); ++k) {
         nodes *= 7;
-        total += mat_bytes(nodes, lv[k].m, lv[k].l, L);
-        total += mat_bytes(nodes, lv[k].l, lv[k].n, L);
-        total += mat_bytes(nodes, lv[k].m, lv[k].n, L);
+        total += mat_bytes(nodes, lv[k].m, rec_ld(lv[k].l), L);
+        total += mat_bytes(nodes, lv[k].l, rec_ld(lv[k].n), L);
+        total += mat_bytes(nodes, lv[k].m, rec_ld(lv[k].n), L);
     }
     return total + 256;
 }
 
-BMat carve(Workspace &ws, int64_t count, int64_t rows, int64_t cols, int L)
+// count matrices of rows x cols, row stride ld (>= cols)
+BMat carve(Workspace &ws, int64_t count, int64_t rows, int64_t cols, int L, int64_t ld = 0)
 {
-    const size_t e = (size_t)count * (size_t)rows * (size_t)cols;
+    if (ld < cols) ld = cols;
+    const size_t e = (size_t)count * (size_t)rows * (size_t)ld;
     BMat b;
     b.limb = (uint64_t *)ws.take(e * 8 * (size_t)L);
     b.exp = (int64_t *)ws.take(e * 8);
     b.sign = (int8_t *)ws.take(e);
-    b.ld = cols;
-    b.plane = rows * cols;
-    b.bs_limb = (int64_t)L * rows * cols;
-    b.bs_es = rows * cols;
+    b.ld = ld;
+    b.plane = rows * ld;
+    b.bs_limb = (int64_t)L * rows * ld;
+    b.bs_es = rows * ld;
     return b;
 }
 
@@ -372,9 +379,9 @@ void rec_down(RecState &r, int algo, const std::vector<LevelDims> &lv, int p, BM
     int64_t nodes = 1;
     for (int k = 1; k <= D; ++k) {
         nodes *= 7;
-        r.A[k] = carve(ws, nodes, lv[k].m, lv[k].l, L);
-        r.B[k] = carve(ws, nodes, lv[k].l, lv[k].n, L);
-        r.C[k] = carve(ws, nodes, lv[k].m, lv[k].n, L);
+        r.A[k] = carve(ws, nodes, lv[k].m, lv[k].l, L, rec_ld(lv[k].l));
+        r.B[k] = carve(ws, nodes, lv[k].l, lv[k].n, L, rec_ld(lv[k].n));
+        r.C[k] = carve(ws, nodes, lv[k].m, lv[k].n, L, rec_ld(lv[k].n));
     }
     r.leaves = nodes;
     nodes = 1;
@@ -476,7 +483,22 @@ int run_recursion(int algo, const std::vector<LevelDims> &lv, int p, BMat A0, BM
 {
     RecState r;
     LeafViews views{};
-    const bool use_views = leaf_views_apply<W>(algo, lv, views);
+    bool use_views = leaf_views_apply<W>(algo, lv, views);
+    if (use_views && W <= 32 && g_ts.leaf_tma) {
+        // With TMA staging, in-place quadrants pay only where the copies can
+        // start at them: an odd column offset (the leaf's l on the A side,
+        // n on the B side) or an odd row stride of the caller's matrices at
+        // the top level would leave the leaves thread-staged; materialised
+        // children (even strides) keep the copies, which gains more.
+        const int D = (int)lv.size() - 1;
+        bool odd = false;
+        for (int t = 0; t < 7; ++t) {
+            if ((views.qa[t] == 2 || views.qa[t] == 4) && (lv[D].l & 1)) odd = true;
+            if ((views.qb[t] == 2 || views.qb[t] == 4) && (lv[D].n & 1)) odd = true;
+        }
+        if (D == 1 && ((A0.ld | A0.plane | B0.ld | B0.plane) & 1)) odd = true;
+        if (odd) use_views = false;
+    }
     rec_down<W>(r, algo, lv, p, A0, B0, C0, ws, s, use_views);
     const int D = (int)lv.size() - 1;
     // the borders run on a second stream, overlapping the leaves, and join

@@ -7,9 +7,11 @@ The cases cover every capacity class the copies serve (128 to 1024 bits),
 precisions whose limb count is below the class's (planes the copies leave
 zero), ragged tiles in m, n and the k-slabs, plain Block products, batched
 products and Strassen / Winograd leaves read in place from their parents'
-quadrants, and layouts the copies cannot address (odd row strides, odd
-quadrant offsets), where the library falls back to the threads' loads.  The
-profiler's launch counts say which kernel ran."""
+quadrants, recursions whose quadrants start at odd columns (the children are
+then all written, with even row strides, and staged by TMA), and layouts the
+copies cannot address (a caller's odd row stride, 2048 bits), where the
+library falls back to the threads' loads.  The profiler's launch counts say
+which kernel ran."""
 import numpy as np
 import pytest
 
@@ -88,15 +90,30 @@ def test_recursion_leaves_in_place(algo, p, dims, cutoff):
 
 
 @pytest.mark.parametrize("algo", [mp.WINOGRAD, mp.STRASSEN])
-def test_odd_leaves_fall_back(algo):
-    # 124 -> 62 -> leaves of 31: odd children strides and quadrant offsets
-    p, n = 512, 124
+@pytest.mark.parametrize("n,cutoff", [(124, 32), (125, 32), (250, 64)])
+def test_odd_leaves_use_materialised_children(algo, n, cutoff):
+    # 124 -> 62 -> leaves of 31 (125 peeled, 250 -> 125 -> 62 with an odd
+    # parent): the quadrants' odd column offsets rule out in-place leaves,
+    # so every child is written, with an even row stride, and staged by TMA
+    p = 512
     A = gen.uniform_pm1(n, n, p, 79, -16, 16)
     B = gen.uniform_pm1(n, n, p, 80, -16, 16)
-    want = orc.gemm(algo, A, B, cutoff=32, policy=orc.PEEL)
-    got, n_tma, n_thr = run(A, B, algo, 32, True)
-    assert n_tma == 0 and n_thr >= 1
-    assert_bits_equal(got, want, "odd leaves")
+    want = orc.gemm(algo, A, B, cutoff=cutoff, policy=orc.PEEL)
+    got, n_tma, n_thr = run(A, B, algo, cutoff, True)
+    assert n_tma == 1 and n_thr == 0
+    assert_bits_equal(got, want, "odd leaves n=%d" % n)
+    ref, n_tma, n_thr = run(A, B, algo, cutoff, False)
+    assert n_tma == 0 and n_thr == 1
+    assert_bits_equal(ref, want, "odd leaves, thread-staged, n=%d" % n)
+
+
+def test_recursion_at_2048_bits_keeps_thread_staging():
+    A = gen.uniform_pm1(40, 40, 2048, 83, -16, 16)
+    B = gen.uniform_pm1(40, 40, 2048, 84, -16, 16)
+    want = orc.gemm(mp.WINOGRAD, A, B, cutoff=16, policy=orc.PEEL)
+    got, n_tma, n_thr = run(A, B, mp.WINOGRAD, 16, True)
+    assert n_tma == 0 and n_thr == 1
+    assert_bits_equal(got, want, "2048-bit leaves")
 
 
 def test_batched_products_use_tma():
