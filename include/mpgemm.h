@@ -412,6 +412,19 @@ int64_t mp_singular_column(void);
  * mp_sync_status calls of this thread (read by the later one). */
 int64_t mp_split_fallbacks(void);
 
+/* Failure-detection self-test (no counterpart in the paper).  Every device
+ * wait of the library -- the mbarrier waits of the split form's slice kernel
+ * and of the TMA-staged Block kernel -- gives up after a bounded number of
+ * clock cycles, records MP_ERR_TIMEOUT in the device status word and ends
+ * its CTA, so a copy or tensor-core operation that never completes is
+ * reported instead of hanging the device.  This call runs one CTA of that
+ * wait against an mbarrier that nothing completes, with a limit of about
+ * `cycles` SM clock cycles (1 .. 2^32), on the calling thread's stream, and
+ * returns what mp_sync_status() then reports: MP_ERR_TIMEOUT when the
+ * mechanism works (the status word is cleared again and the device stays
+ * usable).  MP_ERR_ARG for a limit outside that range. */
+int mp_wait_selftest(int64_t cycles);
+
 const char *mp_strerror(int status);
 
 /* Library version, major * 10000 + minor * 100 + patch. */

@@ -31,7 +31,7 @@ EXPORTS = ["mp_set_stream", "mp_set_workspace", "mp_set_odd_policy", "mp_set_lu"
            "mp_set_split_truncation", "mp_split_fallbacks", "mp_set_leaf_tma",
            "mp_elementwise", "mp_convert", "mpgemm_workspace_size", "mpgemm",
            "mplu_workspace_size", "mplu", "mplu_solve", "mp_sync_status", "mp_singular_column",
-           "mp_strerror", "mp_version", "mp_profile_enable", "mp_profile_read",
+           "mp_strerror", "mp_version", "mp_profile_enable", "mp_profile_read", "mp_wait_selftest",
            "mpgemm_noalloc", "mpgemm_batched", "mp_server_create", "mp_server_submit", "mp_server_cancel",
            "mp_server_poll", "mp_server_drain", "mp_server_stats", "mp_server_set_graphs",
            "mp_server_graph_stats", "mp_server_destroy"]
@@ -84,6 +84,7 @@ def load_library(path: str = LIB_PATH):
                                                   C.c_int32, C.c_int32]
             lib.mplu_workspace_size.restype = C.c_size_t
             lib.mplu_workspace_size.argtypes = [C.c_int64, C.c_int32]
+            lib.mp_wait_selftest.argtypes = [C.c_int64]
             lib.mpgemm.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.c_int32, C.c_int32,
                                    C.c_int32, C.POINTER(MPMat), C.POINTER(MPMat), C.POINTER(MPMat)]
             lib.mpgemm_noalloc.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.c_int32, C.c_int32,
@@ -229,6 +230,12 @@ def check_status(what: str = "") -> None:
 
 def version() -> int:
     return load_library().mp_version()
+
+
+def wait_selftest(cycles: int) -> int:
+    """Status of one bounded device wait on a barrier nothing completes
+    (MP_ERR_TIMEOUT = -4 when the failure detection works)."""
+    return load_library().mp_wait_selftest(cycles)
 
 
 def profile_enable(on: bool = True) -> None:

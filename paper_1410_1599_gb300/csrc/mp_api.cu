@@ -938,6 +938,17 @@ int mp_sync_status(void)
     return MP_OK;
 }
 
+int mp_wait_selftest(int64_t cycles)
+{
+    if (cycles < 1 || cycles > ((int64_t)1 << 32)) return MP_ERR_ARG;
+    DevStatus *st = status_ptr();
+    if (!st) return MP_ERR_CUDA;
+    launch_wait_selftest(st, (long long)cycles, g_ts.stream);
+    const int rc = launch_status();
+    if (rc != MP_OK) return rc;
+    return mp_sync_status();
+}
+
 int64_t mp_singular_column(void) { return g_ts.singular_col; }
 
 int64_t mp_split_fallbacks(void) { return g_ts.split_fallbacks; }

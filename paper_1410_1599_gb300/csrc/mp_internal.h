@@ -106,6 +106,10 @@ bool launch_gemm_leaf_views(BMat A, BMat B, BMat C, const LeafViews &v, int64_t 
 // unit's limits, or no driver entry point.
 bool limb_map(CUtensorMap *map, const BMat &M, int64_t batch, int64_t rows, int64_t cols, int L,
               uint32_t box_x, uint32_t box_y);
+
+// one CTA's bounded wait on an mbarrier that nothing completes (the
+// failure-detection self-test): sets ST_TIMEOUT after about `cycles` clocks
+void launch_wait_selftest(DevStatus *st, long long cycles, cudaStream_t s);
 // one product of a serving group (gemm_group in mp_api.cu): C = A B with
 // algorithm algo, device workspace ws of ws_bytes
 struct GroupGemm {

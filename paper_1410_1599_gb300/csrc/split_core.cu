@@ -360,6 +360,28 @@ bool make_map(CUtensorMap *map, const __half *base, int64_t rows, int64_t lp, ui
 
 }  // namespace
 
+// One CTA waits, through the bounded wait every mbarrier wait of the split
+// and TMA-staged Block kernels uses, on an mbarrier that nothing completes:
+// the wait gives up after about `limit` clock cycles, the timeout goes to
+// the status word, and the CTA ends (nothing was issued, nothing is in
+// flight).
+__global__ void wait_selftest_kernel(DevStatus *status, long long limit)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        tc::mbar_fence_init();
+    }
+    __syncthreads();
+    const bool got = tc::mbar_wait(&bar, 0u, nullptr, limit);
+    if (__syncthreads_or(!got) && threadIdx.x == 0) atomicOr(&status->flags, ST_TIMEOUT);
+}
+
+void launch_wait_selftest(DevStatus *st, long long cycles, cudaStream_t s)
+{
+    wait_selftest_kernel<<<1, 128, 0, s>>>(st, cycles);
+}
+
 bool limb_map(CUtensorMap *map, const BMat &M, int64_t batch, int64_t rows, int64_t cols, int L,
               uint32_t box_x, uint32_t box_y)
 {
