@@ -39,7 +39,7 @@ def run(A, B, algo, cutoff, tma):
     return dC.to_host(), prof["leaf_tma"][0], prof["leaf_gemm"][0]
 
 
-@pytest.mark.parametrize("p", [128, 160, 256, 384, 512, 1000, 1024])
+@pytest.mark.parametrize("p", [2, 64, 128, 160, 256, 384, 512, 1000, 1024])
 def test_block_even_layout_uses_tma(p):
     # ld 70 / 98 and the plane strides even: the copies apply; 66 rows and
     # 98 columns leave ragged tiles, l = 70 a ragged last k-slab
@@ -114,6 +114,24 @@ def test_recursion_at_2048_bits_keeps_thread_staging():
     got, n_tma, n_thr = run(A, B, mp.WINOGRAD, 16, True)
     assert n_tma == 0 and n_thr == 1
     assert_bits_equal(got, want, "2048-bit leaves")
+
+
+@pytest.mark.parametrize("algo", [mp.WINOGRAD, mp.STRASSEN])
+def test_mixed_policy_padding_uses_tma(algo):
+    # 139 = 3 mod 4 is padded to 140 -> 70 -> leaves of 35 (mixed policy):
+    # their odd quadrant offsets rule out in-place leaves, so every child is
+    # written (even row stride) and staged by TMA
+    p, n = 256, 139
+    A = gen.uniform_pm1(n, n, p, 85, -16, 16)
+    B = gen.uniform_pm1(n, n, p, 86, -16, 16)
+    want = orc.gemm(algo, A, B, cutoff=40, policy=orc.MIXED)
+    mp.set_odd_policy(mp.MIXED)
+    try:
+        got, n_tma, n_thr = run(A, B, algo, 40, True)
+    finally:
+        mp.set_odd_policy(mp.PEEL)
+    assert n_tma == 1 and n_thr == 0
+    assert_bits_equal(got, want, "mixed policy")
 
 
 def test_batched_products_use_tma():
