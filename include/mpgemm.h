@@ -367,7 +367,8 @@ void mp_server_destroy(mp_server_t *srv);
 
 /* kernel classes for mp_profile_read */
 enum {
-    MP_K_LEAF = 0,       /* Block GEMM kernel (plain Block and recursion leaves) */
+    MP_K_LEAF = 0,       /* Block GEMM kernel, tiles loaded by its threads (plain Block,
+                            recursion leaves, serving groups, the LU's sub-panel products) */
     MP_K_SIMPLE = 1,     /* Simple GEMM kernel */
     MP_K_OPERANDS = 2,   /* Strassen/Winograd operand sums */
     MP_K_COMBINE = 3,    /* Strassen/Winograd C combinations */
