@@ -368,7 +368,7 @@ void mp_server_destroy(mp_server_t *srv);
 /* kernel classes for mp_profile_read */
 enum {
     MP_K_LEAF = 0,       /* Block GEMM kernel, tiles loaded by its threads (plain Block,
-                            recursion leaves, serving groups, the LU's sub-panel products) */
+                            recursion leaves and serving groups the copies do not serve) */
     MP_K_SIMPLE = 1,     /* Simple GEMM kernel */
     MP_K_OPERANDS = 2,   /* Strassen/Winograd operand sums */
     MP_K_COMBINE = 3,    /* Strassen/Winograd C combinations */
