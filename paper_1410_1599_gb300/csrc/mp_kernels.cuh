@@ -552,7 +552,10 @@ gemm_block_group_kernel(const __grid_constant__ LeafGroup grp, int p, DevStatus 
 // through PlaneWords; planes L .. W/2-1 are zeroed once and never written.
 // Exponents and signs (9 bytes an element against 8L of limbs) are loaded by
 // the threads, with zero exponents outside the product, so the copies may
-// read past a ragged tile's edge without effect.
+// read past a ragged tile's edge without effect.  Slab depths BK per class
+// were chosen by measurement; at 512 bits a thread may also own R rows that
+// share each b_kj (MPG_TMA16_R; 2 measured slower than 1: 128 registers
+// leave two CTAs per SM instead of three).
 #ifndef MPG_TMA8_BK
 #define MPG_TMA8_BK 16
 #endif
