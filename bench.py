@@ -32,6 +32,10 @@ ALGO_NAMES = {"simple": 0, "block": 1, "strassen": 2, "winograd": 3}
 # a launch.  Reset to None whenever the leaf kernel changes.
 LEAF_TRAFFIC_PER_LEAF_P512_C64 = 2.137e9 / 2401
 PEAK_IMAD_PER_CLK_PER_SM = 64      # 32-bit integer multiply-add lanes per SM per clock
+# the kernels behind the library's profiler classes of the GEMM leaf
+KERNEL_OF_CLASS = {"leaf_tma": "gemm_block_tma_kernel",
+                   "leaf_gemm": "gemm_block_sm_kernel / gemm_block_leaf_views_kernel",
+                   "simple_gemm": "gemm_simple_kernel"}
 SM_COUNT_GB300 = 152
 
 
@@ -412,7 +416,8 @@ def run_ours(a, rank, world, local):
             "data": "synthetic", "config": dict(workload_config(a),
                                                 leaf_staging="tma" if a.leaf_tma else "threads"),
             "parallelism": "replicas" if world > 1 else "single",
-            "roofline": {"bound": "alu", "kernel": leaf_name, "achieved": round(achieved, 3),
+            "roofline": {"bound": "alu", "kernel": "%s (class %s)" % (KERNEL_OF_CLASS[leaf_name], leaf_name),
+                         "achieved": round(achieved, 3),
                          "peak": round(peak, 3), "unit": "T IMAD/s",
                          "frac": round(achieved / peak, 4),
                          "peak_note": "derived: 152 SMs x 64 IMAD/clk x 2070 MHz",
