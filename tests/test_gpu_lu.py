@@ -244,13 +244,14 @@ def test_tiny_systems(n, p):
 
 
 @pytest.mark.parametrize("n", [256, 384])
-@pytest.mark.parametrize("p", [256, 1024])
+@pytest.mark.parametrize("p", [128, 256, 512, 1024])
 @pytest.mark.parametrize("kind", ["well", "lotkin", "uniform"])
 def test_config_lu_bit_exact(n, p, kind):
     """The LU workload's own setup (Sec. 4 steps 1-3 with partial pivoting:
     panel 128, trailing products by Winograd with cutoff 64) over two and
     three panels, so that several trailing products recurse one level and
-    the multi-CTA column steps, U12 solves and row exchanges all run:
+    the multi-CTA column steps, U12 solves and row exchanges all run, at
+    every register class of the fused panel (128 to 1024 bits):
     factors, piv and x bit for bit against the oracle.  U[-1,1) + nI
     (no exchanges), the Lotkin matrix and plain U[-1,1) (exchanges at most
     steps)."""
