@@ -279,20 +279,6 @@ struct PlaneWords {
 
 // t = RN_p(a * b) with b's mantissa in shared memory (p = 32W or below),
 // read through bm (RecWords or PlaneWords; PlaneWords for W <= 32 only)
-// b already in registers (shared by several products); the rare exact path
-// reads the words again from the limb planes
-template <int W>
-struct HeldWords {
-    const uint32_t (&r)[W];
-    PlaneWords<W> pw;
-    MP_DEV void load(uint32_t (&b)[W]) const
-    {
-#pragma unroll
-        for (int i = 0; i < W; ++i) b[i] = r[i];
-    }
-    MP_DEV uint32_t operator[](int j) const { return pw[j]; }
-};
-
 template <int W, class BR>
 MP_DEV void mul_sm(Mp<W> &t, const uint32_t (&am)[W], int64_t ae, uint32_t as, const BR &bm,
                    int64_t be, uint32_t bs, const RoundSpec &rs)
@@ -553,9 +539,7 @@ gemm_block_group_kernel(const __grid_constant__ LeafGroup grp, int p, DevStatus 
 // Exponents and signs (9 bytes an element against 8L of limbs) are loaded by
 // the threads, with zero exponents outside the product, so the copies may
 // read past a ragged tile's edge without effect.  Slab depths BK per class
-// were chosen by measurement; at 512 bits a thread may also own R rows that
-// share each b_kj (MPG_TMA16_R; 2 measured slower than 1: 128 registers
-// leave two CTAs per SM instead of three).
+// were chosen by measurement.
 #ifndef MPG_TMA8_BK
 #define MPG_TMA8_BK 16
 #endif
@@ -565,17 +549,9 @@ gemm_block_group_kernel(const __grid_constant__ LeafGroup grp, int p, DevStatus 
 #ifndef MPG_TMA32_BK
 #define MPG_TMA32_BK 6
 #endif
-#ifndef MPG_TMA16_R
-#define MPG_TMA16_R 1
-#endif
-#ifndef MPG_TMA_R2_MINCTAS
-#define MPG_TMA_R2_MINCTAS 2
-#endif
 template <int W> struct BlockTmaCfg {
     using S = BlockSmCfg<W>;
-    static constexpr int R = (W == 16) ? MPG_TMA16_R : 1;            // rows (outputs) per thread
-    static constexpr int BN = S::BN, BM = S::BM * R, THREADS = S::THREADS;
-    static constexpr int MIN_CTAS = (R == 1) ? S::MIN_CTAS : MPG_TMA_R2_MINCTAS;
+    static constexpr int BN = S::BN, BM = S::BM, THREADS = S::THREADS, MIN_CTAS = S::MIN_CTAS;
     static constexpr int LM = W / 2;                                  // limb planes a stage holds
     static constexpr int BK = (W == 4) ? 16 : (W == 8) ? MPG_TMA8_BK : (W == 16) ? MPG_TMA16_BK : MPG_TMA32_BK;
     static constexpr int NB = BK * BN, NA = BM * BK;                 // elements of a B / A chunk
@@ -604,7 +580,7 @@ gemm_block_tma_kernel(const __grid_constant__ TmaOps ops, BMat A, BMat B, BMat C
     using Cfg = BlockTmaCfg<W>;
     static_assert(W <= 32, "b in registers");
     constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK, LM = Cfg::LM, NB = Cfg::NB, NA = Cfg::NA;
-    constexpr int NT = Cfg::THREADS, R = Cfg::R;
+    constexpr int NT = Cfg::THREADS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *sm = smem_raw + ((128u - (tc::saddr(smem_raw) & 127u)) & 127u);
     uint64_t *sB = reinterpret_cast<uint64_t *>(sm);                 // [2][LM][BK][BN]
@@ -643,10 +619,9 @@ gemm_block_tma_kernel(const __grid_constant__ TmaOps ops, BMat A, BMat B, BMat C
             bw = (int32_t)node;
         }
     }
-    // thread (tx, ty) owns the outputs (ty R + q, tx), q < R, of the tile
     const int tx = threadIdx.x % BN, ty = threadIdx.x / BN;
-    const int64_t i0 = tm * BM + ty * R, j = tn * BN + tx;
-    const bool anyv = (i0 < m) && (j < n);
+    const int64_t i = tm * BM + ty, j = tn * BN + tx;
+    const bool valid = (i < m) && (j < n);
     const int nch = (int)((l + BK - 1) / BK);
     const uint32_t bytes = (uint32_t)((NB + NA) * L * 8);
 
@@ -689,9 +664,8 @@ gemm_block_tma_kernel(const __grid_constant__ TmaOps ops, BMat A, BMat B, BMat C
     __syncthreads();
     if (nch > 0 && threadIdx.x == 0) issue(0, 0);
 
-    Mp<W> c[R], t;
-#pragma unroll
-    for (int q = 0; q < R; ++q) set_zero<W>(c[q], 0u);
+    Mp<W> c, t;
+    set_zero<W>(c, 0u);
     for (int ch = 0; ch < nch; ++ch) {
         const int sg = ch & 1;
         const bool more = ch + 1 < nch;
@@ -700,37 +674,18 @@ gemm_block_tma_kernel(const __grid_constant__ TmaOps ops, BMat A, BMat B, BMat C
             stage_es(ch + 1, sg ^ 1);
         }
         const bool got = tc::mbar_wait(&bar[sg], (uint32_t)(ch >> 1) & 1u, nullptr, TMA_WAIT_LIMIT);
-        if (got && anyv) {
+        if (got && valid) {
             const int kc = (int)((l - (int64_t)ch * BK) < BK ? (l - (int64_t)ch * BK) : BK);
-            const uint64_t *pa = sA + sg * LM * NA + ty * R * BK;
+            const uint64_t *pa = sA + sg * LM * NA + ty * BK;
             const uint64_t *pb = sB + sg * LM * NB + tx;
-            const int64_t *ae = sAe + sg * NA + ty * R * BK, *be = sBe + sg * NB + tx;
-            const int8_t *as = sAs + sg * NA + ty * R * BK, *bs = sBs + sg * NB + tx;
+            const int64_t *ae = sAe + sg * NA + ty * BK, *be = sBe + sg * NB + tx;
+            const int8_t *as = sAs + sg * NA + ty * BK, *bs = sBs + sg * NB + tx;
             for (int kk = 0; kk < kc; ++kk) {
-                if constexpr (R == 1) {
-                    uint32_t am[W];
-                    PlaneWords<W>{pa + kk, NA}.load(am);
-                    mul_sm<W>(t, am, ae[kk], (uint32_t)(as[kk] & 1), PlaneWords<W>{pb + kk * BN, NB},
-                              be[kk * BN], (uint32_t)(bs[kk * BN] & 1), rs);
-                    add_impl<W>(c[0], c[0], t, 0u, rs);
-                } else {
-                    // b_kj once for the thread's R products
-                    uint32_t bw[W];
-                    const PlaneWords<W> bp{pb + kk * BN, NB};
-                    bp.load(bw);
-                    const int64_t bek = be[kk * BN];
-                    const uint32_t bsk = (uint32_t)(bs[kk * BN] & 1);
-#pragma unroll
-                    for (int q = 0; q < R; ++q) {
-                        if (i0 + q < m) {
-                            uint32_t am[W];
-                            PlaneWords<W>{pa + q * BK + kk, NA}.load(am);
-                            mul_sm<W>(t, am, ae[q * BK + kk], (uint32_t)(as[q * BK + kk] & 1),
-                                      HeldWords<W>{bw, bp}, bek, bsk, rs);
-                            add_impl<W>(c[q], c[q], t, 0u, rs);
-                        }
-                    }
-                }
+                uint32_t am[W];
+                PlaneWords<W>{pa + kk, NA}.load(am);
+                mul_sm<W>(t, am, ae[kk], (uint32_t)(as[kk] & 1), PlaneWords<W>{pb + kk * BN, NB}, be[kk * BN],
+                          (uint32_t)(bs[kk * BN] & 1), rs);
+                add_impl<W>(c, c, t, 0u, rs);
             }
         }
         if (__syncthreads_or(!got)) {
@@ -745,11 +700,7 @@ gemm_block_tma_kernel(const __grid_constant__ TmaOps ops, BMat A, BMat B, BMat C
             return;
         }
     }
-    bool bad = false;
-#pragma unroll
-    for (int q = 0; q < R; ++q)
-        if (i0 + q < m && j < n) bad |= st<W>(c[q], C, b, i0 + q, j, L);
-    if (bad) flag(status, ST_RANGE);
+    if (valid && st<W>(c, C, b, i, j, L)) flag(status, ST_RANGE);
 }
 
 // ------------------------------------------- recursion: operand sums (Sec. 2)
