@@ -390,17 +390,23 @@ lu_column_kernel(BMat A, int64_t n, int64_t j0, int64_t k, int64_t je, int64_t c
 // s < r; it is then shared, and every row below takes
 // a_ij = RN(a_ij - RN(l_ir a_rj)) -- per element the steps s = j0 .. i-1 in
 // ascending order, as the row-step launches do.
+// three CTAs (columns) per SM: at 1024 bits that caps the kernel at 168
+// registers (a few spilled); the first panels' 640-896 columns then take two
+// rounds instead of three (U12 time -10 % at n = 1024, -12 % at n = 2048)
+#ifndef MPG_U12_MINCTAS
+#define MPG_U12_MINCTAS 3
+#endif
 template <int W>
-__global__ void __launch_bounds__(128) lu_u12_kernel(BMat A, int64_t cend, int64_t j0, int64_t je, int p,
+__global__ void __launch_bounds__(128, MPG_U12_MINCTAS) lu_u12_kernel(BMat A, int64_t cend, int64_t j0, int64_t je, int p,
                                                      DevStatus *status)
 {
     const RoundSpec rs = make_spec<W>(p);
-    __shared__ Mp<W> s_x;
+    __shared__ __align__(16) Mp<W> s_x;
     const int64_t i = j0 + threadIdx.x;
     const bool mine = i < je;
     bool bad = false;
     for (int64_t j = je + blockIdx.x; j < cend; j += gridDim.x) {
-        Mp<W> y, l, ln, x, z;
+        Mp<W> y, l, ln, z;
         if (mine) ld_rw<W>(y, A, 0, i, j, rs.L);
         if (threadIdx.x == 0) s_x = y;
         if (mine && i > j0) ld_rw<W>(ln, A, 0, i, j0, rs.L);
@@ -410,8 +416,9 @@ __global__ void __launch_bounds__(128) lu_u12_kernel(BMat A, int64_t cend, int64
                 l = ln;
                 // the next step's multiplier loads while this one multiplies
                 if (i > r + 1) ld_rw<W>(ln, A, 0, i, r + 1, rs.L);
-                x = s_x;
-                mul<W, true>(z, l, x, rs);
+                // a_rj's words are read from shared memory as the product
+                // forms, as the Block leaf reads b_kj (same bits as mul)
+                mul_sm<W>(z, l.m, l.e, l.s, RecWords<W>{s_x.m}, s_x.e, s_x.s, rs);
                 add<W, true>(y, y, z, 1u, rs);
             }
             __syncthreads();
