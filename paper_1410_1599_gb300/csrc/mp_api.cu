@@ -484,7 +484,7 @@ int run_recursion(int algo, const std::vector<LevelDims> &lv, int p, BMat A0, BM
     RecState r;
     LeafViews views{};
     bool use_views = leaf_views_apply<W>(algo, lv, views);
-    if (use_views && W <= 32 && g_ts.leaf_tma) {
+    if (use_views && W <= TMA_MAX_W && g_ts.leaf_tma) {
         // With TMA staging, in-place quadrants pay only where the copies can
         // start at them: an odd column offset (the leaf's l on the A side,
         // n on the B side) or an odd row stride of the caller's matrices at

@@ -95,6 +95,12 @@ template <int W>
 bool launch_gemm_leaf_views(BMat A, BMat B, BMat C, const LeafViews &v, int64_t batch, int64_t m, int64_t l,
                             int64_t n, int p, DevStatus *st, cudaStream_t s, bool tma = false);
 
+// Largest class whose Block leaf stages its tiles by TMA.  At 2048 bits
+// (b streamed from shared memory by rows, 255 registers) the plane layout
+// measured 433 against 290 ms for a 1024^3 Winograd product (cutoff 32), so
+// that class keeps the thread-staged records.
+constexpr int TMA_MAX_W = 32;
+
 // Tensor map for TMA loads of the limb planes of a batch of `batch`
 // rows x cols matrices laid out as M (limb q of element (b, r, c) at
 // b * bs + q * plane + r * ld + c, bs = M.bs_limb, or one matrix when

@@ -170,17 +170,18 @@ gemm_simple_kernel(BMat A, BMat B, BMat C, int64_t m, int64_t l, int64_t n, int 
 // (mantissa words little-endian; B records padded so that a warp's 16-byte
 // loads hit every bank once).
 
-// rows of b words streamed from shared memory (four per 16-byte load); each
-// partial product with the row carry as one 64-bit multiply-add
-template <int W>
-MP_DEV void mul_trunc_rows_sm(uint32_t (&acc)[W + 2], const uint32_t (&a)[W], const uint32_t *b)
+// rows of b words streamed from shared memory (four at a time, through the
+// reader br: RecWords or PlaneWords); each partial product with the row
+// carry as one 64-bit multiply-add
+template <int W, class BR>
+MP_DEV void mul_trunc_rows_sm(uint32_t (&acc)[W + 2], const uint32_t (&a)[W], const BR &br)
 {
 #pragma unroll
     for (int q = 0; q < W + 2; ++q) acc[q] = 0u;
 #pragma unroll
     for (int j0 = 0; j0 < W; j0 += 4) {
-        const uint4 v = *reinterpret_cast<const uint4 *>(b + j0);
-        const uint32_t bv[4] = {v.x, v.y, v.z, v.w};
+        uint32_t bv[4];
+        br.load4(j0, bv);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int j = j0 + u;
@@ -253,6 +254,15 @@ struct RecWords {
         }
     }
     MP_DEV uint32_t operator[](int j) const { return p[j]; }
+    // words j0 .. j0+3 (j0 a multiple of 4)
+    MP_DEV void load4(int j0, uint32_t (&v)[4]) const
+    {
+        const uint4 x = *reinterpret_cast<const uint4 *>(p + j0);
+        v[0] = x.x;
+        v[1] = x.y;
+        v[2] = x.z;
+        v[3] = x.w;
+    }
 };
 
 // ... or as limb planes (limb q, most significant first, at p[q * stride]:
@@ -274,6 +284,16 @@ struct PlaneWords {
     {
         const uint64_t v = p[((W - 1 - j) >> 1) * stride];
         return (j & 1) ? (uint32_t)(v >> 32) : (uint32_t)v;
+    }
+    // words j0 .. j0+3 (j0 a multiple of 4): the low and high halves of
+    // limbs (W-2-j0)/2 and (W-4-j0)/2
+    MP_DEV void load4(int j0, uint32_t (&v)[4]) const
+    {
+        const uint64_t x = p[((W - 2 - j0) >> 1) * stride], y = p[((W - 4 - j0) >> 1) * stride];
+        v[0] = (uint32_t)x;
+        v[1] = (uint32_t)(x >> 32);
+        v[2] = (uint32_t)y;
+        v[3] = (uint32_t)(y >> 32);
     }
 };
 
@@ -298,7 +318,7 @@ MP_DEV void mul_sm(Mp<W> &t, const uint32_t (&am)[W], int64_t ae, uint32_t as, c
             bm.load(b);
             mul_trunc_cols<W>(acc, am, b);
         } else {
-            mul_trunc_rows_sm<W>(acc, am, bm.p);
+            mul_trunc_rows_sm<W>(acc, am, bm);
         }
         const uint32_t w = acc[1];
         const uint32_t top = acc[W + 1] >> 31;
@@ -553,7 +573,8 @@ template <int W> struct BlockTmaCfg {
     using S = BlockSmCfg<W>;
     static constexpr int BN = S::BN, BM = S::BM, THREADS = S::THREADS, MIN_CTAS = S::MIN_CTAS;
     static constexpr int LM = W / 2;                                  // limb planes a stage holds
-    static constexpr int BK = (W == 4) ? 16 : (W == 8) ? MPG_TMA8_BK : (W == 16) ? MPG_TMA16_BK : MPG_TMA32_BK;
+    static constexpr int BK = (W == 4) ? 16 : (W == 8) ? MPG_TMA8_BK : (W == 16) ? MPG_TMA16_BK
+                            : (W == 32) ? MPG_TMA32_BK : 4;
     static constexpr int NB = BK * BN, NA = BM * BK;                 // elements of a B / A chunk
     static constexpr size_t B_ST = (size_t)NB * LM * 8, A_ST = (size_t)NA * LM * 8;
     static_assert(B_ST % 128 == 0 && A_ST % 128 == 0, "stages keep 128-byte alignment");
@@ -578,7 +599,7 @@ gemm_block_tma_kernel(const __grid_constant__ TmaOps ops, BMat A, BMat B, BMat C
                       int64_t m, int64_t l, int64_t n, int p, int64_t tiles_m, int64_t tiles_n, DevStatus *status)
 {
     using Cfg = BlockTmaCfg<W>;
-    static_assert(W <= 32, "b in registers");
+    static_assert(W <= 64, "register classes");
     constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK, LM = Cfg::LM, NB = Cfg::NB, NA = Cfg::NA;
     constexpr int NT = Cfg::THREADS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -986,7 +1007,7 @@ bool launch_gemm_block(BMat A, BMat B, BMat C, int64_t batch, int64_t m, int64_t
                        int p, DevStatus *st, cudaStream_t s, bool tma)
 {
     if (batch <= 0 || m <= 0 || n <= 0) return false;
-    if constexpr (W <= 32) {
+    if constexpr (W <= TMA_MAX_W) {
         if (tma) {
             using Cfg = BlockTmaCfg<W>;
             const int L = (p + 63) / 64;
@@ -1106,7 +1127,7 @@ bool launch_gemm_leaf_views(BMat A, BMat B, BMat C, const LeafViews &v, int64_t 
                             int64_t n, int p, DevStatus *st, cudaStream_t s, bool tma)
 {
     if (batch <= 0 || m <= 0 || n <= 0) return false;
-    if constexpr (W <= 32) {
+    if constexpr (W <= TMA_MAX_W) {
         if (tma) {
             // a quadrant in the right half starts l (A) or n (B) columns in:
             // the copies need that offset a whole number of 16-byte units

@@ -3,14 +3,14 @@
 the same bits (arXiv 1410.1599 Sec. 2, Eq. 2: every c_ij summed over k in
 ascending order, rounded after every operation).
 
-The cases cover every capacity class the copies serve (128 to 1024 bits),
+The cases cover every capacity class the copies serve (2 to 1024 bits),
 precisions whose limb count is below the class's (planes the copies leave
 zero), ragged tiles in m, n and the k-slabs, plain Block products, batched
 products and Strassen / Winograd leaves read in place from their parents'
 quadrants, recursions whose quadrants start at odd columns (the children are
 then all written, with even row strides, and staged by TMA), and layouts the
-copies cannot address (a caller's odd row stride, 2048 bits), where the
-library falls back to the threads' loads.  The profiler's launch counts say
+copies cannot address (a caller's odd row stride) and the 2048-bit class,
+where the library keeps the threads' loads.  The profiler's launch counts say
 which kernel ran."""
 import numpy as np
 import pytest
@@ -65,12 +65,27 @@ def test_block_odd_stride_falls_back(p):
     assert_bits_equal(got, orc.gemm(orc.SIMPLE, A, B), "fallback p=%d" % p)
 
 
-def test_wide_classes_keep_thread_staging():
-    A = gen.uniform_pm1(34, 36, 2048, 75, -16, 16)
-    B = gen.uniform_pm1(36, 40, 2048, 76, -16, 16)
+@pytest.mark.parametrize("p", [1500, 2048])
+def test_2048_bit_class_keeps_thread_staging(p):
+    A = gen.uniform_pm1(34, 36, p, 75, -16, 16)
+    B = gen.uniform_pm1(36, 40, p, 76, -16, 16)
     got, n_tma, n_thr = run(A, B, mp.BLOCK, 64, True)
     assert (n_tma, n_thr) == (0, 1)
-    assert_bits_equal(got, orc.gemm(orc.SIMPLE, A, B), "2048 bits")
+    assert_bits_equal(got, orc.gemm(orc.SIMPLE, A, B), "%d bits" % p)
+    A = gen.uniform_pm1(72, 48, p, 77, -16, 16)
+    B = gen.uniform_pm1(48, 56, p, 78, -16, 16)
+    got, n_tma, n_thr = run(A, B, mp.WINOGRAD, 16, True)
+    assert (n_tma, n_thr) == (0, 1)
+    assert_bits_equal(got, orc.gemm(mp.WINOGRAD, A, B, cutoff=16, policy=orc.PEEL), "%d-bit leaves" % p)
+
+
+def test_wide_class_has_no_block_kernel():
+    # above 2048 bits the Block product runs the batched Simple kernel
+    A = gen.uniform_pm1(10, 12, 4000, 75, -16, 16)
+    B = gen.uniform_pm1(12, 14, 4000, 76, -16, 16)
+    got, n_tma, n_thr = run(A, B, mp.BLOCK, 64, True)
+    assert (n_tma, n_thr) == (0, 1)
+    assert_bits_equal(got, orc.gemm(orc.SIMPLE, A, B), "4000 bits")
 
 
 @pytest.mark.parametrize("algo", [mp.WINOGRAD, mp.STRASSEN])
@@ -107,13 +122,12 @@ def test_odd_leaves_use_materialised_children(algo, n, cutoff):
     assert_bits_equal(ref, want, "odd leaves, thread-staged, n=%d" % n)
 
 
-def test_recursion_at_2048_bits_keeps_thread_staging():
-    A = gen.uniform_pm1(40, 40, 2048, 83, -16, 16)
-    B = gen.uniform_pm1(40, 40, 2048, 84, -16, 16)
-    want = orc.gemm(mp.WINOGRAD, A, B, cutoff=16, policy=orc.PEEL)
-    got, n_tma, n_thr = run(A, B, mp.WINOGRAD, 16, True)
+def test_user_layout_with_odd_stride_falls_back():
+    A = gen.uniform_pm1(21, 35, 1024, 83, -16, 16)          # ld 35: no tensor map
+    B = gen.uniform_pm1(35, 19, 1024, 84, -16, 16)
+    got, n_tma, n_thr = run(A, B, mp.BLOCK, 64, True)
     assert n_tma == 0 and n_thr == 1
-    assert_bits_equal(got, want, "2048-bit leaves")
+    assert_bits_equal(got, orc.gemm(orc.SIMPLE, A, B), "1024 bits, odd stride")
 
 
 @pytest.mark.parametrize("algo", [mp.WINOGRAD, mp.STRASSEN])
